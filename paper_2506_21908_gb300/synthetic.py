@@ -1,0 +1,344 @@
+"""Seeded synthetic workloads for the spinor real-time propagation step.
+
+This module only builds inputs: cell, grid, atoms, projector constants,
+k-points, occupations, field tables and initial spinors.  It holds none of
+the propagation arithmetic, so both the CUDA library and the FP64 oracle can
+be fed the very same arrays.
+
+Workloads stand in for the paper's systems (Fe2/Fe6 clusters and bcc Fe
+supercells, Sec. 4), which need pseudopotential files that are not
+available: synthetic Z=8 atoms with an erf-screened local potential,
+Gaussian Kleinman-Bylander projectors (Eq. Vps) and an L.S coupling of
+0.02 Ha (Eq. Vps-soc).
+
+Array conventions (shared by every consumer):
+  * grid arrays are indexed [z][y][x] (x fastest); r = (x*hx, y*hy, z*hz)
+  * spinors are complex128 arrays [nk][nstates][2][nz][ny][nx], normalised
+    with the grid inner product  <a|b> = sum_r conj(a) b dV
+  * field tables hold A(t) and B(t) in atomic units at given times
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+FS_AU = 41.341373335  # atomic units of time per femtosecond
+BOHR_PER_ANGSTROM = 1.0 / 0.529177210903
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    L: np.ndarray            # (3,) orthorhombic cell lengths, bohr
+    n: int                   # grid points per axis (cubic grid)
+    pos: np.ndarray          # (natoms, 3) bohr
+    species: np.ndarray      # (natoms,) int32
+    Z: np.ndarray            # (nspecies,)
+    rc_loc: np.ndarray       # (nspecies,)  local potential -Z erf(r/rc)/r
+    width: np.ndarray        # (nspecies,)  projector Gaussian width
+    lmax: int
+    D: np.ndarray            # (nspecies, lmax+1) Ha, KB channel energies
+    lam: np.ndarray          # (nspecies, lmax+1) Ha, L.S coefficient
+    r_cut: float
+    kpts: np.ndarray         # (nk, 3) cartesian, 1/bohr
+    kw: np.ndarray           # (nk,)
+    occ: np.ndarray          # (nk, nstates)
+    dt: float
+    nsteps: int
+    seed: int
+    times: np.ndarray = None  # (nt,) field table times
+    A: np.ndarray = None      # (nt, 3) vector potential
+    B: np.ndarray = None      # (nt, 3) magnetic field
+    xc: int = 1
+    n_sc: int = 1
+    exp_order: int = 0
+
+    @property
+    def nk(self):
+        return self.kpts.shape[0]
+
+    @property
+    def nstates(self):
+        return self.occ.shape[1]
+
+    @property
+    def ng(self):
+        return self.n ** 3
+
+    @property
+    def updates_per_step(self):
+        """Spinor-grid-point updates per step: N_k * N_occ * N_g."""
+        return self.nk * self.nstates * self.ng
+
+
+# ----------------------------------------------------------------------------
+# fields
+
+def gauss_laser_E(t, E0, omega, t0, tau, pol):
+    """E(t) = E0 pol cos(omega (t - t0)) exp(-(t-t0)^2 / (2 tau^2)) (Sec. 4.4 pulse form)."""
+    t = np.asarray(t, dtype=np.float64)
+    env = np.exp(-((t - t0) ** 2) / (2.0 * tau * tau))
+    return (E0 * np.cos(omega * (t - t0)) * env)[..., None] * np.asarray(pol, np.float64)
+
+
+def vector_potential_table(times, efield, nquad=16):
+    """A(t) = -int_{t_0}^{t} E dt' on the given (sorted) times, Gauss-Legendre per interval."""
+    x, w = np.polynomial.legendre.leggauss(nquad)
+    A = np.zeros((len(times), 3))
+    for i in range(1, len(times)):
+        a, b = times[i - 1], times[i]
+        tq = 0.5 * (b - a) * x + 0.5 * (b + a)
+        integral = (0.5 * (b - a) * w[:, None] * efield(tq)).sum(axis=0)
+        A[i] = A[i - 1] - integral
+    return A
+
+
+def laser_table(nsteps, dt, E0=0.01, omega=0.057, fwhm_fs=10.0, pol=(1.0, 0.0, 0.0),
+                t0=None, B_static=(0.0, 0.0, 0.0)):
+    """Field table at every step time for a Gaussian laser in velocity gauge.
+
+    The FWHM refers to the field envelope; the pulse peak sits at the middle
+    of the run unless t0 is given."""
+    times = np.arange(nsteps + 1, dtype=np.float64) * dt
+    tau = fwhm_fs * FS_AU / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    if t0 is None:
+        t0 = 0.5 * nsteps * dt
+    A = vector_potential_table(times, lambda t: gauss_laser_E(t, E0, omega, t0, tau, pol))
+    B = np.tile(np.asarray(B_static, np.float64), (len(times), 1))
+    return times, A, B
+
+
+def zero_fields(nsteps, dt):
+    times = np.arange(nsteps + 1, dtype=np.float64) * dt
+    return times, np.zeros((len(times), 3)), np.zeros((len(times), 3))
+
+
+# ----------------------------------------------------------------------------
+# geometry
+
+def icosahedron(center, radius):
+    """13-atom cluster: centre atom plus the 12 vertices of an icosahedron at the given radius."""
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    v = []
+    for a in (-1.0, 1.0):
+        for b in (-phi, phi):
+            v += [(0.0, a, b), (a, b, 0.0), (b, 0.0, a)]
+    v = np.array(v)
+    v *= radius / np.linalg.norm(v[0])
+    return np.vstack([np.asarray(center)[None, :], np.asarray(center)[None, :] + v])
+
+
+def bcc_supercell(a, reps, jitter=0.0, rng=None):
+    pos = []
+    for i in range(reps):
+        for j in range(reps):
+            for k in range(reps):
+                base = np.array([i, j, k], dtype=np.float64) * a
+                pos.append(base)
+                pos.append(base + 0.5 * a)
+    pos = np.array(pos)
+    if jitter > 0.0:
+        pos = pos + rng.normal(0.0, jitter, size=pos.shape)
+    L = a * reps
+    return np.mod(pos, L)
+
+
+def min_image(d, L):
+    return d - L * np.round(d / L)
+
+
+def grid_coords(L, n):
+    h = np.asarray(L, np.float64) / n
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    return np.stack([x * h[0], y * h[1], z * h[2]], axis=-1)  # [z][y][x][3]
+
+
+# ----------------------------------------------------------------------------
+# initial spinors
+
+def _gram_schmidt(phis, dV):
+    """Modified Gram-Schmidt in index order with the grid inner product."""
+    out = []
+    for p in phis:
+        q = p.copy()
+        for o in out:
+            q = q - (np.vdot(o, q) * dV) * o
+        q = q / math.sqrt((np.vdot(q, q).real) * dV)
+        out.append(q)
+    return np.array(out)
+
+
+def random_tilted_states(L, n, nstates, seed, polar_deg=30.0):
+    """Seeded complex Gaussian orbitals, orthonormalised, each times the spinor
+    (cos(theta/2), sin(theta/2)) with the spin tilted polar_deg from z."""
+    rng = np.random.default_rng(seed)
+    dV = float(np.prod(L)) / n ** 3
+    phis = rng.normal(size=(nstates, n, n, n)) + 1j * rng.normal(size=(nstates, n, n, n))
+    phis = _gram_schmidt(phis.reshape(nstates, -1), dV).reshape(nstates, n, n, n)
+    th = math.radians(polar_deg)
+    chi = np.array([math.cos(th / 2.0), math.sin(th / 2.0)])
+    psi = phis[:, None, :, :, :] * chi[None, :, None, None, None]
+    return psi[None].astype(np.complex128)
+
+
+def spinor_along(theta, phi, parallel=True):
+    if parallel:
+        return np.array([math.cos(theta / 2.0), np.exp(1j * phi) * math.sin(theta / 2.0)])
+    return np.array([-np.exp(-1j * phi) * math.sin(theta / 2.0), math.cos(theta / 2.0)])
+
+
+def lowdin(psi_k, dV):
+    """Loewdin orthonormalisation of the rows of psi_k (nstates, npts)."""
+    S = (psi_k.conj() @ psi_k.T) * dV
+    w, U = np.linalg.eigh(S)
+    Sm = (U * (1.0 / np.sqrt(w))) @ U.conj().T
+    return Sm.T @ psi_k
+
+
+def atomic_orbital_states(L, n, pos, kpts, axes, per_atom=8, n_par=5, sigma=1.0, seed=0):
+    """8 orbitals per atom: seeded random complex combinations of the s, p and d
+    Gaussians (width sigma) on that atom; n_par parallel and the rest
+    antiparallel to the atom's spin axis; Bloch phase folded into u_k;
+    Loewdin-orthonormalised per k-point."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(L, np.float64)
+    r = grid_coords(L, n).reshape(-1, 3)
+    dV = float(np.prod(L)) / n ** 3
+    nk = len(kpts)
+    natoms = len(pos)
+    ns = natoms * per_atom
+    coef = rng.normal(size=(natoms, per_atom, 9)) + 1j * rng.normal(size=(natoms, per_atom, 9))
+    out = np.empty((nk, ns, 2, n ** 3), np.complex128)
+    for a in range(natoms):
+        d = min_image(r - pos[a], L)
+        g = np.exp(-(d * d).sum(-1) / (2.0 * sigma * sigma))
+        x, y, z = d[:, 0], d[:, 1], d[:, 2]
+        basis = np.stack([g, x * g, y * g, z * g, x * y * g, y * z * g, z * x * g,
+                          (x * x - y * y) * g, (3 * z * z - (d * d).sum(-1)) * g])
+        orbs = coef[a] @ basis  # (per_atom, npts)
+        th, ph = axes[a]
+        for j in range(per_atom):
+            chi = spinor_along(th, ph, parallel=(j < n_par))
+            for ik, kv in enumerate(kpts):
+                phase = np.exp(-1j * ((pos[a][None, :] + d) @ kv))
+                out[ik, a * per_atom + j, 0] = chi[0] * orbs[j] * phase
+                out[ik, a * per_atom + j, 1] = chi[1] * orbs[j] * phase
+    for ik in range(nk):
+        flat = out[ik].reshape(ns, -1)
+        out[ik] = lowdin(flat, dV).reshape(ns, 2, -1)
+    return out.reshape(nk, ns, 2, n, n, n)
+
+
+# ----------------------------------------------------------------------------
+# workloads
+
+def _species_block(nspecies, lmax, Z=8.0, rc=0.8, width=1.0, lam=0.0):
+    D_all = np.array([1.0, 0.5, 0.25, 0.125])[: lmax + 1]
+    D = np.tile(D_all, (nspecies, 1))
+    lam_arr = np.full((nspecies, lmax + 1), lam)
+    lam_arr[:, 0] = 0.0
+    return (np.full(nspecies, Z), np.full(nspecies, rc), np.full(nspecies, width), D, lam_arr)
+
+
+def tiny(seed=20250621):
+    """Tiny oracle case: 10 bohr cube, 24^3, one Z=8 atom, l=0,1 projectors without SOC,
+    4 random spinors tilted 30 deg, 10 steps of dt=0.05, no field."""
+    L = np.array([10.0, 10.0, 10.0])
+    n = 24
+    Z, rc, w, D, lam = _species_block(1, 1)
+    times, A, B = zero_fields(10, 0.05)
+    return Workload("tiny", L, n, np.array([[5.0, 5.0, 5.0]]), np.zeros(1, np.int32), Z, rc, w, 1,
+                    D, lam, 5.0, np.zeros((1, 3)), np.ones(1), np.ones((1, 4)), 0.05, 10, seed,
+                    times, A, B)
+
+
+def tiny_states(wl):
+    return random_tilted_states(wl.L, wl.n, wl.nstates, wl.seed)
+
+
+def cluster(n=64, nsteps=2000, seed=20250622, lam=0.02, laser=True):
+    """13-atom icosahedral cluster (centre-vertex 4.7 bohr) in a 24 bohr cube; Z=8 atoms with
+    l=0,1,2 projectors and L.S coefficient 0.02 Ha; 104 occupied spinors of 112
+    (only occupied ones are propagated); Gaussian x-polarised laser in velocity gauge."""
+    L = np.array([24.0, 24.0, 24.0])
+    pos = icosahedron(L / 2.0, 4.7)
+    Z, rc, w, D, lam_arr = _species_block(1, 2, lam=lam)
+    dt = 0.04
+    if laser:
+        times, A, B = laser_table(nsteps, dt)
+    else:
+        times, A, B = zero_fields(nsteps, dt)
+    return Workload("cluster%d" % n, L, n, pos, np.zeros(13, np.int32), Z, rc, w, 2, D, lam_arr, 5.0,
+                    np.zeros((1, 3)), np.ones(1), np.ones((1, 104)), dt, nsteps, seed, times, A, B)
+
+
+def cluster_axes(natoms, tilted=1, tilt_deg=20.0):
+    axes = [(0.0, 0.0)] * natoms
+    axes[tilted] = (math.radians(tilt_deg), 0.0)
+    return axes
+
+
+def cluster_states(wl, per_atom=8):
+    return atomic_orbital_states(wl.L, wl.n, wl.pos, wl.kpts, cluster_axes(len(wl.pos)),
+                                 per_atom=per_atom, seed=wl.seed)
+
+
+def bcc(nsteps=1000, seed=20250623):
+    """2x2x2 bcc supercell (a=5.42 bohr, 16 Z=8 atoms with L.S 0.02 Ha) on 48^3; 2x2x2
+    Monkhorst-Pack k-points; 128 occupied spinors of 144 per k; static B_x = 0.001 plus laser."""
+    a = 5.42
+    L = np.array([2 * a] * 3)
+    pos = bcc_supercell(a, 2)
+    Z, rc, w, D, lam = _species_block(1, 2, lam=0.02)
+    q = 0.25 * 2.0 * math.pi / L[0]
+    kpts = np.array([[sx * q, sy * q, sz * q] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)])
+    dt = 0.04
+    times, A, B = laser_table(nsteps, dt, B_static=(0.001, 0.0, 0.0))
+    return Workload("bcc48", L, 48, pos, np.zeros(16, np.int32), Z, rc, w, 2, D, lam, 5.0,
+                    kpts, np.full(8, 1.0 / 8.0), np.ones((8, 128)), dt, nsteps, seed, times, A, B)
+
+
+def bcc_states(wl):
+    return atomic_orbital_states(wl.L, wl.n, wl.pos, wl.kpts, [(0.0, 0.0)] * len(wl.pos), seed=wl.seed)
+
+
+def small_parity(n=16, nstates=5, nk=2, seed=7, lam=0.02, lmax=2, field=True, natoms=3):
+    """Small multi-feature case for element-wise parity: several atoms with SOC, two k-points,
+    an odd number of states, laser plus static B."""
+    rng = np.random.default_rng(seed)
+    L = np.array([9.0, 9.0, 9.0])
+    pos = rng.uniform(0.0, 9.0, size=(natoms, 3))
+    Z, rc, w, D, lam_arr = _species_block(1, lmax, lam=lam, Z=3.0)
+    kpts = rng.uniform(-0.3, 0.3, size=(nk, 3)) if nk > 1 else np.zeros((1, 3))
+    kw = np.full(nk, 1.0 / nk)
+    occ = np.ones((nk, nstates))
+    occ[:, -1] = 0.5
+    dt = 0.05
+    nsteps = 4
+    if field:
+        times, A, B = laser_table(nsteps, dt, E0=0.3, omega=0.3, fwhm_fs=0.2, pol=(0.6, 0.0, 0.8),
+                                  B_static=(0.02, -0.01, 0.03))
+    else:
+        times, A, B = zero_fields(nsteps, dt)
+    return Workload("parity%d" % n, L, n, pos, np.zeros(natoms, np.int32), Z, rc, w, lmax, D, lam_arr,
+                    4.0, kpts, kw, occ, dt, nsteps, seed, times, A, B)
+
+
+def small_parity_states(wl):
+    rng = np.random.default_rng(wl.seed + 1)
+    n = wl.n
+    dV = float(np.prod(wl.L)) / n ** 3
+    out = np.empty((wl.nk, wl.nstates, 2, n, n, n), np.complex128)
+    for ik in range(wl.nk):
+        raw = rng.normal(size=(wl.nstates, 2 * n ** 3)) + 1j * rng.normal(size=(wl.nstates, 2 * n ** 3))
+        # smooth the states a little so the kinetic energy stays moderate
+        raw = raw.reshape(wl.nstates, 2, n, n, n)
+        f = np.fft.fftn(raw, axes=(-3, -2, -1))
+        g = np.fft.fftfreq(n) * n
+        gz, gy, gx = np.meshgrid(g, g, g, indexing="ij")
+        f *= np.exp(-(gx ** 2 + gy ** 2 + gz ** 2) / (0.08 * n * n))
+        raw = np.fft.ifftn(f, axes=(-3, -2, -1)).reshape(wl.nstates, -1)
+        out[ik] = lowdin(raw, dV).reshape(wl.nstates, 2, n, n, n)
+    return out
