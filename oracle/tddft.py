@@ -202,15 +202,19 @@ class FieldTable:
 
 
 class AtomProjectors:
-    """Sphere of grid points around one atom (|d| < r_cut, minimum image) with the
-    real projector values beta[(l,mu), point] (reading P5)."""
+    """Sphere of grid points around one atom (|d| < r_cut, minimum image, surface points
+    excluded with a 1e-10 relative margin) with the real projector values
+    beta[(l,mu), point] (reading P5)."""
 
     def __init__(self, grid, R, w, lmax, r_cut):
         r = grid.r.reshape(-1, 3)
         d = r - R
         d = d - grid.L * np.round(d / grid.L)
         dist = np.sqrt((d * d).sum(-1))
-        sel = dist < r_cut
+        # points on the cut-off sphere itself (|d| = r_cut in exact arithmetic, common when the
+        # grid is commensurate with r_cut) are excluded with a 1e-10 relative margin, so that the
+        # set does not depend on the rounding of |d|
+        sel = (d * d).sum(-1) < r_cut * r_cut * (1.0 - 1e-10)
         self.idx = np.nonzero(sel)[0]
         self.d = d[sel]
         dd = dist[sel]
