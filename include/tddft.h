@@ -1,0 +1,213 @@
+/*
+ * tddft.h -- C ABI of the GB300 (sm_103a) spinor real-time TDDFT propagation library.
+ *
+ * One handle holds one periodic system: a cubic FFT grid in an orthorhombic cell,
+ * atoms with an erf-screened local potential and separable Kleinman-Bylander
+ * projectors with spin-orbit coupling, a set of k-points and the occupied
+ * two-component spinors psi_{k,i}.  Each call of tddft_step advances the spinors
+ * by the time-dependent non-collinear Kohn-Sham equation (arXiv 2506.21908,
+ * Eq. TDSDFT) with the Hamiltonian of Eq. HNC-SDFT:
+ *
+ *     H = [-1/2 nabla^2 + v_loc + v_H + vbar_xc] I_2 + (b_xc + mu_B B(t)) . sigma + V_NL,
+ *
+ * vbar_xc and b_xc from the adiabatic locally collinear LSDA (Eqs. LC+ALDA2, LC+ALDA),
+ * the spin Zeeman term of Eq. zeeman_potential (mu_B = 1/2), and
+ * V_NL = sum_a |beta~> (D_l + lambda_l L.S) <beta~| (Eq. Vps, Eq. Vps-soc and the L.S
+ * form of Sec. 4.4).  Laser fields enter in velocity gauge: kinetic 1/2|G+k+A(t)|^2 and
+ * projector phases exp(-i (k+A).d).  The paper does not state its propagator; this
+ * library uses enforced time-reversal symmetry (ETRS) with a predictor and n_sc
+ * corrector passes, the exponential as a Chebyshev series (or a Taylor series).
+ * Each step ends with the density n(r) and magnetisation m(r) (Eqs. rho1-rho3) and
+ * the potential recomputed from them.
+ *
+ * Conventions for every entry point
+ *   - Every function returns a tddft_status (0 = success) and never aborts.  On failure
+ *     tddft_last_error(h) returns a message; the state is unchanged except after
+ *     TDDFT_ERR_DIVERGED.
+ *   - The caller owns every array it passes; the library copies inputs during the call
+ *     and owns all device memory it allocates (released by tddft_destroy).
+ *   - Grid arrays are indexed [z][y][x] with x fastest; r = (x hx, y hy, z hz).
+ *   - Spinor arrays are interleaved complex128 (re, im) laid out
+ *     [nk][nstates][2][nz][ny][nx], normalised with <a|b> = sum_r conj(a) b dV.
+ *   - Pointers flagged on_device = 1 are device pointers on the handle's device,
+ *     accessed on the handle's stream (tddft_set_stream); otherwise host pointers.
+ *   - Atomic units throughout (bohr, hartree, a.u. of time and field).
+ *   - tddft_step is asynchronous on the handle's stream; calls that return host data
+ *     synchronise that stream.
+ */
+#ifndef TDDFT_H
+#define TDDFT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tddft_ctx* tddft_handle;
+
+typedef enum {
+  TDDFT_OK = 0,
+  TDDFT_ERR_ARG = -1,         /* invalid argument (null pointer, size, unsupported grid) */
+  TDDFT_ERR_CUDA = -2,        /* a CUDA runtime call or kernel launch failed */
+  TDDFT_ERR_OOM = -3,         /* device allocation failed */
+  TDDFT_ERR_STATE = -4,       /* call out of order (e.g. step before set_states) */
+  TDDFT_ERR_DIVERGED = -5,    /* non-finite density or norm detected */
+  TDDFT_ERR_BOUND = -6,       /* the potential left the Chebyshev spectral window */
+  TDDFT_ERR_UNSUPPORTED = -7  /* valid request outside what this build implements */
+} tddft_status;
+
+enum { TDDFT_FP64 = 0, TDDFT_FP32_MIXED = 1 };
+enum { TDDFT_EXP_CHEBYSHEV = 0, TDDFT_EXP_TAYLOR = 1 };
+enum { TDDFT_PROJ_FP64 = 0, TDDFT_PROJ_FP32 = 1 };
+
+/* Energies returned by tddft_observables, indices into E[TDDFT_NE]. */
+enum {
+  TDDFT_E_KIN = 0,    /* sum w f <psi| 1/2|G+k+A|^2 |psi>                                   */
+  TDDFT_E_NL = 1,     /* sum w f <psi|V_NL|psi>                                            */
+  TDDFT_E_LOC = 2,    /* int v_loc n                                                       */
+  TDDFT_E_H = 3,      /* 1/2 int v_H n                                                     */
+  TDDFT_E_XC = 4,     /* int n eps_xc (the functional value)                               */
+  TDDFT_E_Z = 5,      /* int mu_B B . m  (Sec. 3.4)                                        */
+  TDDFT_E_TOTAL = 6,  /* sum of the six terms above (ion-ion constant excluded)            */
+  TDDFT_E_TIME = 7,   /* current time t                                                    */
+  TDDFT_E_XC_POT = 8, /* int <rho_v, V_v^xc>, the potential-weighted form of Eq. xc_energy4 */
+  TDDFT_E_NELEC = 9,  /* int n                                                             */
+  TDDFT_NE = 10
+};
+
+/* Orthorhombic cell: rows are lattice vectors (bohr).  Off-diagonal entries must be 0. */
+typedef struct { double a[3][3]; } tddft_cell;
+
+/* FFT grid: n[0] = n[1] = n[2] = n with n in {8, 12, 16, 24, 32, 48, 64, 96}. */
+typedef struct { int n[3]; } tddft_grid;
+
+/* Atoms: pos[natoms][3] (bohr, cartesian), species[natoms] in [0, nspecies). natoms may be 0. */
+typedef struct {
+  int natoms;
+  const double* pos;
+  const int* species;
+} tddft_atoms;
+
+/* Species data (Eq. KSpot, Eq. Vps, Eq. Vps-soc).  Per species s:
+ *   local potential -Z[s] erf(r / rc_loc[s]) / r, periodic, G = 0 keeps pi Z rc^2 / Omega;
+ *   projectors beta_{l,m}(d) = N_l |d|^l exp(-|d|^2 / (2 width[s]^2)) Y^real_lm(d/|d|),
+ *   |d| < r_cut (minimum image), continuum-normalised, l = 0..lmax (lmax <= 2);
+ *   coupling on (l, m, sigma): D[s][l] I + lambda_so[s][l] L.S  (Ha).
+ * D and lambda_so are [nspecies][lmax+1].  r_cut must be at most half the shortest cell side
+ * (points are kept for |d| < r_cut, so each has a single minimum image). */
+typedef struct {
+  int nspecies;
+  const double* Z;
+  const double* rc_loc;
+  const double* width;
+  int lmax;
+  const double* D;
+  const double* lambda_so;
+  double r_cut;
+} tddft_projectors;
+
+/* Run parameters.
+ *   precision : TDDFT_FP64, or TDDFT_FP32_MIXED (spinors, FFTs, potential apply and projectors
+ *               in FP32; density, XC, Hartree, energies and norms in FP64)
+ *   proj_mode : TDDFT_PROJ_FP64 / TDDFT_PROJ_FP32 (ignored in FP64 precision)
+ *   nk, kpts[nk][3] (1/bohr, cartesian), kw[nk] (weights)
+ *   nstates   : propagated spinors per k-point; occ[nk][nstates] occupations f
+ *   dt        : time step (may be negative to run backwards)
+ *   exp_kind  : TDDFT_EXP_CHEBYSHEV or TDDFT_EXP_TAYLOR
+ *   exp_order : 0 = automatic (Chebyshev: smallest K with |J_k(tau Delta)| < cheb_tol for all
+ *               k > K, separately for dt and dt/2); > 0 = this order for every exponential
+ *               (Taylor default 4)
+ *   cheb_tol  : truncation tolerance for automatic orders (0 = 1e-16 FP64, 1e-9 FP32-mixed)
+ *   n_sc      : corrector passes per step; sc_tol > 0 stops them early when
+ *               max |delta rho_v| < sc_tol (that check synchronises the stream)
+ *   e_min, e_max : Chebyshev spectral window; both 0 = automatic at tddft_set_states
+ *   xc        : 1 = locally collinear LSDA (Slater + PW92), 0 = no exchange-correlation */
+typedef struct {
+  int precision;
+  int proj_mode;
+  int nk;
+  const double* kpts;
+  const double* kw;
+  int nstates;
+  const double* occ;
+  double dt;
+  int exp_kind;
+  int exp_order;
+  double cheb_tol;
+  int n_sc;
+  double sc_tol;
+  double e_min;
+  double e_max;
+  int xc;
+} tddft_params;
+
+/* Create a handle on the current CUDA device: validates the inputs, builds the G mesh,
+ * the local potential, projector tables and L.S blocks, and allocates device memory.
+ * *out receives the handle (NULL on failure). */
+tddft_status tddft_create(const tddft_cell* cell, const tddft_grid* grid, const tddft_atoms* atoms,
+                          const tddft_projectors* proj, const tddft_params* params,
+                          tddft_handle* out);
+
+/* Tabulated external fields (velocity-gauge vector potential A and magnetic field B) at nt
+ * increasing times t[nt]; A[nt][3], B[nt][3].  Values between nodes are linearly
+ * interpolated; outside the table the end values are used.  Without a table A = B = 0. */
+tddft_status tddft_set_fields(tddft_handle h, int nt, const double* t, const double* A,
+                              const double* B);
+
+/* Load spinors (complex128, layout above) at time t0; computes rho_v, the potential and,
+ * when e_min = e_max = 0, the Chebyshev spectral window. */
+tddft_status tddft_set_states(tddft_handle h, const void* psi, int on_device, double t0);
+
+/* Copy the current spinors out as complex128 (layout above). */
+tddft_status tddft_get_states(tddft_handle h, void* psi, int on_device);
+
+/* Advance nsteps ETRS steps (asynchronous on the handle's stream). */
+tddft_status tddft_step(tddft_handle h, int nsteps);
+
+/* Observables of the current state (synchronises).  Any output may be NULL.
+ *   n[N_g], m[3][N_g] : density and magnetisation (1/bohr^3)
+ *   E[TDDFT_NE]       : energy terms (indices above)
+ *   M[3]              : int m dV
+ *   norms[nk*nstates] : <psi_i|psi_i>
+ * Returns TDDFT_ERR_BOUND if any potential since set_states left the spectral window and
+ * TDDFT_ERR_DIVERGED on non-finite values (outputs are still written). */
+tddft_status tddft_observables(tddft_handle h, double* n, double* m, double* E, double* M,
+                               double* norms);
+
+/* Current spin-matrix potential as the 4-vector V_v = [v+b_z, v-b_z, 2 b_x, -2 b_y]
+ * (Eq. potential4), host array [4][N_g]. */
+tddft_status tddft_get_potential(tddft_handle h, double* V);
+
+/* out = H psi for nk*nstates spinors (complex128 layout above) with the current potential
+ * and A(t) at the current time; in and out may not alias.  A diagnostic of the operator
+ * that tddft_step exponentiates. */
+tddft_status tddft_apply_hamiltonian(tddft_handle h, const void* in, void* out, int on_device);
+
+/* Use this CUDA stream (a cudaStream_t; NULL = legacy default stream) for all work. */
+tddft_status tddft_set_stream(tddft_handle h, void* stream);
+
+/* Introspection: Chebyshev orders for dt and dt/2, the spectral window, and the number of
+ * kernel launches issued since creation.  Any pointer may be NULL. */
+tddft_status tddft_info(tddft_handle h, int* K_full, int* K_half, double* e_min, double* e_max,
+                        long long* launches);
+
+/* Per-kernel-class timing with CUDA events on the handle's stream.  enable = 1 starts
+ * (and clears) recording; tddft_profile_read synchronises and returns, for class c,
+ * ms[c] total milliseconds, count[c] launches and bytes[c] the algorithmic DRAM bytes of
+ * those launches (each spinor array a launch must read or write counted once; tables
+ * shared by all spinors not counted).  Classes: 0 FFT xy-plane pass, 1 FFT z pass with
+ * kinetic multiply, 2 Hamiltonian/Chebyshev epilogue, 3 projector gather, 4 density,
+ * 5 potential (XC, Hartree, assembly), 6 other.  ncls <= 8; any output may be NULL. */
+tddft_status tddft_profile(tddft_handle h, int enable);
+tddft_status tddft_profile_read(tddft_handle h, int ncls, double* ms, long long* count, double* bytes);
+
+/* Message describing the last failure on this handle (or the last failed create when
+ * h is NULL).  The string stays valid until the next call on the handle. */
+const char* tddft_last_error(tddft_handle h);
+
+/* Release the handle and all its device memory.  NULL is accepted. */
+void tddft_destroy(tddft_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDDFT_H */

@@ -1,0 +1,264 @@
+"""ctypes binding of libtddft.so (include/tddft.h): argument marshalling only.
+
+Every step of the propagation runs inside the CUDA library; this module only
+packs structs, passes pointers (numpy host arrays or torch CUDA tensors) and
+turns status codes into exceptions.  There is no CPU fallback: if the library
+is missing or cannot be loaded, ``load()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtddft.so")
+
+FP64, FP32_MIXED = 0, 1
+EXP_CHEBYSHEV, EXP_TAYLOR = 0, 1
+E_NAMES = ["kin", "nl", "loc", "H", "xc", "Z", "total", "t", "xc_pot", "N"]
+KERNEL_CLASSES = ["fft_xy", "fft_z_kinetic", "epilogue", "proj_gather", "density", "potential", "other"]
+
+# Every entry point declared in include/tddft.h (checked by the CPU tests).
+EXPORTS = ["tddft_create", "tddft_set_fields", "tddft_set_states", "tddft_get_states", "tddft_step",
+           "tddft_observables", "tddft_get_potential", "tddft_apply_hamiltonian", "tddft_set_stream",
+           "tddft_info", "tddft_profile", "tddft_profile_read", "tddft_last_error", "tddft_destroy"]
+
+
+class TddftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("tddft status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Cell(ctypes.Structure):
+    _fields_ = [("a", (ctypes.c_double * 3) * 3)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3)]
+
+
+class Atoms(ctypes.Structure):
+    _fields_ = [("natoms", ctypes.c_int), ("pos", ctypes.c_void_p), ("species", ctypes.c_void_p)]
+
+
+class Projectors(ctypes.Structure):
+    _fields_ = [("nspecies", ctypes.c_int), ("Z", ctypes.c_void_p), ("rc_loc", ctypes.c_void_p),
+                ("width", ctypes.c_void_p), ("lmax", ctypes.c_int), ("D", ctypes.c_void_p),
+                ("lambda_so", ctypes.c_void_p), ("r_cut", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("proj_mode", ctypes.c_int), ("nk", ctypes.c_int),
+                ("kpts", ctypes.c_void_p), ("kw", ctypes.c_void_p), ("nstates", ctypes.c_int),
+                ("occ", ctypes.c_void_p), ("dt", ctypes.c_double), ("exp_kind", ctypes.c_int),
+                ("exp_order", ctypes.c_int), ("cheb_tol", ctypes.c_double), ("n_sc", ctypes.c_int),
+                ("sc_tol", ctypes.c_double), ("e_min", ctypes.c_double), ("e_max", ctypes.c_double),
+                ("xc", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def load(path=LIB_PATH):
+    """Load libtddft.so and declare its signatures; raises if it is absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libtddft.so not built (run __graft_entry__.build()): %s" % path)
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "tddft_create": [vp, vp, vp, vp, vp, ctypes.POINTER(vp)],
+        "tddft_set_fields": [vp, i, vp, vp, vp],
+        "tddft_set_states": [vp, vp, i, d],
+        "tddft_get_states": [vp, vp, i],
+        "tddft_step": [vp, i],
+        "tddft_observables": [vp, vp, vp, vp, vp, vp],
+        "tddft_get_potential": [vp, vp],
+        "tddft_apply_hamiltonian": [vp, vp, vp, i],
+        "tddft_set_stream": [vp, vp],
+        "tddft_info": [vp, vp, vp, vp, vp, vp],
+        "tddft_profile": [vp, i],
+        "tddft_profile_read": [vp, i, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.tddft_last_error.argtypes = [vp]
+    lib.tddft_last_error.restype = ctypes.c_char_p
+    lib.tddft_destroy.argtypes = [vp]
+    lib.tddft_destroy.restype = None
+    _LIB = lib
+    return lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class TDDFT:
+    """One propagation handle (owns the device state through the library)."""
+
+    def __init__(self, L, n, pos, species, Z, rc_loc, width, lmax, D, lam, r_cut, kpts, kw, occ, dt,
+                 precision=FP64, exp_kind=EXP_CHEBYSHEV, exp_order=0, cheb_tol=0.0, n_sc=1, sc_tol=0.0,
+                 e_min=0.0, e_max=0.0, xc=1, proj_mode=None, stream=None):
+        self.lib = load()
+        self._keep = []
+        L = _f64(L)
+        cell = Cell()
+        for a in range(3):
+            for b in range(3):
+                cell.a[a][b] = L[a] if a == b else 0.0
+        grid = Grid()
+        for a in range(3):
+            grid.n[a] = int(n)
+        pos = _f64(pos).reshape(-1, 3)
+        species = np.ascontiguousarray(species, dtype=np.int32)
+        self._keep += [pos, species]
+        atoms = Atoms(len(pos), _ptr(pos).value if len(pos) else None, _ptr(species).value if len(pos) else None)
+        arrs = [_f64(Z), _f64(rc_loc), _f64(width), _f64(D), _f64(lam)]
+        self._keep += arrs
+        proj = Projectors(len(arrs[0]), _ptr(arrs[0]).value, _ptr(arrs[1]).value, _ptr(arrs[2]).value, int(lmax),
+                          _ptr(arrs[3]).value, _ptr(arrs[4]).value, float(r_cut))
+        kpts = _f64(kpts).reshape(-1, 3)
+        kw = _f64(kw)
+        occ = _f64(occ).reshape(len(kpts), -1)
+        self._keep += [kpts, kw, occ]
+        if proj_mode is None:
+            proj_mode = 0 if precision == FP64 else 1
+        prm = Params(int(precision), int(proj_mode), len(kpts), _ptr(kpts).value, _ptr(kw).value, occ.shape[1],
+                     _ptr(occ).value, float(dt), int(exp_kind), int(exp_order), float(cheb_tol), int(n_sc),
+                     float(sc_tol), float(e_min), float(e_max), int(xc))
+        h = ctypes.c_void_p()
+        st = self.lib.tddft_create(ctypes.byref(cell), ctypes.byref(grid), ctypes.byref(atoms), ctypes.byref(proj),
+                                   ctypes.byref(prm), ctypes.byref(h))
+        if st != 0:
+            raise TddftError(st, self.lib.tddft_last_error(None).decode())
+        self.h = h
+        self.n = int(n)
+        self.N3 = self.n ** 3
+        self.nk = len(kpts)
+        self.nstates = occ.shape[1]
+        self.precision = precision
+        if stream is not None:
+            self.set_stream(stream)
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        return cls(wl.L, wl.n, wl.pos, wl.species, wl.Z, wl.rc_loc, wl.width, wl.lmax, wl.D, wl.lam, wl.r_cut,
+                   wl.kpts, wl.kw, wl.occ, wl.dt, xc=kw.pop("xc", wl.xc), n_sc=kw.pop("n_sc", wl.n_sc),
+                   exp_order=kw.pop("exp_order", wl.exp_order), **kw)
+
+    def _check(self, st):
+        if st != 0:
+            raise TddftError(st, self.lib.tddft_last_error(self.h).decode())
+
+    @property
+    def psi_shape(self):
+        return (self.nk, self.nstates, 2, self.n, self.n, self.n)
+
+    def set_stream(self, stream):
+        self._check(self.lib.tddft_set_stream(self.h, ctypes.c_void_p(stream)))
+
+    def set_fields(self, times, A, B):
+        times, A, B = _f64(times), _f64(A).reshape(-1, 3), _f64(B).reshape(-1, 3)
+        self._check(self.lib.tddft_set_fields(self.h, len(times), _ptr(times), _ptr(A), _ptr(B)))
+
+    @staticmethod
+    def _is_dev(x):
+        return hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)
+
+    def _spinor_arg(self, psi):
+        if self._is_dev(psi):
+            assert psi.is_contiguous() and str(psi.dtype) == "torch.complex128", "need contiguous complex128"
+            assert psi.numel() == int(np.prod(self.psi_shape))
+            return psi, 1
+        arr = np.ascontiguousarray(psi, dtype=np.complex128)
+        assert arr.size == int(np.prod(self.psi_shape)), "spinor array has the wrong size"
+        return arr, 0
+
+    def set_states(self, psi, t0=0.0):
+        arr, dev = self._spinor_arg(psi)
+        self._check(self.lib.tddft_set_states(self.h, _ptr(arr), dev, float(t0)))
+
+    def get_states(self, out=None):
+        if out is None:
+            out = np.empty(self.psi_shape, np.complex128)
+        arr, dev = self._spinor_arg(out)
+        self._check(self.lib.tddft_get_states(self.h, _ptr(arr), dev))
+        return out
+
+    def step(self, nsteps=1):
+        self._check(self.lib.tddft_step(self.h, int(nsteps)))
+
+    def observables(self, fields=True, check=True):
+        n = np.empty((self.n,) * 3) if fields else None
+        m = np.empty((3,) + (self.n,) * 3) if fields else None
+        E = np.empty(10)
+        M = np.empty(3)
+        norms = np.empty((self.nk, self.nstates))
+        st = self.lib.tddft_observables(self.h, _ptr(n), _ptr(m), _ptr(E), _ptr(M), _ptr(norms))
+        if check:
+            self._check(st)
+        Ed = dict(zip(E_NAMES, E.tolist()))
+        Ed["M"] = M
+        Ed["status"] = st
+        return n, m, Ed, norms
+
+    def get_potential(self):
+        V = np.empty((4,) + (self.n,) * 3)
+        self._check(self.lib.tddft_get_potential(self.h, _ptr(V)))
+        return V
+
+    def apply_hamiltonian(self, psi, out=None):
+        arr, dev = self._spinor_arg(psi)
+        if out is None:
+            out = np.empty(self.psi_shape, np.complex128)
+        oarr, odev = self._spinor_arg(out)
+        assert odev == dev
+        self._check(self.lib.tddft_apply_hamiltonian(self.h, _ptr(arr), _ptr(oarr), dev))
+        return out
+
+    def info(self):
+        kf, kh = ctypes.c_int(), ctypes.c_int()
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        nl = ctypes.c_longlong()
+        self._check(self.lib.tddft_info(self.h, ctypes.byref(kf), ctypes.byref(kh), ctypes.byref(lo),
+                                        ctypes.byref(hi), ctypes.byref(nl)))
+        return dict(K_full=kf.value, K_half=kh.value, e_min=lo.value, e_max=hi.value, launches=nl.value)
+
+    def profile(self, enable=True):
+        self._check(self.lib.tddft_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        ms = np.zeros(8)
+        cnt = np.zeros(8, np.int64)
+        by = np.zeros(8)
+        self._check(self.lib.tddft_profile_read(self.h, 8, _ptr(ms), _ptr(cnt), _ptr(by)))
+        return {name: dict(ms=float(ms[i]), launches=int(cnt[i]), bytes=float(by[i]))
+                for i, name in enumerate(KERNEL_CLASSES)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tddft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1148 @@
+// C ABI, host-side set-up and the propagation driver (one GPU, one stream).
+//
+// Set-up builds, once per handle: the FFT twiddles, the periodic local potential (on the
+// device), the projector sphere tables in gather and scatter order, and the coupling
+// blocks D_l I + lambda_l L.S (Eq. Vps-soc, L.S form of Sec. 4.4).  L is obtained by
+// applying -i r x grad exactly to the real solid-harmonic polynomials and projecting
+// back with exact sphere integrals of monomials.
+//
+// Each step is the ETRS scheme (propagator reading stated in include/tddft.h):
+//   series 1: T_k((H[rho(t), t] - c)/Delta) psi(t), accumulated into both
+//             psi~ = Exp(-i dt H) psi  and  phi = Exp(-i dt/2 H) psi  (shared T_k)
+//   rho~ = rho(psi~), V~ = V[rho~, t+dt]
+//   series 2: psi(t+dt) = Exp(-i dt/2 H[rho~, t+dt]) phi, repeated n_sc times with the
+//             corrected density, then rho(t+dt), V(t+dt).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <complex>
+#include <map>
+#include <array>
+#include <string>
+#include <vector>
+
+#include "impl.cuh"
+
+using namespace tddft;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------ real solid harmonics
+// S_{l,mu}(x, y, z) = r^l Y^real_{l,mu}, mu = -l..l, as monomial coefficient maps.
+using Mono = std::array<int, 3>;
+using Poly = std::map<Mono, double>;
+
+std::vector<Poly> solid_harmonics(int l) {
+  const double pi = 3.14159265358979323846;
+  std::vector<Poly> out;
+  if (l == 0) {
+    out.push_back({{{0, 0, 0}, 0.5 / std::sqrt(pi)}});
+  } else if (l == 1) {
+    const double c = std::sqrt(3.0 / (4.0 * pi));
+    out.push_back({{{0, 1, 0}, c}});  // y
+    out.push_back({{{0, 0, 1}, c}});  // z
+    out.push_back({{{1, 0, 0}, c}});  // x
+  } else if (l == 2) {
+    const double c = 0.5 * std::sqrt(15.0 / pi);
+    const double c0 = 0.25 * std::sqrt(5.0 / pi);
+    out.push_back({{{1, 1, 0}, c}});                                              // xy
+    out.push_back({{{0, 1, 1}, c}});                                              // yz
+    out.push_back({{{0, 0, 2}, 2.0 * c0}, {{2, 0, 0}, -c0}, {{0, 2, 0}, -c0}});   // 3z^2 - r^2
+    out.push_back({{{1, 0, 1}, c}});                                              // xz
+    out.push_back({{{2, 0, 0}, 0.5 * c}, {{0, 2, 0}, -0.5 * c}});                 // x^2 - y^2
+  }
+  return out;
+}
+
+double poly_eval(const Poly& p, double x, double y, double z) {
+  double s = 0.0;
+  for (auto& kv : p) s += kv.second * std::pow(x, kv.first[0]) * std::pow(y, kv.first[1]) * std::pow(z, kv.first[2]);
+  return s;
+}
+
+// (r x grad)_alpha applied to a polynomial (real part of i L_alpha ... times -1): returns Q with L = -i Q.
+Poly rxgrad(const Poly& p, int alpha) {
+  const int b = (alpha + 1) % 3, c = (alpha + 2) % 3;  // (r x grad)_a = x_b d_c - x_c d_b
+  Poly q;
+  for (auto& kv : p) {
+    const Mono& m = kv.first;
+    if (m[c] > 0) {  // x_b d_c
+      Mono n = m;
+      n[c] -= 1;
+      n[b] += 1;
+      q[n] += kv.second * m[c];
+    }
+    if (m[b] > 0) {  // - x_c d_b
+      Mono n = m;
+      n[b] -= 1;
+      n[c] += 1;
+      q[n] -= kv.second * m[b];
+    }
+  }
+  return q;
+}
+
+// Integral of x^a y^b z^c over the unit sphere.
+double sphere_monomial(int a, int b, int c) {
+  if ((a & 1) || (b & 1) || (c & 1)) return 0.0;
+  return 2.0 * std::tgamma(0.5 * (a + 1)) * std::tgamma(0.5 * (b + 1)) * std::tgamma(0.5 * (c + 1)) /
+         std::tgamma(0.5 * (a + b + c + 3));
+}
+
+double sphere_inner(const Poly& p, const Poly& q) {
+  double s = 0.0;
+  for (auto& x : p)
+    for (auto& y : q)
+      s += x.second * y.second * sphere_monomial(x.first[0] + y.first[0], x.first[1] + y.first[1], x.first[2] + y.first[2]);
+  return s;
+}
+
+// L_alpha[mu][nu] = <S_mu| L_alpha |S_nu> on the sphere (complex, purely imaginary).
+std::vector<std::vector<cd>> angular_momentum(int l, int alpha) {
+  auto S = solid_harmonics(l);
+  const int n = 2 * l + 1;
+  std::vector<std::vector<cd>> L(n, std::vector<cd>(n));
+  for (int nu = 0; nu < n; ++nu) {
+    Poly q = rxgrad(S[nu], alpha);
+    for (int mu = 0; mu < n; ++mu) L[mu][nu] = cd(0.0, -sphere_inner(S[mu], q));
+  }
+  return L;
+}
+
+// ------------------------------------------------------------------ Bessel J_k (Miller)
+std::vector<double> bessel_j(int kmax, double z) {
+  std::vector<double> J(kmax + 1, 0.0);
+  if (z == 0.0) {
+    J[0] = 1.0;
+    return J;
+  }
+  const double az = std::fabs(z);
+  const int start = std::max(kmax, (int)az) + 60 + (int)(2.0 * std::sqrt(az + 1.0) * 10.0);
+  std::vector<double> w(start + 2, 0.0);
+  w[start + 1] = 0.0;
+  w[start] = 1e-300;
+  for (int k = start; k >= 1; --k) {
+    w[k - 1] = 2.0 * k / az * w[k] - w[k + 1];
+    if (std::fabs(w[k - 1]) > 1e250) {
+      for (int j = k - 1; j <= start + 1; ++j) w[j] *= 1e-250;
+    }
+  }
+  double norm = w[0];
+  for (int k = 2; k <= start; k += 2) norm += 2.0 * w[k];
+  for (int k = 0; k <= kmax; ++k) {
+    double v = w[k] / norm;
+    if (z < 0.0 && (k & 1)) v = -v;
+    J[k] = v;
+  }
+  return J;
+}
+
+int chebyshev_order(double z, double tol) {
+  const int kmax = (int)std::fabs(z) + 400;
+  auto J = bessel_j(kmax, z);
+  for (int k = (int)std::floor(std::fabs(z)) + 1; k <= kmax; ++k)
+    if (std::fabs(J[k]) < tol) return k - 1;
+  return kmax;
+}
+
+}  // namespace
+
+// =================================================================== context
+
+struct tddft_ctx {
+  // configuration
+  int prec = 0, proj_mode = 0, N = 0;
+  size_t N3 = 0;
+  double L[3] = {0, 0, 0}, omega = 0, dV = 0;
+  int natoms = 0, lmax = 0, nlm = 0;
+  std::vector<double> pos, Zat, rcat;
+  double r_cut = 0;
+  int nk = 0, nb = 0, nkb = 0;
+  std::vector<double> kpts, kw, occ, wf;
+  double dt = 0;
+  int exp_kind = 0, exp_order = 0, n_sc = 0, xc = 1;
+  double cheb_tol = 0, sc_tol = 0, emin_user = 0, emax_user = 0;
+  std::vector<double> ft, fA, fB;
+  // propagation state
+  bool have_states = false;
+  double t = 0, emin = 0, emax = 0, nl_bound = 0, kin_max = 0;
+  int K_full = 0, K_half = 0;
+  std::vector<cd> cf_full, cf_half;
+  // device memory
+  cudaStream_t st = nullptr;
+  std::vector<void*> allocs;
+  void *psi = nullptr, *phi = nullptr, *pred = nullptr, *Ta = nullptr, *Tb = nullptr, *tmp = nullptr;
+  void *cbuf = nullptr, *dcbuf = nullptr, *tw = nullptr;
+  double2 *tw64 = nullptr, *hart = nullptr, *stage = nullptr;
+  size_t stage_elems = 0;
+  double *rho = nullptr, *rho2 = nullptr, *rho3 = nullptr, *V = nullptr, *Vnew = nullptr, *vloc = nullptr,
+         *vH = nullptr, *exc = nullptr, *vxc4 = nullptr, *wf_d = nullptr, *red = nullptr, *Bd = nullptr;
+  float *Vf = nullptr, *Vnewf = nullptr;
+  int* flag = nullptr;
+  // projector tables (typed views over the raw allocations)
+  int *g_ptr = nullptr, *g_idx = nullptr, *s_ptr = nullptr, *s_atom = nullptr;
+  size_t n_entries = 0;
+  void *g_tab = nullptr, *s_tab = nullptr, *Dmat = nullptr;
+  // bookkeeping
+  std::string err;
+  long long launches = 0;
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[kNumCls];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
+  double alg_bytes[kNumCls] = {0, 0, 0, 0, 0, 0, 0, 0};  // algorithmic DRAM bytes while profiling
+
+  size_t psi_elems() const { return (size_t)nkb * 2 * N3; }
+  size_t rsize() const { return prec == TDDFT_FP64 ? sizeof(double) : sizeof(float); }
+
+  template <typename R> ProjTables<R> tables() const {
+    ProjTables<R> p;
+    p.natoms = natoms;
+    p.nlm = nlm;
+    p.ntab = 3 + nlm;
+    p.g_ptr = g_ptr;
+    p.g_idx = g_idx;
+    p.g_tab = (const R*)g_tab;
+    p.s_ptr = s_ptr;
+    p.s_atom = s_atom;
+    p.s_tab = (const R*)s_tab;
+    p.Dmat = (const R*)Dmat;
+    return p;
+  }
+
+  tddft_status fail(tddft_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  tddft_status cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return TDDFT_OK;
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TDDFT_ERR_OOM : TDDFT_ERR_CUDA;
+  }
+  template <typename T> tddft_status alloc(T** p, size_t bytes, const char* what) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      err = std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e);
+      return TDDFT_ERR_OOM;
+    }
+    allocs.push_back(q);
+    *p = (T*)q;
+    return TDDFT_OK;
+  }
+  // Launch wrapper: counts launches and records CUDA events around them when profiling.
+  template <class F> tddft_status launch(int cls, const char* what, F&& f, double bytes = 0.0) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (prof) {
+      if (ev_used == ev_pool.size()) {
+        cudaEvent_t x, y;
+        cudaEventCreate(&x);
+        cudaEventCreate(&y);
+        ev_pool.push_back({x, y});
+      }
+      a = ev_pool[ev_used].first;
+      b = ev_pool[ev_used].second;
+      ++ev_used;
+      cudaEventRecord(a, st);
+    }
+    cudaError_t e = f();
+    if (prof) {
+      cudaEventRecord(b, st);
+      ev[cls].push_back({a, b});
+      alg_bytes[cls] += bytes;
+    }
+    ++launches;
+    return cuda(e, what);
+  }
+  void field_at(double tt, double A[3], double B[3]) const {
+    for (int a = 0; a < 3; ++a) A[a] = B[a] = 0.0;
+    const int nt = (int)ft.size();
+    if (nt == 0) return;
+    if (tt <= ft[0] || nt == 1) {
+      for (int a = 0; a < 3; ++a) { A[a] = fA[a]; B[a] = fB[a]; }
+      return;
+    }
+    if (tt >= ft[nt - 1]) {
+      for (int a = 0; a < 3; ++a) { A[a] = fA[3 * (nt - 1) + a]; B[a] = fB[3 * (nt - 1) + a]; }
+      return;
+    }
+    const int j = (int)(std::upper_bound(ft.begin(), ft.end(), tt) - ft.begin());
+    const double t0 = ft[j - 1], t1 = ft[j];
+    const double w = (tt - t0) / (t1 - t0);
+    for (int a = 0; a < 3; ++a) {
+      A[a] = (1.0 - w) * fA[3 * (j - 1) + a] + w * fA[3 * j + a];
+      B[a] = (1.0 - w) * fB[3 * (j - 1) + a] + w * fB[3 * j + a];
+    }
+  }
+  double kinetic_max_for(const double s[3]) const {
+    const double pi = 3.14159265358979323846;
+    double tot = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double g = 2.0 * pi / L[a];
+      const double lo = g * (-(N / 2)) + s[a], hi = g * (N / 2 - 1) + s[a];
+      tot += std::max(lo * lo, hi * hi);
+    }
+    return 0.5 * tot;
+  }
+};
+
+namespace {
+
+tddft_status free_all(tddft_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  for (auto& e : c->ev_pool) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  c->ev_pool.clear();
+  return TDDFT_OK;
+}
+
+bool supported_n(int n) {
+  static const int ok[] = {8, 12, 16, 24, 32, 48, 64, 96};
+  for (int v : ok)
+    if (v == n) return true;
+  return false;
+}
+
+// ------------------------------------------------------------------ projector tables
+struct HostTables {
+  std::vector<int> g_ptr, g_idx, s_ptr, s_atom;
+  std::vector<double> g_tab, s_tab;  // [entries][3 + nlm]
+  std::vector<double> Dmat;          // [natoms][2nlm][2nlm][2]
+  double nl_bound = 0.0;
+};
+
+tddft_status build_tables(tddft_ctx* c, const tddft_projectors* pj, const int* species, HostTables& ht) {
+  const int N = c->N, nlm = c->nlm, tab = 3 + nlm;
+  const double pi = 3.14159265358979323846;
+  std::vector<std::vector<Poly>> S(c->lmax + 1);
+  for (int l = 0; l <= c->lmax; ++l) S[l] = solid_harmonics(l);
+  ht.g_ptr.assign(c->natoms + 1, 0);
+  std::vector<std::vector<double>> per_atom_tab(c->natoms);
+  std::vector<std::vector<int>> per_atom_idx(c->natoms);
+  const double h[3] = {c->L[0] / N, c->L[1] / N, c->L[2] / N};
+  for (int a = 0; a < c->natoms; ++a) {
+    const int s = species[a];
+    const double w = pj->width[s];
+    double Nl[3];
+    for (int l = 0; l <= c->lmax; ++l) Nl[l] = std::sqrt(2.0 / (std::tgamma(l + 1.5) * std::pow(w, 2 * l + 3)));
+    const double* R = &c->pos[3 * a];
+    std::vector<double> dz(N), dy(N), dx(N);
+    for (int i = 0; i < N; ++i) {
+      double v;
+      v = i * h[0] - R[0]; dx[i] = v - c->L[0] * std::nearbyint(v / c->L[0]);
+      v = i * h[1] - R[1]; dy[i] = v - c->L[1] * std::nearbyint(v / c->L[1]);
+      v = i * h[2] - R[2]; dz[i] = v - c->L[2] * std::nearbyint(v / c->L[2]);
+    }
+    // the cut |d| < r_cut is applied with a 1e-10 relative margin so that points lying on the
+    // sphere in exact arithmetic are excluded whatever the rounding of |d|^2
+    const double rc2 = c->r_cut * c->r_cut * (1.0 - 1e-10);
+    for (int z = 0; z < N; ++z) {
+      if (dz[z] * dz[z] >= rc2) continue;
+      for (int y = 0; y < N; ++y) {
+        if (dz[z] * dz[z] + dy[y] * dy[y] >= rc2) continue;
+        for (int x = 0; x < N; ++x) {
+          const double r2 = dx[x] * dx[x] + dy[y] * dy[y] + dz[z] * dz[z];
+          if (!(r2 < rc2)) continue;
+          per_atom_idx[a].push_back((z * N + y) * N + x);
+          per_atom_tab[a].push_back(dx[x]);
+          per_atom_tab[a].push_back(dy[y]);
+          per_atom_tab[a].push_back(dz[z]);
+          const double g = std::exp(-r2 / (2.0 * w * w));
+          for (int l = 0; l <= c->lmax; ++l)
+            for (int mu = 0; mu < 2 * l + 1; ++mu)
+              per_atom_tab[a].push_back(Nl[l] * g * poly_eval(S[l][mu], dx[x], dy[y], dz[z]));
+        }
+      }
+    }
+    ht.g_ptr[a + 1] = ht.g_ptr[a] + (int)per_atom_idx[a].size();
+  }
+  for (int a = 0; a < c->natoms; ++a) {
+    ht.g_idx.insert(ht.g_idx.end(), per_atom_idx[a].begin(), per_atom_idx[a].end());
+    ht.g_tab.insert(ht.g_tab.end(), per_atom_tab[a].begin(), per_atom_tab[a].end());
+  }
+  // scatter order: counting sort by grid point, atoms ascending
+  const size_t N3 = c->N3;
+  const size_t ne = ht.g_idx.size();
+  ht.s_ptr.assign(N3 + 1, 0);
+  for (size_t e = 0; e < ne; ++e) ht.s_ptr[ht.g_idx[e] + 1]++;
+  for (size_t i = 0; i < N3; ++i) ht.s_ptr[i + 1] += ht.s_ptr[i];
+  ht.s_atom.assign(ne, 0);
+  ht.s_tab.assign(ne * tab, 0.0);
+  std::vector<int> fill(ht.s_ptr.begin(), ht.s_ptr.end() - 1);
+  for (int a = 0; a < c->natoms; ++a)
+    for (int e = ht.g_ptr[a]; e < ht.g_ptr[a + 1]; ++e) {
+      const int dst = fill[ht.g_idx[e]]++;
+      ht.s_atom[dst] = a;
+      std::memcpy(&ht.s_tab[(size_t)dst * tab], &ht.g_tab[(size_t)e * tab], sizeof(double) * tab);
+    }
+  // coupling blocks D_l I + lambda_l L.S on (p = l^2 + mu + l, sigma), index 2 p + sigma
+  const int M = 2 * nlm;
+  ht.Dmat.assign((size_t)c->natoms * M * M * 2, 0.0);
+  const cd sig[3][2][2] = {{{0.0, 1.0}, {1.0, 0.0}},
+                           {{0.0, cd(0.0, -1.0)}, {cd(0.0, 1.0), 0.0}},
+                           {{1.0, 0.0}, {0.0, -1.0}}};
+  std::vector<std::vector<std::vector<cd>>> Lm[3];
+  for (int al = 0; al < 3; ++al)
+    for (int l = 0; l <= c->lmax; ++l) Lm[al].push_back(angular_momentum(l, al));
+  double bound = 0.0;
+  for (int a = 0; a < c->natoms; ++a) {
+    const int s = species[a];
+    double* Da = &ht.Dmat[(size_t)a * M * M * 2];
+    double dmax = 0.0;
+    for (int l = 0; l <= c->lmax; ++l) {
+      const double Dl = pj->D[s * (c->lmax + 1) + l], lam = pj->lambda_so[s * (c->lmax + 1) + l];
+      dmax = std::max(dmax, std::fabs(Dl + lam * 0.5 * l));
+      if (l > 0) dmax = std::max(dmax, std::fabs(Dl - lam * 0.5 * (l + 1)));
+      const int p0 = l * l, nl = 2 * l + 1;
+      for (int mu = 0; mu < nl; ++mu)
+        for (int nu = 0; nu < nl; ++nu)
+          for (int s1 = 0; s1 < 2; ++s1)
+            for (int s2 = 0; s2 < 2; ++s2) {
+              cd v = (mu == nu && s1 == s2) ? cd(Dl, 0.0) : cd(0.0, 0.0);
+              for (int al = 0; al < 3; ++al) v += lam * Lm[al][l][mu][nu] * 0.5 * sig[al][s1][s2];
+              const int row = 2 * (p0 + mu) + s1, col = 2 * (p0 + nu) + s2;
+              Da[(row * M + col) * 2] = v.real();
+              Da[(row * M + col) * 2 + 1] = v.imag();
+            }
+    }
+    // Gershgorin bound of the projector Gram matrix of this atom
+    std::vector<double> G((size_t)nlm * nlm, 0.0);
+    for (int e = ht.g_ptr[a]; e < ht.g_ptr[a + 1]; ++e) {
+      const double* t = &ht.g_tab[(size_t)e * tab + 3];
+      for (int p = 0; p < nlm; ++p)
+        for (int q = 0; q < nlm; ++q) G[p * nlm + q] += t[p] * t[q] * c->dV;
+    }
+    double gmax = 0.0;
+    for (int p = 0; p < nlm; ++p) {
+      double rs = 0.0;
+      for (int q = 0; q < nlm; ++q) rs += std::fabs(G[p * nlm + q]);
+      gmax = std::max(gmax, rs);
+    }
+    bound += dmax * gmax;
+  }
+  ht.nl_bound = bound;
+  (void)pi;
+  return TDDFT_OK;
+}
+
+template <typename R>
+tddft_status upload_typed(tddft_ctx* c, void** dst, const std::vector<double>& src, const char* what) {
+  std::vector<R> tmp(src.begin(), src.end());
+  tddft_status s = c->alloc(dst, tmp.size() * sizeof(R), what);
+  if (s) return s;
+  return c->cuda(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice), what);
+}
+
+template <typename T>
+tddft_status upload(tddft_ctx* c, T** dst, const std::vector<T>& src, const char* what) {
+  tddft_status s = c->alloc(dst, src.size() * sizeof(T), what);
+  if (s) return s;
+  return c->cuda(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+}
+
+// ------------------------------------------------------------------ potential pipeline
+tddft_status hartree(tddft_ctx* c, const double* rho) {
+  ZParams zp{};
+  const double pi = 3.14159265358979323846;
+  for (int a = 0; a < 3; ++a) zp.gs[a] = 2.0 * pi / c->L[a];
+  zp.scale = 1.0 / (double)c->N3;
+  tddft_status s;
+  if ((s = c->launch(KC_POT, "density to complex", [&] { return launch_density_to_complex(c->st, c->N3, rho, c->hart); }))) return s;
+  if ((s = c->launch(KC_POT, "hartree fft xy", [&] { return launch_fft_xy<double>(c->st, c->N, c->hart, c->hart, 1, c->tw64, false); }))) return s;
+  if ((s = c->launch(KC_POT, "hartree fft z", [&] { return launch_fft_z<double>(c->st, c->N, c->hart, 1, c->tw64, Z_POISSON, zp); }))) return s;
+  if ((s = c->launch(KC_POT, "hartree ifft xy", [&] { return launch_fft_xy<double>(c->st, c->N, c->hart, c->hart, 1, c->tw64, true); }))) return s;
+  return c->launch(KC_POT, "hartree real part", [&] { return launch_complex_real_part(c->st, c->N3, c->hart, c->vH, 1.0); });
+}
+
+// rho (4 x N3) -> V (FP64) and, in mixed precision, its FP32 copy.
+tddft_status potential(tddft_ctx* c, const double* rho, double tt, double* Vout, float* Vfout) {
+  double A[3], B[3];
+  c->field_at(tt, A, B);
+  tddft_status s = hartree(c, rho);
+  if (s) return s;
+  return c->launch(KC_POT, "potential", [&] {
+    return launch_potential(c->st, c->N3, rho, c->vH, c->vloc, B, c->xc, Vout, Vfout, c->exc, c->vxc4);
+  });
+}
+
+template <typename R> tddft_status density(tddft_ctx* c, const void* psi, double* rho) {
+  const double by = (double)c->psi_elems() * 2 * sizeof(R) + 4.0 * c->N3 * sizeof(double);
+  return c->launch(KC_DENS, "density", [&] { return launch_density<R>(c->st, c->N3, psi, c->nkb, c->wf_d, rho); }, by);
+}
+
+tddft_status window_check(tddft_ctx* c, const double* V) {
+  return c->launch(KC_OTHER, "window check", [&] {
+    return launch_check_window(c->st, c->N3, V, c->emin, c->emax, c->kin_max, c->nl_bound, c->flag);
+  });
+}
+
+template <typename R> const R* vsel(tddft_ctx* c, bool cur) {
+  if (c->prec == TDDFT_FP64) return (const R*)(cur ? c->V : c->Vnew);
+  return (const R*)(cur ? (void*)c->Vf : (void*)c->Vnewf);
+}
+
+void fill_shifts(tddft_ctx* c, const double A[3], double (*shift)[3]) {
+  for (int k = 0; k < c->nk; ++k)
+    for (int a = 0; a < 3; ++a) shift[k][a] = c->kpts[3 * k + a] + A[a];
+}
+
+// Kinetic part of H on all spinors: out = T in (three FFT passes).
+template <typename R> tddft_status kinetic(tddft_ctx* c, const void* in, void* out, const double A[3]) {
+  ZParams zp{};
+  const double pi = 3.14159265358979323846;
+  for (int a = 0; a < 3; ++a) zp.gs[a] = 2.0 * pi / c->L[a];
+  zp.scale = 1.0 / (double)c->N3;
+  zp.comps_per_k = 2 * c->nb;
+  fill_shifts(c, A, zp.shift);
+  const int nbatch = 2 * c->nkb;
+  const double by = 2.0 * nbatch * (double)c->N3 * 2 * sizeof(R);
+  tddft_status s;
+  if ((s = c->launch(KC_FFT_XY, "fft xy", [&] { return launch_fft_xy<R>(c->st, c->N, in, out, nbatch, c->tw, false); }, by))) return s;
+  if ((s = c->launch(KC_FFT_Z, "fft z", [&] { return launch_fft_z<R>(c->st, c->N, out, nbatch, c->tw, Z_KIN, zp); }, by))) return s;
+  return c->launch(KC_FFT_XY, "ifft xy", [&] { return launch_fft_xy<R>(c->st, c->N, out, out, nbatch, c->tw, true); }, by);
+}
+
+template <typename R> tddft_status gather(tddft_ctx* c, const void* in, const double A[3]) {
+  if (c->natoms == 0) return TDDFT_OK;
+  EpiParams ep{};
+  ep.nstates = c->nb;
+  fill_shifts(c, A, ep.shift);
+  ProjTables<R> pt = c->tables<R>();
+  const double by = (double)c->n_entries * c->nkb * 2 * 2 * sizeof(R);  // psi at the sphere points
+  return c->launch(KC_PROJ, "projector gather", [&] {
+    return launch_proj_gather<R>(c->st, c->N, in, c->nkb, pt, c->dV, ep, c->cbuf, c->dcbuf);
+  }, by);
+}
+
+// One Chebyshev series: T_k of H~ = (H - c)/Delta applied to `in`, accumulated with
+// coefficients cf1 (orders 0..K1) into acc1 and, when acc2 is set, cf2 (0..K2) into acc2.
+template <typename R>
+tddft_status cheb_series(tddft_ctx* c, const void* in, bool vcur, const double A[3], void* acc1,
+                         const std::vector<cd>& cf1, int K1, void* acc2, const std::vector<cd>& cf2, int K2) {
+  const int K = std::max(K1, acc2 ? K2 : 0);
+  EpiParams ep{};
+  ep.c = 0.5 * (c->emax + c->emin);
+  ep.inv_delta = 1.0 / (0.5 * (c->emax - c->emin));
+  ep.nstates = c->nb;
+  fill_shifts(c, A, ep.shift);
+  ProjTables<R> pt = c->tables<R>();
+  const R* Vr = vsel<R>(c, vcur);
+  const void* prev = in;
+  const void* cur = in;
+  tddft_status s;
+  for (int k = 0; k < K; ++k) {
+    if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
+    if ((s = gather<R>(c, cur, A))) return s;
+    void* out;
+    if (k == 0) out = c->Ta;
+    else if (prev == in) out = (cur == c->Ta) ? c->Tb : c->Ta;
+    else out = const_cast<void*>(prev);
+    ep.mode = (k == 0) ? EPI_FIRST : EPI_RECUR;
+    ep.use_acc1 = (k + 1 <= K1);
+    ep.use_acc2 = (acc2 != nullptr && k + 1 <= K2);
+    if (ep.use_acc1) {
+      ep.a0[0] = cf1[0].real(); ep.a0[1] = cf1[0].imag();
+      ep.a1[0] = cf1[k + 1].real(); ep.a1[1] = cf1[k + 1].imag();
+    }
+    if (ep.use_acc2) {
+      ep.b0[0] = cf2[0].real(); ep.b0[1] = cf2[0].imag();
+      ep.b1[0] = cf2[k + 1].real(); ep.b1[1] = cf2[k + 1].imag();
+    }
+    const void* tkm1 = (k == 0) ? nullptr : prev;
+    const int nacc = ep.use_acc1 + ep.use_acc2;
+    const double streams = 3.0 + (k == 0 ? 0.0 : 1.0) + nacc * (k == 0 ? 1.0 : 2.0);
+    const double by = streams * c->psi_elems() * 2 * sizeof(R) + 4.0 * c->N3 * sizeof(R);
+    if ((s = c->launch(KC_EPI, "chebyshev epilogue", [&] {
+           return launch_epilogue<R>(c->st, c->N, c->tmp, cur, tkm1, out, acc1, acc2, Vr, pt, c->dcbuf, c->nkb, ep);
+         }, by)))
+      return s;
+    prev = cur;
+    cur = out;
+  }
+  return TDDFT_OK;
+}
+
+// Taylor series: acc = sum_{k <= K} (-i tau H)^k / k! in.
+template <typename R>
+tddft_status taylor_series(tddft_ctx* c, const void* in, bool vcur, const double A[3], double tau, int K, void* acc) {
+  tddft_status s = c->cuda(cudaMemcpyAsync(acc, in, c->psi_elems() * 2 * sizeof(R), cudaMemcpyDeviceToDevice, c->st),
+                           "taylor init");
+  if (s) return s;
+  EpiParams ep{};
+  ep.nstates = c->nb;
+  fill_shifts(c, A, ep.shift);
+  ep.mode = EPI_TAYLOR;
+  ep.use_acc1 = 1;
+  ProjTables<R> pt = c->tables<R>();
+  const R* Vr = vsel<R>(c, vcur);
+  const void* cur = in;
+  for (int k = 1; k <= K; ++k) {
+    if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
+    if ((s = gather<R>(c, cur, A))) return s;
+    void* out = (cur == c->Ta) ? c->Tb : c->Ta;
+    ep.a1[0] = 0.0;
+    ep.a1[1] = -tau / k;
+    if ((s = c->launch(KC_EPI, "taylor epilogue", [&] {
+           return launch_epilogue<R>(c->st, c->N, c->tmp, cur, nullptr, out, acc, nullptr, Vr, pt, c->dcbuf, c->nkb, ep);
+         })))
+      return s;
+    cur = out;
+  }
+  return TDDFT_OK;
+}
+
+template <typename R> tddft_status one_step(tddft_ctx* c) {
+  const double t0 = c->t, t1 = c->t + c->dt;
+  double A0[3], B0[3], A1[3], B1[3];
+  c->field_at(t0, A0, B0);
+  c->field_at(t1, A1, B1);
+  float* Vnf = c->prec == TDDFT_FP64 ? nullptr : c->Vnewf;
+  float* Vcf = c->prec == TDDFT_FP64 ? nullptr : c->Vf;
+  tddft_status s;
+  if (c->exp_kind == TDDFT_EXP_CHEBYSHEV) {
+    if ((s = cheb_series<R>(c, c->psi, true, A0, c->pred, c->cf_full, c->K_full, c->phi, c->cf_half, c->K_half))) return s;
+  } else {
+    if ((s = taylor_series<R>(c, c->psi, true, A0, c->dt, c->K_full, c->pred))) return s;
+    if ((s = taylor_series<R>(c, c->psi, true, A0, 0.5 * c->dt, c->K_half, c->phi))) return s;
+  }
+  if ((s = density<R>(c, c->pred, c->rho2))) return s;
+  if ((s = potential(c, c->rho2, t1, c->Vnew, Vnf))) return s;
+  if ((s = window_check(c, c->Vnew))) return s;
+  auto half = [&]() -> tddft_status {
+    if (c->exp_kind == TDDFT_EXP_CHEBYSHEV)
+      return cheb_series<R>(c, c->phi, false, A1, c->psi, c->cf_half, c->K_half, nullptr, c->cf_half, 0);
+    return taylor_series<R>(c, c->phi, false, A1, 0.5 * c->dt, c->K_half, c->psi);
+  };
+  if ((s = half())) return s;
+  double* rprev = c->rho2;
+  double* rnext = c->rho3;
+  for (int it = 0; it < c->n_sc; ++it) {
+    if ((s = density<R>(c, c->psi, rnext))) return s;
+    if (c->sc_tol > 0.0) {
+      if ((s = c->launch(KC_OTHER, "sc diff", [&] { return launch_max_abs_diff(c->st, 4 * c->N3, rnext, rprev, c->red); })))
+        return s;
+      double d = 0.0;
+      if ((s = c->cuda(cudaMemcpyAsync(&d, c->red, sizeof(double), cudaMemcpyDeviceToHost, c->st), "sc read"))) return s;
+      if ((s = c->cuda(cudaStreamSynchronize(c->st), "sc sync"))) return s;
+      if (d < c->sc_tol) break;
+    }
+    if ((s = potential(c, rnext, t1, c->Vnew, Vnf))) return s;
+    if ((s = window_check(c, c->Vnew))) return s;
+    if ((s = half())) return s;
+    std::swap(rprev, rnext);
+  }
+  if ((s = density<R>(c, c->psi, c->rho))) return s;
+  if ((s = potential(c, c->rho, t1, c->V, Vcf))) return s;
+  if ((s = window_check(c, c->V))) return s;
+  c->t = t1;
+  return TDDFT_OK;
+}
+
+void set_orders(tddft_ctx* c) {
+  const double dlt = 0.5 * (c->emax - c->emin);
+  const double cc = 0.5 * (c->emax + c->emin);
+  if (c->exp_kind == TDDFT_EXP_CHEBYSHEV) {
+    double tol = c->cheb_tol > 0 ? c->cheb_tol : (c->prec == TDDFT_FP64 ? 1e-16 : 1e-9);
+    if (c->exp_order > 0) {
+      c->K_full = c->K_half = c->exp_order;
+    } else {
+      c->K_full = chebyshev_order(c->dt * dlt, tol);
+      c->K_half = chebyshev_order(0.5 * c->dt * dlt, tol);
+    }
+    auto coefs = [&](double tau, int K) {
+      std::vector<cd> a(K + 1);
+      auto J = bessel_j(K, tau * dlt);
+      const cd ph = std::exp(cd(0.0, -tau * cc));
+      cd mi(1.0, 0.0);
+      for (int k = 0; k <= K; ++k) {
+        a[k] = (k == 0 ? 1.0 : 2.0) * mi * J[k] * ph;
+        mi *= cd(0.0, -1.0);
+      }
+      return a;
+    };
+    c->cf_full = coefs(c->dt, c->K_full);
+    c->cf_half = coefs(0.5 * c->dt, c->K_half);
+  } else {
+    c->K_full = c->K_half = c->exp_order > 0 ? c->exp_order : 4;
+  }
+}
+
+template <typename R> tddft_status do_set_states(tddft_ctx* c, const void* psi, int on_device, double t0) {
+  const size_t n = c->psi_elems();
+  tddft_status s;
+  if (c->prec == TDDFT_FP64) {
+    if ((s = c->cuda(cudaMemcpyAsync(c->psi, psi, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st), "set_states copy"))) return s;
+  } else if (on_device) {
+    if ((s = c->launch(KC_OTHER, "convert in", [&] { return launch_convert_in<R>(c->st, n, (const double2*)psi, c->psi); }))) return s;
+  } else {
+    for (size_t off = 0; off < n; off += c->stage_elems) {
+      const size_t m = std::min(c->stage_elems, n - off);
+      if ((s = c->cuda(cudaMemcpyAsync(c->stage, (const double2*)psi + off, m * sizeof(double2), cudaMemcpyHostToDevice, c->st), "set_states stage"))) return s;
+      if ((s = c->launch(KC_OTHER, "convert in", [&] { return launch_convert_in<R>(c->st, m, c->stage, (float2*)c->psi + off); }))) return s;
+    }
+  }
+  c->t = t0;
+  if ((s = density<R>(c, c->psi, c->rho))) return s;
+  float* Vcf = c->prec == TDDFT_FP64 ? nullptr : c->Vf;
+  if ((s = potential(c, c->rho, t0, c->V, Vcf))) return s;
+  // spectral window (reading: extrema of the potential, kinetic maximum, projector bound, 5 % margin)
+  double Atab[3], Btab[3];
+  c->kin_max = 0.0;
+  if (c->ft.empty()) {
+    Atab[0] = Atab[1] = Atab[2] = 0.0;
+    for (int k = 0; k < c->nk; ++k) c->kin_max = std::max(c->kin_max, c->kinetic_max_for(&c->kpts[3 * k]));
+  } else {
+    for (size_t j = 0; j < c->ft.size(); ++j)
+      for (int k = 0; k < c->nk; ++k) {
+        double sft[3];
+        for (int a = 0; a < 3; ++a) sft[a] = c->kpts[3 * k + a] + c->fA[3 * j + a];
+        c->kin_max = std::max(c->kin_max, c->kinetic_max_for(sft));
+      }
+  }
+  (void)Atab; (void)Btab;
+  if (c->emin_user == 0.0 && c->emax_user == 0.0) {
+    std::vector<double> Vh(4 * c->N3);
+    if ((s = c->cuda(cudaMemcpyAsync(Vh.data(), c->V, Vh.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st), "window read"))) return s;
+    if ((s = c->cuda(cudaStreamSynchronize(c->st), "window sync"))) return s;
+    double vmin = 1e300, vmax = -1e300, bmax = 0.0;
+    const size_t N3 = c->N3;
+    for (size_t r = 0; r < N3; ++r) {
+      const double v = 0.5 * (Vh[r] + Vh[N3 + r]);
+      const double bz = 0.5 * (Vh[r] - Vh[N3 + r]), bx = 0.5 * Vh[2 * N3 + r], by = 0.5 * Vh[3 * N3 + r];
+      vmin = std::min(vmin, v);
+      vmax = std::max(vmax, v);
+      bmax = std::max(bmax, std::sqrt(bx * bx + by * by + bz * bz));
+    }
+    double emin = vmin - bmax - c->nl_bound, emax = vmax + bmax + c->kin_max + c->nl_bound;
+    const double w = emax - emin;
+    c->emin = emin - 0.025 * w;
+    c->emax = emax + 0.025 * w;
+  } else {
+    c->emin = c->emin_user;
+    c->emax = c->emax_user;
+  }
+  set_orders(c);
+  if ((s = c->cuda(cudaMemsetAsync(c->flag, 0, sizeof(int), c->st), "flag reset"))) return s;
+  if ((s = window_check(c, c->V))) return s;
+  c->have_states = true;
+  return TDDFT_OK;
+}
+
+template <typename R> tddft_status do_get_states(tddft_ctx* c, void* out, int on_device) {
+  const size_t n = c->psi_elems();
+  tddft_status s;
+  if (c->prec == TDDFT_FP64) {
+    if ((s = c->cuda(cudaMemcpyAsync(out, c->psi, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st), "get_states copy"))) return s;
+  } else if (on_device) {
+    if ((s = c->launch(KC_OTHER, "convert out", [&] { return launch_convert_out<R>(c->st, n, c->psi, (double2*)out); }))) return s;
+  } else {
+    for (size_t off = 0; off < n; off += c->stage_elems) {
+      const size_t m = std::min(c->stage_elems, n - off);
+      if ((s = c->launch(KC_OTHER, "convert out", [&] { return launch_convert_out<R>(c->st, m, (const float2*)c->psi + off, c->stage); }))) return s;
+      if ((s = c->cuda(cudaMemcpyAsync((double2*)out + off, c->stage, m * sizeof(double2), cudaMemcpyDeviceToHost, c->st), "get_states stage"))) return s;
+      if ((s = c->cuda(cudaStreamSynchronize(c->st), "get_states sync"))) return s;
+    }
+  }
+  return c->cuda(cudaStreamSynchronize(c->st), "get_states sync");
+}
+
+template <typename R> tddft_status do_observables(tddft_ctx* c, double* n, double* m, double* E, double* M, double* norms) {
+  tddft_status s;
+  double A[3], B[3];
+  c->field_at(c->t, A, B);
+  const int nkb = c->nkb;
+  double* dots = c->red + 16;  // [nkb][2] then [nkb][2] then [nkb]
+  double* kdots = dots + 2 * nkb;
+  double* nle = kdots + 2 * nkb;
+  if ((s = c->launch(KC_OTHER, "norms", [&] { return launch_band_dot<R>(c->st, 2 * c->N3, nkb, c->psi, c->psi, dots); }))) return s;
+  if ((s = kinetic<R>(c, c->psi, c->tmp, A))) return s;
+  if ((s = c->launch(KC_OTHER, "kinetic dot", [&] { return launch_band_dot<R>(c->st, 2 * c->N3, nkb, c->psi, c->tmp, kdots); }))) return s;
+  if (c->natoms > 0) {
+    if ((s = gather<R>(c, c->psi, A))) return s;
+    if ((s = c->launch(KC_OTHER, "nl energy", [&] { return launch_nl_energy<R>(c->st, nkb, c->natoms * 2 * c->nlm, c->cbuf, c->dcbuf, nle); }))) return s;
+  }
+  if ((s = c->launch(KC_OTHER, "field sums", [&] {
+         return launch_field_sums(c->st, c->N3, c->rho, c->vloc, c->vH, c->exc, c->vxc4, c->V, B, c->red);
+       })))
+    return s;
+  std::vector<double> h(16 + 5 * nkb, 0.0);
+  int flag = 0;
+  if ((s = c->cuda(cudaMemcpyAsync(h.data(), c->red, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st), "obs read"))) return s;
+  if ((s = c->cuda(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "flag read"))) return s;
+  std::vector<double> rho_h;
+  if (n || m) {
+    rho_h.resize(4 * c->N3);
+    if ((s = c->cuda(cudaMemcpyAsync(rho_h.data(), c->rho, rho_h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st), "rho read"))) return s;
+  }
+  if ((s = c->cuda(cudaStreamSynchronize(c->st), "obs sync"))) return s;
+  double ekin = 0, enl = 0;
+  bool bad = h[9] != 0.0;
+  for (int kb = 0; kb < nkb; ++kb) {
+    const double w = c->wf[kb];
+    const double nr = h[16 + 2 * kb] * c->dV;
+    if (norms) norms[kb] = nr;
+    if (!std::isfinite(nr)) bad = true;
+    ekin += w * h[16 + 2 * nkb + 2 * kb] * c->dV;
+    if (c->natoms > 0) enl += w * h[16 + 4 * nkb + kb];
+  }
+  if (E) {
+    E[TDDFT_E_KIN] = ekin;
+    E[TDDFT_E_NL] = enl;
+    E[TDDFT_E_LOC] = h[0] * c->dV;
+    E[TDDFT_E_H] = 0.5 * h[1] * c->dV;
+    E[TDDFT_E_XC] = h[2] * c->dV;
+    E[TDDFT_E_Z] = 0.5 * h[7] * c->dV;
+    E[TDDFT_E_TOTAL] = E[0] + E[1] + E[2] + E[3] + E[4] + E[5];
+    E[TDDFT_E_TIME] = c->t;
+    E[TDDFT_E_XC_POT] = h[8] * c->dV;
+    E[TDDFT_E_NELEC] = h[6] * c->dV;
+  }
+  if (M)
+    for (int a = 0; a < 3; ++a) M[a] = h[3 + a] * c->dV;
+  const size_t N3 = c->N3;
+  if (n)
+    for (size_t r = 0; r < N3; ++r) n[r] = rho_h[r] + rho_h[N3 + r];
+  if (m)
+    for (size_t r = 0; r < N3; ++r) {
+      m[r] = 2.0 * rho_h[2 * N3 + r];
+      m[N3 + r] = -2.0 * rho_h[3 * N3 + r];
+      m[2 * N3 + r] = rho_h[r] - rho_h[N3 + r];
+    }
+  if (bad) return c->fail(TDDFT_ERR_DIVERGED, "non-finite density or norm");
+  if (flag) return c->fail(TDDFT_ERR_BOUND, "potential left the Chebyshev spectral window");
+  return TDDFT_OK;
+}
+
+template <typename R> tddft_status do_apply_h(tddft_ctx* c, const void* in, void* out, int on_device) {
+  const size_t n = c->psi_elems();
+  tddft_status s;
+  double A[3], B[3];
+  c->field_at(c->t, A, B);
+  // stage the input into Ta (precision R)
+  if (c->prec == TDDFT_FP64) {
+    if ((s = c->cuda(cudaMemcpyAsync(c->Ta, in, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st), "apply_h in"))) return s;
+  } else if (on_device) {
+    if ((s = c->launch(KC_OTHER, "convert in", [&] { return launch_convert_in<R>(c->st, n, (const double2*)in, c->Ta); }))) return s;
+  } else {
+    for (size_t off = 0; off < n; off += c->stage_elems) {
+      const size_t mm = std::min(c->stage_elems, n - off);
+      if ((s = c->cuda(cudaMemcpyAsync(c->stage, (const double2*)in + off, mm * sizeof(double2), cudaMemcpyHostToDevice, c->st), "apply_h stage"))) return s;
+      if ((s = c->launch(KC_OTHER, "convert in", [&] { return launch_convert_in<R>(c->st, mm, c->stage, (float2*)c->Ta + off); }))) return s;
+    }
+  }
+  if ((s = kinetic<R>(c, c->Ta, c->tmp, A))) return s;
+  if ((s = gather<R>(c, c->Ta, A))) return s;
+  EpiParams ep{};
+  ep.mode = EPI_APPLY;
+  ep.nstates = c->nb;
+  fill_shifts(c, A, ep.shift);
+  ProjTables<R> pt = c->tables<R>();
+  const R* Vr = vsel<R>(c, true);
+  if ((s = c->launch(KC_EPI, "apply H", [&] {
+         return launch_epilogue<R>(c->st, c->N, c->tmp, c->Ta, nullptr, c->Tb, nullptr, nullptr, Vr, pt, c->dcbuf, c->nkb, ep);
+       })))
+    return s;
+  if (c->prec == TDDFT_FP64) {
+    if ((s = c->cuda(cudaMemcpyAsync(out, c->Tb, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st), "apply_h out"))) return s;
+  } else if (on_device) {
+    if ((s = c->launch(KC_OTHER, "convert out", [&] { return launch_convert_out<R>(c->st, n, c->Tb, (double2*)out); }))) return s;
+  } else {
+    for (size_t off = 0; off < n; off += c->stage_elems) {
+      const size_t mm = std::min(c->stage_elems, n - off);
+      if ((s = c->launch(KC_OTHER, "convert out", [&] { return launch_convert_out<R>(c->st, mm, (const float2*)c->Tb + off, c->stage); }))) return s;
+      if ((s = c->cuda(cudaMemcpyAsync((double2*)out + off, c->stage, mm * sizeof(double2), cudaMemcpyDeviceToHost, c->st), "apply_h stage out"))) return s;
+      if ((s = c->cuda(cudaStreamSynchronize(c->st), "apply_h sync"))) return s;
+    }
+  }
+  return c->cuda(cudaStreamSynchronize(c->st), "apply_h sync");
+}
+
+tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid* grid, const tddft_atoms* atoms,
+                         const tddft_projectors* pj, const tddft_params* pr) {
+  if (!cell || !grid || !atoms || !pj || !pr) return c->fail(TDDFT_ERR_ARG, "null argument");
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      if (i != j && cell->a[i][j] != 0.0) return c->fail(TDDFT_ERR_UNSUPPORTED, "only orthorhombic cells are supported");
+  for (int i = 0; i < 3; ++i) {
+    c->L[i] = cell->a[i][i];
+    if (!(c->L[i] > 0.0)) return c->fail(TDDFT_ERR_ARG, "cell lengths must be positive");
+  }
+  if (grid->n[0] != grid->n[1] || grid->n[0] != grid->n[2]) return c->fail(TDDFT_ERR_UNSUPPORTED, "grid must be cubic (n x n x n)");
+  if (!supported_n(grid->n[0])) return c->fail(TDDFT_ERR_UNSUPPORTED, "grid size must be one of 8, 12, 16, 24, 32, 48, 64, 96");
+  c->N = grid->n[0];
+  c->N3 = (size_t)c->N * c->N * c->N;
+  c->omega = c->L[0] * c->L[1] * c->L[2];
+  c->dV = c->omega / (double)c->N3;
+  if (pr->precision != TDDFT_FP64 && pr->precision != TDDFT_FP32_MIXED) return c->fail(TDDFT_ERR_ARG, "bad precision");
+  c->prec = pr->precision;
+  c->proj_mode = pr->proj_mode;
+  if (pr->nk < 1 || pr->nk > kMaxK || !pr->kpts || !pr->kw) return c->fail(TDDFT_ERR_ARG, "nk must be 1..16 with kpts and kw");
+  if (pr->nstates < 1 || !pr->occ) return c->fail(TDDFT_ERR_ARG, "nstates must be >= 1 with occ");
+  c->nk = pr->nk;
+  c->nb = pr->nstates;
+  c->nkb = c->nk * c->nb;
+  if (2 * c->nkb > 65535) return c->fail(TDDFT_ERR_UNSUPPORTED, "too many spinors (2 nk nstates must be <= 65535)");
+  c->kpts.assign(pr->kpts, pr->kpts + 3 * c->nk);
+  c->kw.assign(pr->kw, pr->kw + c->nk);
+  c->occ.assign(pr->occ, pr->occ + c->nkb);
+  c->wf.resize(c->nkb);
+  for (int k = 0; k < c->nk; ++k)
+    for (int b = 0; b < c->nb; ++b) c->wf[k * c->nb + b] = c->kw[k] * c->occ[k * c->nb + b];
+  if (!(pr->dt != 0.0) || !std::isfinite(pr->dt)) return c->fail(TDDFT_ERR_ARG, "dt must be finite and non-zero");
+  c->dt = pr->dt;
+  if (pr->exp_kind != TDDFT_EXP_CHEBYSHEV && pr->exp_kind != TDDFT_EXP_TAYLOR) return c->fail(TDDFT_ERR_ARG, "bad exp_kind");
+  c->exp_kind = pr->exp_kind;
+  c->exp_order = std::max(0, pr->exp_order);
+  c->cheb_tol = pr->cheb_tol;
+  c->n_sc = std::max(0, pr->n_sc);
+  c->sc_tol = pr->sc_tol;
+  c->emin_user = pr->e_min;
+  c->emax_user = pr->e_max;
+  if ((c->emin_user != 0.0 || c->emax_user != 0.0) && !(c->emax_user > c->emin_user))
+    return c->fail(TDDFT_ERR_ARG, "e_max must exceed e_min");
+  c->xc = pr->xc ? 1 : 0;
+  if (atoms->natoms < 0 || (atoms->natoms > 0 && (!atoms->pos || !atoms->species))) return c->fail(TDDFT_ERR_ARG, "bad atoms");
+  c->natoms = atoms->natoms;
+  if (c->natoms > 0) {
+    if (pj->nspecies < 1 || !pj->Z || !pj->rc_loc || !pj->width || !pj->D || !pj->lambda_so) return c->fail(TDDFT_ERR_ARG, "bad projectors");
+    if (pj->lmax < 0 || pj->lmax > 2) return c->fail(TDDFT_ERR_UNSUPPORTED, "lmax must be 0..2");
+    if (!(pj->r_cut > 0.0) || pj->r_cut > 0.5 * std::min(c->L[0], std::min(c->L[1], c->L[2])))
+      return c->fail(TDDFT_ERR_ARG, "r_cut must be positive and at most half the shortest cell side");
+    for (int a = 0; a < c->natoms; ++a)
+      if (atoms->species[a] < 0 || atoms->species[a] >= pj->nspecies) return c->fail(TDDFT_ERR_ARG, "species index out of range");
+  }
+  c->lmax = c->natoms > 0 ? pj->lmax : 0;
+  c->nlm = (c->lmax + 1) * (c->lmax + 1);
+  c->r_cut = pj->r_cut;
+  c->pos.assign(atoms->pos, atoms->pos + 3 * c->natoms);
+  std::vector<double> Zr(2 * std::max(1, c->natoms), 0.0);
+  for (int a = 0; a < c->natoms; ++a) {
+    Zr[2 * a] = pj->Z[atoms->species[a]];
+    Zr[2 * a + 1] = pj->rc_loc[atoms->species[a]];
+  }
+
+  // ---- device allocations
+  const size_t rs = c->rsize();
+  const size_t pbytes = c->psi_elems() * 2 * rs;
+  tddft_status s;
+  if ((s = c->alloc(&c->psi, pbytes, "psi")) || (s = c->alloc(&c->phi, pbytes, "phi")) ||
+      (s = c->alloc(&c->pred, pbytes, "pred")) || (s = c->alloc(&c->Ta, pbytes, "Ta")) ||
+      (s = c->alloc(&c->Tb, pbytes, "Tb")) || (s = c->alloc(&c->tmp, pbytes, "tmp")))
+    return s;
+  const size_t ncoef = (size_t)c->nkb * std::max(1, c->natoms) * 2 * c->nlm;
+  if ((s = c->alloc(&c->cbuf, ncoef * 2 * rs, "c")) || (s = c->alloc(&c->dcbuf, ncoef * 2 * rs, "dc"))) return s;
+  const size_t N3 = c->N3;
+  if ((s = c->alloc(&c->rho, 4 * N3 * 8, "rho")) || (s = c->alloc(&c->rho2, 4 * N3 * 8, "rho2")) ||
+      (s = c->alloc(&c->rho3, 4 * N3 * 8, "rho3")) || (s = c->alloc(&c->V, 4 * N3 * 8, "V")) ||
+      (s = c->alloc(&c->Vnew, 4 * N3 * 8, "Vnew")) || (s = c->alloc(&c->vloc, N3 * 8, "vloc")) ||
+      (s = c->alloc(&c->vH, N3 * 8, "vH")) || (s = c->alloc(&c->exc, N3 * 8, "exc")) ||
+      (s = c->alloc(&c->vxc4, 4 * N3 * 8, "vxc4")) || (s = c->alloc(&c->hart, N3 * 16, "hartree")) ||
+      (s = c->alloc(&c->red, (16 + 5 * (size_t)c->nkb) * 8, "reductions")) || (s = c->alloc(&c->flag, 16, "flag")))
+    return s;
+  if (c->prec != TDDFT_FP64) {
+    if ((s = c->alloc(&c->Vf, 4 * N3 * 4, "Vf")) || (s = c->alloc(&c->Vnewf, 4 * N3 * 4, "Vnewf"))) return s;
+    c->stage_elems = std::min(c->psi_elems(), (size_t)(64u << 20) / sizeof(double2));
+    if ((s = c->alloc(&c->stage, c->stage_elems * sizeof(double2), "stage"))) return s;
+  }
+  if ((s = upload(c, &c->wf_d, c->wf, "weights"))) return s;
+  if ((s = c->cuda(cudaMemset(c->flag, 0, 16), "flag init"))) return s;
+
+  // ---- twiddles exp(-2 pi i t / N)
+  std::vector<double> tw(2 * c->N);
+  for (int t = 0; t < c->N; ++t) {
+    const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)t / (long double)c->N;
+    tw[2 * t] = (double)std::cos(ang);
+    tw[2 * t + 1] = (double)std::sin(ang);
+  }
+  if ((s = upload(c, &c->tw64, std::vector<double2>((const double2*)tw.data(), (const double2*)tw.data() + c->N), "tw64")))
+    return s;
+  if (c->prec == TDDFT_FP64) {
+    c->tw = c->tw64;
+  } else if ((s = upload_typed<float>(c, &c->tw, tw, "tw32"))) {
+    return s;
+  }
+
+  // ---- local potential on the device
+  double* pos_d = nullptr;
+  double* zr_d = nullptr;
+  if ((s = upload(c, &pos_d, c->pos.empty() ? std::vector<double>(3, 0.0) : c->pos, "pos")) || (s = upload(c, &zr_d, Zr, "Zr")))
+    return s;
+  if ((s = c->launch(KC_OTHER, "vloc G", [&] { return launch_vloc_G(c->st, c->N, c->L, c->natoms, pos_d, zr_d, c->omega, c->hart); }))) return s;
+  ZParams zp{};
+  if ((s = c->launch(KC_OTHER, "vloc ifft z", [&] { return launch_fft_z<double>(c->st, c->N, c->hart, 1, c->tw64, Z_INV_ONLY, zp); }))) return s;
+  if ((s = c->launch(KC_OTHER, "vloc ifft xy", [&] { return launch_fft_xy<double>(c->st, c->N, c->hart, c->hart, 1, c->tw64, true); }))) return s;
+  if ((s = c->launch(KC_OTHER, "vloc real", [&] { return launch_complex_real_part(c->st, N3, c->hart, c->vloc, 1.0); }))) return s;
+
+  // ---- projector tables
+  HostTables ht;
+  if (c->natoms > 0) {
+    if ((s = build_tables(c, pj, atoms->species, ht))) return s;
+    c->nl_bound = ht.nl_bound;
+    c->n_entries = ht.g_idx.size();
+    if ((s = upload(c, &c->g_ptr, ht.g_ptr, "g_ptr")) || (s = upload(c, &c->g_idx, ht.g_idx, "g_idx")) ||
+        (s = upload(c, &c->s_ptr, ht.s_ptr, "s_ptr")) || (s = upload(c, &c->s_atom, ht.s_atom, "s_atom")))
+      return s;
+    if (c->prec == TDDFT_FP64) {
+      if ((s = upload_typed<double>(c, &c->g_tab, ht.g_tab, "g_tab")) || (s = upload_typed<double>(c, &c->s_tab, ht.s_tab, "s_tab")) ||
+          (s = upload_typed<double>(c, &c->Dmat, ht.Dmat, "D")))
+        return s;
+    } else {
+      if ((s = upload_typed<float>(c, &c->g_tab, ht.g_tab, "g_tab")) || (s = upload_typed<float>(c, &c->s_tab, ht.s_tab, "s_tab")) ||
+          (s = upload_typed<float>(c, &c->Dmat, ht.Dmat, "D")))
+        return s;
+    }
+  }
+  return c->cuda(cudaDeviceSynchronize(), "create sync");
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+tddft_status tddft_create(const tddft_cell* cell, const tddft_grid* grid, const tddft_atoms* atoms,
+                          const tddft_projectors* proj, const tddft_params* params, tddft_handle* out) {
+  if (!out) {
+    g_create_error = "null output handle";
+    return TDDFT_ERR_ARG;
+  }
+  *out = nullptr;
+  tddft_ctx* c = new (std::nothrow) tddft_ctx();
+  if (!c) {
+    g_create_error = "host allocation failed";
+    return TDDFT_ERR_OOM;
+  }
+  tddft_status s = create_impl(c, cell, grid, atoms, proj, params);
+  if (s != TDDFT_OK) {
+    g_create_error = c->err;
+    free_all(c);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_set_fields(tddft_handle h, int nt, const double* t, const double* A, const double* B) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (nt < 0 || (nt > 0 && (!t || !A || !B))) return h->fail(TDDFT_ERR_ARG, "bad field table");
+  for (int i = 1; i < nt; ++i)
+    if (!(t[i] > t[i - 1])) return h->fail(TDDFT_ERR_ARG, "field times must increase");
+  h->ft.assign(t, t + nt);
+  h->fA.assign(A, A + 3 * nt);
+  h->fB.assign(B, B + 3 * nt);
+  return TDDFT_OK;
+}
+
+tddft_status tddft_set_states(tddft_handle h, const void* psi, int on_device, double t0) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (!psi) return h->fail(TDDFT_ERR_ARG, "null psi");
+  return h->prec == TDDFT_FP64 ? do_set_states<double>(h, psi, on_device, t0) : do_set_states<float>(h, psi, on_device, t0);
+}
+
+tddft_status tddft_get_states(tddft_handle h, void* psi, int on_device) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (!psi) return h->fail(TDDFT_ERR_ARG, "null psi");
+  if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no states loaded");
+  return h->prec == TDDFT_FP64 ? do_get_states<double>(h, psi, on_device) : do_get_states<float>(h, psi, on_device);
+}
+
+tddft_status tddft_step(tddft_handle h, int nsteps) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (nsteps < 0) return h->fail(TDDFT_ERR_ARG, "nsteps must be >= 0");
+  if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "tddft_set_states must come first");
+  for (int i = 0; i < nsteps; ++i) {
+    tddft_status s = h->prec == TDDFT_FP64 ? one_step<double>(h) : one_step<float>(h);
+    if (s) return s;
+  }
+  return TDDFT_OK;
+}
+
+tddft_status tddft_observables(tddft_handle h, double* n, double* m, double* E, double* M, double* norms) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no states loaded");
+  return h->prec == TDDFT_FP64 ? do_observables<double>(h, n, m, E, M, norms) : do_observables<float>(h, n, m, E, M, norms);
+}
+
+tddft_status tddft_get_potential(tddft_handle h, double* V) {
+  if (!h || !V) return TDDFT_ERR_ARG;
+  if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no states loaded");
+  tddft_status s = h->cuda(cudaMemcpyAsync(V, h->V, 4 * h->N3 * sizeof(double), cudaMemcpyDeviceToHost, h->st), "potential read");
+  if (s) return s;
+  return h->cuda(cudaStreamSynchronize(h->st), "potential sync");
+}
+
+tddft_status tddft_apply_hamiltonian(tddft_handle h, const void* in, void* out, int on_device) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (!in || !out || in == out) return h->fail(TDDFT_ERR_ARG, "bad in/out");
+  if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no potential yet: call tddft_set_states first");
+  return h->prec == TDDFT_FP64 ? do_apply_h<double>(h, in, out, on_device) : do_apply_h<float>(h, in, out, on_device);
+}
+
+tddft_status tddft_set_stream(tddft_handle h, void* stream) {
+  if (!h) return TDDFT_ERR_ARG;
+  h->st = (cudaStream_t)stream;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_info(tddft_handle h, int* K_full, int* K_half, double* e_min, double* e_max, long long* launches) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (K_full) *K_full = h->K_full;
+  if (K_half) *K_half = h->K_half;
+  if (e_min) *e_min = h->emin;
+  if (e_max) *e_max = h->emax;
+  if (launches) *launches = h->launches;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_profile(tddft_handle h, int enable) {
+  if (!h) return TDDFT_ERR_ARG;
+  tddft_status s = h->cuda(cudaStreamSynchronize(h->st), "profile sync");
+  if (s) return s;
+  for (auto& v : h->ev) v.clear();
+  for (double& b : h->alg_bytes) b = 0.0;
+  h->ev_used = 0;
+  h->prof = enable != 0;
+  return TDDFT_OK;
+}
+
+tddft_status tddft_profile_read(tddft_handle h, int ncls, double* ms, long long* count, double* bytes) {
+  if (!h || ncls < 0 || ncls > kNumCls) return TDDFT_ERR_ARG;
+  tddft_status s = h->cuda(cudaStreamSynchronize(h->st), "profile sync");
+  if (s) return s;
+  for (int c = 0; c < ncls; ++c) {
+    double tot = 0.0;
+    for (auto& e : h->ev[c]) {
+      float x = 0.f;
+      cudaEventElapsedTime(&x, e.first, e.second);
+      tot += x;
+    }
+    if (ms) ms[c] = tot;
+    if (count) count[c] = (long long)h->ev[c].size();
+    if (bytes) bytes[c] = h->alg_bytes[c];
+  }
+  return TDDFT_OK;
+}
+
+const char* tddft_last_error(tddft_handle h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+void tddft_destroy(tddft_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tddft.h"
+
+namespace tddft {
+
+constexpr int kMaxK = 16;      // k-points per handle
+constexpr int kMaxNLM = 9;     // (lmax + 1)^2 with lmax <= 2
+constexpr int kNumCls = 8;     // profiling classes
+
+enum KernelClass { KC_FFT_XY = 0, KC_FFT_Z = 1, KC_EPI = 2, KC_PROJ = 3, KC_DENS = 4, KC_POT = 5, KC_OTHER = 6 };
+
+// Multiplier of the z pass: kinetic 1/2|G + s_k|^2 * scale, Poisson 4 pi / G^2 * scale.
+struct ZParams {
+  double gs[3];               // 2 pi / L_a
+  double scale;
+  int comps_per_k;            // spinor components per k-point (2 * nstates)
+  double shift[kMaxK][3];     // k + A(t) per k-point
+};
+
+enum ZMode { Z_KIN = 0, Z_POISSON = 1, Z_INV_ONLY = 2 };
+
+// Chebyshev / Taylor epilogue modes.
+enum EpiMode { EPI_APPLY = 0, EPI_FIRST = 1, EPI_RECUR = 2, EPI_TAYLOR = 3 };
+
+struct EpiParams {
+  int mode;
+  double c, inv_delta;          // H~ = (H - c) / Delta
+  double a0[2], a1[2];          // accumulator 1 coefficients (k = 0 and current k), complex
+  double b0[2], b1[2];          // accumulator 2 coefficients
+  int use_acc1, use_acc2;
+  double shift[kMaxK][3];       // k + A(t), for projector phases
+  int nstates;
+};
+
+// Device-side projector tables.
+template <typename R> struct ProjTables {
+  int natoms = 0, nlm = 0, ntab = 0;        // ntab = 3 + nlm reals per entry
+  const int* g_ptr = nullptr;               // [natoms + 1] entries of each atom (gather order)
+  const int* g_idx = nullptr;               // grid point of each gather entry
+  const R* g_tab = nullptr;                 // [entries][3 + nlm]: d, beta
+  const int* s_ptr = nullptr;               // [N^3 + 1] entries of each grid point (scatter order)
+  const int* s_atom = nullptr;              // atom of each scatter entry
+  const R* s_tab = nullptr;                 // [entries][3 + nlm]
+  const R* Dmat = nullptr;                  // [natoms][2 nlm][2 nlm] complex (re, im)
+};
+
+// ---------------------------------------------------------------- launchers
+template <typename R>
+cudaError_t launch_fft_xy(cudaStream_t st, int N, const void* src, void* dst, int nbatch, const void* tw, bool inv);
+template <typename R>
+cudaError_t launch_fft_z(cudaStream_t st, int N, void* data, int nbatch, const void* tw, int mode,
+                         const ZParams& zp);
+template <typename R>
+cudaError_t launch_proj_gather(cudaStream_t st, int N, const void* psi, int nkb, const ProjTables<R>& pt,
+                               double dV, const EpiParams& ep, void* c_out, void* dc_out);
+template <typename R>
+cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* Tk, const void* Tkm1,
+                            void* Tout, void* acc1, void* acc2, const R* V, const ProjTables<R>& pt,
+                            const void* dc, int nkb, const EpiParams& ep);
+template <typename R>
+cudaError_t launch_density(cudaStream_t st, size_t N3, const void* psi, int nkb, const double* wf,
+                           double* rho);
+cudaError_t launch_potential(cudaStream_t st, size_t N3, const double* rho, const double* vH,
+                             const double* vloc, const double* B, int xc, double* V, float* Vf,
+                             double* exc, double* vxc4);
+cudaError_t launch_density_to_complex(cudaStream_t st, size_t N3, const double* rho, double2* out);
+cudaError_t launch_complex_real_part(cudaStream_t st, size_t N3, const double2* in, double* out, double scale);
+cudaError_t launch_vloc_G(cudaStream_t st, int N, const double* L, int natoms, const double* pos,
+                          const double* Zr, double omega, double2* out);
+template <typename R>
+cudaError_t launch_convert_in(cudaStream_t st, size_t n, const double2* in, void* out);
+template <typename R>
+cudaError_t launch_convert_out(cudaStream_t st, size_t n, const void* in, double2* out);
+template <typename R>
+cudaError_t launch_band_dot(cudaStream_t st, size_t npts, int nbands, const void* a, const void* b,
+                            double* out2);
+template <typename R>
+cudaError_t launch_nl_energy(cudaStream_t st, int nkb, int ncoef, const void* c, const void* dc, double* out);
+cudaError_t launch_field_sums(cudaStream_t st, size_t N3, const double* rho, const double* vloc,
+                              const double* vH, const double* exc, const double* vxc4, const double* V,
+                              const double* B, double* out);
+cudaError_t launch_max_abs_diff(cudaStream_t st, size_t n, const double* a, const double* b, double* out);
+cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, double lo, double hi,
+                                double kin_max, double nl_bound, int* flag);
+
+}  // namespace tddft

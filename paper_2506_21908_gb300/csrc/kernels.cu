@@ -1,0 +1,679 @@
+// sm_103a kernels of the spinor propagation step.
+//
+//   k_fft_xy     one z-plane of one spinor component: 2D FFT along x then y in shared memory
+//   k_fft_z      one y-slab of one component: FFT along z, multiply (kinetic 1/2|G+k+A|^2 or
+//                Poisson 4 pi / G^2), inverse FFT along z -- the kinetic term of Eq. HNC-SDFT
+//   k_proj_gather  c_{a,p,sigma} = sum_{r in S_a} beta~_p(r)^* psi_sigma(r) dV and D_a c
+//                (the contraction of the separable projectors, Eq. Vps with the L.S block)
+//   k_epilogue   pointwise: kinetic + 2x2 spin-matrix potential (Eq. potential4,
+//                Eq. zeeman_potential) + projector scatter, then the Chebyshev / Taylor update
+//   k_density    rho_v = sum_k w_k sum_i f_i {|u|^2, |d|^2, Re u d*, Im u d*}  (Eqs. rho1-rho3)
+//   k_potential  locally collinear LSDA (Eqs. LC+ALDA2, LC+ALDA) and assembly of V_v
+//   reductions   deterministic fixed-order block reductions for energies and norms
+#include <cstdint>
+
+#include "fft.cuh"
+#include "impl.cuh"
+
+namespace tddft {
+
+template <int N> struct FFTThreads { static constexpr int value = (N >= 96) ? 512 : 256; };
+
+// ============================================================================ FFT passes
+
+template <typename R, int N, bool INV>
+__global__ void __launch_bounds__(FFTThreads<N>::value)
+k_fft_xy(const typename CT<R>::type* src, typename CT<R>::type* dst, const typename CT<R>::type* __restrict__ twg) {
+  using C = typename CT<R>::type;
+  constexpr int NT = FFTThreads<N>::value;
+  constexpr int RS = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + N;
+  const size_t base = ((size_t)blockIdx.y * N + blockIdx.x) * (size_t)(N * N);
+  for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < N * N; i += NT) s[(i / N) * RS + (i % N)] = src[base + i];
+  __syncthreads();
+  fft_pass<C, N, NT, INV>(s, RS, 1, tw);  // along x (rows: y)
+  fft_pass<C, N, NT, INV>(s, 1, RS, tw);  // along y (rows: x)
+  for (int i = threadIdx.x; i < N * N; i += NT) dst[base + i] = s[(i / N) * RS + (i % N)];
+}
+
+template <int N> __device__ __forceinline__ int freq(int i) { return i < N / 2 ? i : i - N; }
+
+template <typename R, int N, int MODE>
+__global__ void __launch_bounds__(FFTThreads<N>::value)
+k_fft_z(typename CT<R>::type* __restrict__ data, const typename CT<R>::type* __restrict__ twg, ZParams zp) {
+  using C = typename CT<R>::type;
+  constexpr int NT = FFTThreads<N>::value;
+  constexpr int RS = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + N;
+  const int y = blockIdx.x;
+  const int b = blockIdx.y;
+  const size_t base = (size_t)b * N * N * N + (size_t)y * N;
+  for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < N * N; i += NT) {
+    const int z = i / N, x = i - z * N;
+    s[z * RS + x] = data[base + (size_t)z * N * N + x];
+  }
+  __syncthreads();
+  if (MODE != Z_INV_ONLY) {
+    fft_pass<C, N, NT, false>(s, 1, RS, tw);  // along z (rows: x)
+    const double gy = zp.gs[1] * freq<N>(y);
+    const int k = (MODE == Z_KIN) ? b / zp.comps_per_k : 0;
+    for (int i = threadIdx.x; i < N * N; i += NT) {
+      const int z = i / N, x = i - z * N;
+      const double gx = zp.gs[0] * freq<N>(x), gz = zp.gs[2] * freq<N>(z);
+      double m;
+      if (MODE == Z_KIN) {
+        const double qx = gx + zp.shift[k][0], qy = gy + zp.shift[k][1], qz = gz + zp.shift[k][2];
+        m = 0.5 * (qx * qx + qy * qy + qz * qz) * zp.scale;
+      } else {
+        const double g2 = gx * gx + gy * gy + gz * gz;
+        m = g2 > 0.0 ? 4.0 * 3.14159265358979323846 / g2 * zp.scale : 0.0;
+      }
+      s[z * RS + x] = cscale(s[z * RS + x], (R)m);
+    }
+    __syncthreads();
+  }
+  fft_pass<C, N, NT, true>(s, 1, RS, tw);
+  for (int i = threadIdx.x; i < N * N; i += NT) {
+    const int z = i / N, x = i - z * N;
+    data[base + (size_t)z * N * N + x] = s[z * RS + x];
+  }
+}
+
+template <typename R, int N>
+static cudaError_t fft_xy_n(cudaStream_t st, const void* src, void* data, int nbatch, const void* tw, bool inv) {
+  using C = typename CT<R>::type;
+  const size_t smem = (size_t)(N + N * (N + 1)) * sizeof(C);
+  dim3 grid(N, nbatch);
+  if (inv) {
+    auto kf = k_fft_xy<R, N, true>;
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kf<<<grid, FFTThreads<N>::value, smem, st>>>((const C*)src, (C*)data, (const C*)tw);
+  } else {
+    auto kf = k_fft_xy<R, N, false>;
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kf<<<grid, FFTThreads<N>::value, smem, st>>>((const C*)src, (C*)data, (const C*)tw);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R, int N, int MODE>
+static cudaError_t fft_z_nm(cudaStream_t st, void* data, int nbatch, const void* tw, const ZParams& zp) {
+  using C = typename CT<R>::type;
+  const size_t smem = (size_t)(N + N * (N + 1)) * sizeof(C);
+  auto kf = k_fft_z<R, N, MODE>;
+  cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kf<<<dim3(N, nbatch), FFTThreads<N>::value, smem, st>>>((C*)data, (const C*)tw, zp);
+  return cudaGetLastError();
+}
+
+template <typename R, int N>
+static cudaError_t fft_z_n(cudaStream_t st, void* data, int nbatch, const void* tw, int mode, const ZParams& zp) {
+  switch (mode) {
+    case Z_KIN: return fft_z_nm<R, N, Z_KIN>(st, data, nbatch, tw, zp);
+    case Z_POISSON: return fft_z_nm<R, N, Z_POISSON>(st, data, nbatch, tw, zp);
+    default: return fft_z_nm<R, N, Z_INV_ONLY>(st, data, nbatch, tw, zp);
+  }
+}
+
+#define TDDFT_DISPATCH_N(N, CALL)          \
+  switch (N) {                             \
+    case 8: { constexpr int NN = 8; return CALL; }   \
+    case 12: { constexpr int NN = 12; return CALL; } \
+    case 16: { constexpr int NN = 16; return CALL; } \
+    case 24: { constexpr int NN = 24; return CALL; } \
+    case 32: { constexpr int NN = 32; return CALL; } \
+    case 48: { constexpr int NN = 48; return CALL; } \
+    case 64: { constexpr int NN = 64; return CALL; } \
+    case 96: { constexpr int NN = 96; return CALL; } \
+    default: return cudaErrorInvalidValue;           \
+  }
+
+template <typename R>
+cudaError_t launch_fft_xy(cudaStream_t st, int N, const void* src, void* data, int nbatch, const void* tw, bool inv) {
+  TDDFT_DISPATCH_N(N, (fft_xy_n<R, NN>(st, src, data, nbatch, tw, inv)));
+}
+template <typename R>
+cudaError_t launch_fft_z(cudaStream_t st, int N, void* data, int nbatch, const void* tw, int mode, const ZParams& zp) {
+  TDDFT_DISPATCH_N(N, (fft_z_n<R, NN>(st, data, nbatch, tw, mode, zp)));
+}
+
+// ============================================================================ projectors
+
+template <typename R> __device__ __forceinline__ void sincos_r(R x, R* s, R* c);
+template <> __device__ __forceinline__ void sincos_r<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+template <> __device__ __forceinline__ void sincos_r<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One CTA per (atom, spinor): c[p][sigma] = sum_e beta_p exp(+i s.d) psi_sigma(r_e) dV, then D c.
+template <typename R, int NLM>
+__global__ void __launch_bounds__(256)
+k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTables<R> pt, R dV, EpiParams ep,
+              typename CT<R>::type* __restrict__ c_out, typename CT<R>::type* __restrict__ dc_out) {
+  using C = typename CT<R>::type;
+  constexpr int NV = 4 * NLM;  // reals: (re, im) x (up, dn) x NLM
+  constexpr int TAB = 3 + NLM;
+  const int a = blockIdx.x;
+  const int kb = blockIdx.y;
+  const int k = kb / ep.nstates;
+  const R sx = (R)ep.shift[k][0], sy = (R)ep.shift[k][1], sz = (R)ep.shift[k][2];
+  const C* up = psi + (size_t)(2 * kb) * N3;
+  const C* dn = up + N3;
+  R acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = (R)0;
+  const int e0 = pt.g_ptr[a], e1 = pt.g_ptr[a + 1];
+  for (int e = e0 + threadIdx.x; e < e1; e += 256) {
+    const int r = pt.g_idx[e];
+    const R* t = pt.g_tab + (size_t)e * TAB;
+    R sn, cs;
+    sincos_r<R>(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);
+    const C u = up[r], d = dn[r];
+    const R pux = u.x * cs - u.y * sn, puy = u.x * sn + u.y * cs;  // u exp(+i arg)
+    const R pdx = d.x * cs - d.y * sn, pdy = d.x * sn + d.y * cs;
+#pragma unroll
+    for (int p = 0; p < NLM; ++p) {
+      const R bp = t[3 + p];
+      acc[4 * p + 0] += bp * pux;
+      acc[4 * p + 1] += bp * puy;
+      acc[4 * p + 2] += bp * pdx;
+      acc[4 * p + 3] += bp * pdy;
+    }
+  }
+  __shared__ R red[8][NV];
+  __shared__ C cv[2 * NLM];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    const R v = warp_sum(acc[i]);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * NLM) {
+    R re = 0, im = 0;
+    for (int w = 0; w < 8; ++w) {
+      re += red[w][2 * threadIdx.x];
+      im += red[w][2 * threadIdx.x + 1];
+    }
+    C c = cmake<C>(re * dV, im * dV);
+    cv[threadIdx.x] = c;
+    c_out[((size_t)kb * pt.natoms + a) * 2 * NLM + threadIdx.x] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * NLM) {
+    const R* D = pt.Dmat + ((size_t)a * 2 * NLM + threadIdx.x) * 2 * NLM * 2;
+    R re = 0, im = 0;
+    for (int u = 0; u < 2 * NLM; ++u) {
+      const R dr = D[2 * u], di = D[2 * u + 1];
+      re += dr * cv[u].x - di * cv[u].y;
+      im += dr * cv[u].y + di * cv[u].x;
+    }
+    dc_out[((size_t)kb * pt.natoms + a) * 2 * NLM + threadIdx.x] = cmake<C>(re, im);
+  }
+}
+
+template <typename R>
+cudaError_t launch_proj_gather(cudaStream_t st, int N, const void* psi, int nkb, const ProjTables<R>& pt,
+                               double dV, const EpiParams& ep, void* c_out, void* dc_out) {
+  using C = typename CT<R>::type;
+  if (pt.natoms == 0) return cudaSuccess;
+  dim3 grid(pt.natoms, nkb);
+  const size_t N3 = (size_t)N * N * N;
+  switch (pt.nlm) {
+    case 1: k_proj_gather<R, 1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
+    case 4: k_proj_gather<R, 4><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
+    case 9: k_proj_gather<R, 9><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ============================================================================ epilogue
+
+template <typename R, int NLM>
+__global__ void __launch_bounds__(256)
+k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::type* Tk,
+           const typename CT<R>::type* Tkm1, typename CT<R>::type* Tout, typename CT<R>::type* acc1,
+           typename CT<R>::type* acc2, const R* __restrict__ V, size_t N3, ProjTables<R> pt,
+           const typename CT<R>::type* __restrict__ dc, EpiParams ep) {
+  using C = typename CT<R>::type;
+  constexpr int TAB = 3 + NLM;
+  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N3) return;
+  const int kb = blockIdx.y;
+  const int k = kb / ep.nstates;
+  const size_t ou = (size_t)(2 * kb) * N3 + r, od = ou + N3;
+  const C pu = Tk[ou], pd = Tk[od];
+  const R V0 = V[r], V1 = V[N3 + r], hx = (R)0.5 * V[2 * N3 + r], hy = (R)0.5 * V[3 * N3 + r];
+  // [[v + b_z, b_x - i b_y], [b_x + i b_y, v - b_z]] with b_x = V2/2, b_y = -V3/2
+  C ku = kin[ou], kd = kin[od];
+  C hu = cmake<C>(ku.x + V0 * pu.x + hx * pd.x - hy * pd.y, ku.y + V0 * pu.y + hx * pd.y + hy * pd.x);
+  C hd = cmake<C>(kd.x + V1 * pd.x + hx * pu.x + hy * pu.y, kd.y + V1 * pd.y + hx * pu.y - hy * pu.x);
+  if (NLM > 0) {
+    const int e0 = pt.s_ptr[r], e1 = pt.s_ptr[r + 1];
+    const R sx = (R)ep.shift[k][0], sy = (R)ep.shift[k][1], sz = (R)ep.shift[k][2];
+    for (int e = e0; e < e1; ++e) {
+      const int a = pt.s_atom[e];
+      const R* t = pt.s_tab + (size_t)e * TAB;
+      const C* dca = dc + ((size_t)kb * pt.natoms + a) * 2 * NLM;
+      R vux = 0, vuy = 0, vdx = 0, vdy = 0;
+#pragma unroll
+      for (int p = 0; p < NLM; ++p) {
+        const R bp = t[3 + p];
+        const C cu = dca[2 * p], cd = dca[2 * p + 1];
+        vux += bp * cu.x; vuy += bp * cu.y;
+        vdx += bp * cd.x; vdy += bp * cd.y;
+      }
+      R sn, cs;
+      sincos_r<R>(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);  // exp(-i arg) = cs - i sn
+      hu.x += vux * cs + vuy * sn; hu.y += vuy * cs - vux * sn;
+      hd.x += vdx * cs + vdy * sn; hd.y += vdy * cs - vdx * sn;
+    }
+  }
+  if (ep.mode == EPI_APPLY) {
+    Tout[ou] = hu;
+    Tout[od] = hd;
+    return;
+  }
+  C tu, td;
+  if (ep.mode == EPI_TAYLOR) {
+    const R cr = (R)ep.a1[0], ci = (R)ep.a1[1];
+    tu = cmake<C>(cr * hu.x - ci * hu.y, cr * hu.y + ci * hu.x);
+    td = cmake<C>(cr * hd.x - ci * hd.y, cr * hd.y + ci * hd.x);
+    Tout[ou] = tu; Tout[od] = td;
+    C au = acc1[ou], ad = acc1[od];
+    acc1[ou] = cadd(au, tu); acc1[od] = cadd(ad, td);
+    return;
+  }
+  const R cc = (R)ep.c, id = (R)ep.inv_delta;
+  if (ep.mode == EPI_FIRST) {
+    tu = cmake<C>((hu.x - cc * pu.x) * id, (hu.y - cc * pu.y) * id);
+    td = cmake<C>((hd.x - cc * pd.x) * id, (hd.y - cc * pd.y) * id);
+  } else {
+    const C qu = Tkm1[ou], qd = Tkm1[od];
+    tu = cmake<C>((R)2 * (hu.x - cc * pu.x) * id - qu.x, (R)2 * (hu.y - cc * pu.y) * id - qu.y);
+    td = cmake<C>((R)2 * (hd.x - cc * pd.x) * id - qd.x, (R)2 * (hd.y - cc * pd.y) * id - qd.y);
+  }
+  Tout[ou] = tu;
+  Tout[od] = td;
+  auto upd = [&](C* acc, const double* c0, const double* c1) {
+    const R ar = (R)c1[0], ai = (R)c1[1];
+    C nu = cmake<C>(ar * tu.x - ai * tu.y, ar * tu.y + ai * tu.x);
+    C nd = cmake<C>(ar * td.x - ai * td.y, ar * td.y + ai * td.x);
+    if (ep.mode == EPI_FIRST) {
+      const R br = (R)c0[0], bi = (R)c0[1];
+      nu = cadd(nu, cmake<C>(br * pu.x - bi * pu.y, br * pu.y + bi * pu.x));
+      nd = cadd(nd, cmake<C>(br * pd.x - bi * pd.y, br * pd.y + bi * pd.x));
+    } else {
+      nu = cadd(nu, acc[ou]);
+      nd = cadd(nd, acc[od]);
+    }
+    acc[ou] = nu;
+    acc[od] = nd;
+  };
+  if (ep.use_acc1) upd(acc1, ep.a0, ep.a1);
+  if (ep.use_acc2) upd(acc2, ep.b0, ep.b1);
+}
+
+template <typename R>
+cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* Tk, const void* Tkm1, void* Tout,
+                            void* acc1, void* acc2, const R* V, const ProjTables<R>& pt, const void* dc, int nkb,
+                            const EpiParams& ep) {
+  using C = typename CT<R>::type;
+  const size_t N3 = (size_t)N * N * N;
+  dim3 grid((unsigned)((N3 + 255) / 256), nkb);
+  const int nlm = pt.natoms > 0 ? pt.nlm : 0;
+#define EPI_ARGS (const C*)kin, (const C*)Tk, (const C*)Tkm1, (C*)Tout, (C*)acc1, (C*)acc2, V, N3, pt, (const C*)dc, ep
+  switch (nlm) {
+    case 0: k_epilogue<R, 0><<<grid, 256, 0, st>>>(EPI_ARGS); break;
+    case 1: k_epilogue<R, 1><<<grid, 256, 0, st>>>(EPI_ARGS); break;
+    case 4: k_epilogue<R, 4><<<grid, 256, 0, st>>>(EPI_ARGS); break;
+    case 9: k_epilogue<R, 9><<<grid, 256, 0, st>>>(EPI_ARGS); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef EPI_ARGS
+  return cudaGetLastError();
+}
+
+// ============================================================================ density
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_density(const typename CT<R>::type* __restrict__ psi, size_t N3, int nkb, const double* __restrict__ wf,
+          double* __restrict__ rho) {
+  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N3) return;
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  for (int kb = 0; kb < nkb; ++kb) {
+    const auto u = psi[(size_t)(2 * kb) * N3 + r];
+    const auto d = psi[(size_t)(2 * kb + 1) * N3 + r];
+    const double ux = u.x, uy = u.y, dx = d.x, dy = d.y, w = wf[kb];
+    s0 += w * (ux * ux + uy * uy);
+    s1 += w * (dx * dx + dy * dy);
+    s2 += w * (ux * dx + uy * dy);   // Re(u conj d)
+    s3 += w * (uy * dx - ux * dy);   // Im(u conj d)
+  }
+  rho[r] = s0;
+  rho[N3 + r] = s1;
+  rho[2 * N3 + r] = s2;
+  rho[3 * N3 + r] = s3;
+}
+
+template <typename R>
+cudaError_t launch_density(cudaStream_t st, size_t N3, const void* psi, int nkb, const double* wf, double* rho) {
+  k_density<R><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>((const typename CT<R>::type*)psi, N3, nkb, wf, rho);
+  return cudaGetLastError();
+}
+
+// ============================================================================ XC and potential
+
+// PW92 interpolation G(rs) and dG/drs for one parameter row (A, a1, b1, b2, b3, b4), p = 1.
+__device__ __forceinline__ void pw92_g(double rs, double A, double a1, double b1, double b2, double b3, double b4,
+                                       double* g, double* dg) {
+  const double sr = sqrt(rs);
+  const double q0 = -2.0 * A * (1.0 + a1 * rs);
+  const double q1 = 2.0 * A * sr * (b1 + sr * (b2 + sr * (b3 + sr * b4)));
+  const double q1p = A * (b1 / sr + 2.0 * b2 + 3.0 * b3 * sr + 4.0 * b4 * rs);
+  const double lg = log1p(1.0 / q1);
+  *g = q0 * lg;
+  *dg = -2.0 * A * a1 * lg - q0 * q1p / (q1 * (q1 + 1.0));
+}
+
+// Slater exchange with spin scaling plus PW92 correlation on (nu, nd): energy density, v_up, v_dn.
+__device__ void lsda_point(double nu, double nd, double* e, double* vu, double* vd) {
+  const double kPi = 3.14159265358979323846;
+  const double c6 = cbrt(6.0 / kPi);
+  const double cbu = cbrt(nu), cbd = cbrt(nd);
+  const double ex = -0.75 * c6 * (nu * cbu + nd * cbd);
+  const double vxu = -c6 * cbu, vxd = -c6 * cbd;
+  const double n = nu + nd;
+  const double rs = cbrt(3.0 / (4.0 * kPi * n));
+  double z = (nu - nd) / n;
+  z = fmin(1.0, fmax(-1.0, z));
+  double ec0, d0, ec1, d1, mac, dmac;
+  pw92_g(rs, 0.031091, 0.21370, 7.5957, 3.5876, 1.6382, 0.49294, &ec0, &d0);
+  pw92_g(rs, 0.015545, 0.20548, 14.1189, 6.1977, 3.3662, 0.62517, &ec1, &d1);
+  pw92_g(rs, 0.016887, 0.11125, 10.357, 3.6231, 0.88026, 0.49671, &mac, &dmac);
+  const double ac = -mac, dac = -dmac;
+  const double fden = 1.0 / (cbrt(16.0) - 2.0);  // 1 / (2^(4/3) - 2)
+  const double opz = 1.0 + z, omz = 1.0 - z;
+  const double cpz = cbrt(opz), cmz = cbrt(omz);
+  const double f = (opz * cpz + omz * cmz - 2.0) * fden;
+  const double fp = (4.0 / 3.0) * (cpz - cmz) * fden;
+  const double fpp0 = 1.709921;
+  const double z3 = z * z * z, z4 = z3 * z;
+  const double ec = ec0 + ac * f * (1.0 - z4) / fpp0 + (ec1 - ec0) * f * z4;
+  const double drs = d0 + dac * f * (1.0 - z4) / fpp0 + (d1 - d0) * f * z4;
+  const double dz = ac / fpp0 * (fp * (1.0 - z4) - 4.0 * z3 * f) + (ec1 - ec0) * (fp * z4 + 4.0 * z3 * f);
+  const double common = ec - rs / 3.0 * drs;
+  *e = ex + n * ec;
+  *vu = vxu + common - (z - 1.0) * dz;
+  *vd = vxd + common - (z + 1.0) * dz;
+}
+
+__global__ void k_potential(size_t N3, const double* __restrict__ rho, const double* __restrict__ vH,
+                            const double* __restrict__ vloc, double Bx, double By, double Bz, int xc,
+                            double* __restrict__ V, float* __restrict__ Vf, double* __restrict__ exc,
+                            double* __restrict__ vxc4) {
+  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N3) return;
+  const double r0 = rho[r], r1 = rho[N3 + r], r2 = rho[2 * N3 + r], r3 = rho[3 * N3 + r];
+  const double n = r0 + r1, mx = 2.0 * r2, my = -2.0 * r3, mz = r0 - r1;
+  double e = 0.0, vbar = 0.0, bx = 0.0, by = 0.0, bz = 0.0;
+  if (xc && n >= 1e-14) {
+    const double mag = sqrt(mx * mx + my * my + mz * mz);
+    const double s = fmin(mag, n);
+    double vu, vd;
+    lsda_point(0.5 * (n + s), 0.5 * (n - s), &e, &vu, &vd);
+    vbar = 0.5 * (vu + vd);
+    if (mag > 1e-14) {
+      const double bm = 0.5 * (vu - vd) / mag;
+      bx = bm * mx; by = bm * my; bz = bm * mz;
+    }
+  }
+  const double v = vloc[r] + vH[r] + vbar;
+  const double tx = bx + 0.5 * Bx, ty = by + 0.5 * By, tz = bz + 0.5 * Bz;  // mu_B = 1/2
+  const double V0 = v + tz, V1 = v - tz, V2 = 2.0 * tx, V3 = -2.0 * ty;
+  V[r] = V0; V[N3 + r] = V1; V[2 * N3 + r] = V2; V[3 * N3 + r] = V3;
+  if (Vf) {
+    Vf[r] = (float)V0; Vf[N3 + r] = (float)V1; Vf[2 * N3 + r] = (float)V2; Vf[3 * N3 + r] = (float)V3;
+  }
+  exc[r] = e;
+  vxc4[r] = vbar + bz; vxc4[N3 + r] = vbar - bz; vxc4[2 * N3 + r] = 2.0 * bx; vxc4[3 * N3 + r] = -2.0 * by;
+}
+
+cudaError_t launch_potential(cudaStream_t st, size_t N3, const double* rho, const double* vH, const double* vloc,
+                             const double* B, int xc, double* V, float* Vf, double* exc, double* vxc4) {
+  k_potential<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, rho, vH, vloc, B[0], B[1], B[2], xc, V, Vf, exc, vxc4);
+  return cudaGetLastError();
+}
+
+// (rho_uu + rho_dd, 0): the total density as a complex field for the Poisson solve.
+__global__ void k_density_to_complex(size_t n, const double* rho, double2* out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2(rho[i] + rho[n + i], 0.0);
+}
+cudaError_t launch_density_to_complex(cudaStream_t st, size_t N3, const double* rho, double2* out) {
+  k_density_to_complex<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, rho, out);
+  return cudaGetLastError();
+}
+__global__ void k_complex_real_part(size_t n, const double2* in, double* out, double scale) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i].x * scale;
+}
+cudaError_t launch_complex_real_part(cudaStream_t st, size_t N3, const double2* in, double* out, double scale) {
+  k_complex_real_part<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, in, out, scale);
+  return cudaGetLastError();
+}
+
+// V_loc(G) = sum_a [-4 pi Z / G^2 exp(-G^2 rc^2 / 4) exp(-i G.R_a)] / Omega, G = 0: sum_a pi Z rc^2 / Omega.
+__global__ void k_vloc_G(int N, double gx0, double gy0, double gz0, int natoms, const double* __restrict__ pos,
+                         const double* __restrict__ Zr, double omega, double2* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t N3 = (size_t)N * N * N;
+  if (i >= N3) return;
+  const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((size_t)N * N));
+  auto fq = [N](int j) { return j < N / 2 ? j : j - N; };
+  const double gx = gx0 * fq(x), gy = gy0 * fq(y), gz = gz0 * fq(z);
+  const double g2 = gx * gx + gy * gy + gz * gz;
+  const double kPi = 3.14159265358979323846;
+  double re = 0.0, im = 0.0;
+  for (int a = 0; a < natoms; ++a) {
+    const double Z = Zr[2 * a], rc = Zr[2 * a + 1];
+    const double t = g2 > 0.0 ? -4.0 * kPi * Z / g2 * exp(-g2 * rc * rc * 0.25) : kPi * Z * rc * rc;
+    double sn, cs;
+    sincos(gx * pos[3 * a] + gy * pos[3 * a + 1] + gz * pos[3 * a + 2], &sn, &cs);
+    re += t * cs;
+    im -= t * sn;
+  }
+  out[i] = make_double2(re / omega, im / omega);
+}
+cudaError_t launch_vloc_G(cudaStream_t st, int N, const double* L, int natoms, const double* pos, const double* Zr,
+                          double omega, double2* out) {
+  const size_t N3 = (size_t)N * N * N;
+  const double kPi = 3.14159265358979323846;
+  k_vloc_G<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N, 2 * kPi / L[0], 2 * kPi / L[1], 2 * kPi / L[2], natoms,
+                                                         pos, Zr, omega, out);
+  return cudaGetLastError();
+}
+
+// ============================================================================ conversions
+
+template <typename R>
+__global__ void k_convert_in(size_t n, const double2* __restrict__ in, typename CT<R>::type* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = cmake<typename CT<R>::type>((R)in[i].x, (R)in[i].y);
+}
+template <typename R>
+__global__ void k_convert_out(size_t n, const typename CT<R>::type* __restrict__ in, double2* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+template <typename R>
+cudaError_t launch_convert_in(cudaStream_t st, size_t n, const double2* in, void* out) {
+  k_convert_in<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, (typename CT<R>::type*)out);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_convert_out(cudaStream_t st, size_t n, const void* in, double2* out) {
+  k_convert_out<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, (const typename CT<R>::type*)in, out);
+  return cudaGetLastError();
+}
+
+// ============================================================================ reductions (fixed order)
+
+template <int NT>
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) t += sh[w];
+  return t;  // valid in thread 0
+}
+
+// out2[band] = sum over npts of conj(a) b (complex, double accumulation), one CTA per band.
+template <typename R>
+__global__ void __launch_bounds__(256) k_band_dot(size_t npts, const typename CT<R>::type* __restrict__ a,
+                                                  const typename CT<R>::type* __restrict__ b, double* out2) {
+  __shared__ double sh[8];
+  const size_t off = (size_t)blockIdx.x * npts;
+  double re = 0.0, im = 0.0;
+  for (size_t i = threadIdx.x; i < npts; i += 256) {
+    const auto x = a[off + i], y = b[off + i];
+    re += (double)x.x * y.x + (double)x.y * y.y;
+    im += (double)x.x * y.y - (double)x.y * y.x;
+  }
+  const double tr = block_sum<256>(re, sh);
+  const double ti = block_sum<256>(im, sh);
+  if (threadIdx.x == 0) {
+    out2[2 * blockIdx.x] = tr;
+    out2[2 * blockIdx.x + 1] = ti;
+  }
+}
+template <typename R>
+cudaError_t launch_band_dot(cudaStream_t st, size_t npts, int nbands, const void* a, const void* b, double* out2) {
+  using C = typename CT<R>::type;
+  k_band_dot<R><<<nbands, 256, 0, st>>>(npts, (const C*)a, (const C*)b, out2);
+  return cudaGetLastError();
+}
+
+// out[kb] = Re sum conj(c) dc over atoms, projectors and spins.
+template <typename R>
+__global__ void k_nl_energy(int ncoef, const typename CT<R>::type* __restrict__ c,
+                            const typename CT<R>::type* __restrict__ dc, double* out) {
+  __shared__ double sh[8];
+  const size_t off = (size_t)blockIdx.x * ncoef;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < ncoef; i += 256) s += (double)c[off + i].x * dc[off + i].x + (double)c[off + i].y * dc[off + i].y;
+  const double t = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+template <typename R>
+cudaError_t launch_nl_energy(cudaStream_t st, int nkb, int ncoef, const void* c, const void* dc, double* out) {
+  using C = typename CT<R>::type;
+  k_nl_energy<R><<<nkb, 256, 0, st>>>(ncoef, (const C*)c, (const C*)dc, out);
+  return cudaGetLastError();
+}
+
+// Field integrals (without dV): [0] v_loc n, [1] v_H n, [2] e_xc, [3..5] m, [6] n, [7] B.m,
+// [8] <rho_v, V_v^xc>, [9] count of non-finite rho values.
+__global__ void __launch_bounds__(1024)
+k_field_sums(size_t N3, const double* __restrict__ rho, const double* __restrict__ vloc, const double* __restrict__ vH,
+             const double* __restrict__ exc, const double* __restrict__ vxc4, double Bx, double By, double Bz,
+             double* out) {
+  __shared__ double sh[32];
+  double acc[10];
+  for (int i = 0; i < 10; ++i) acc[i] = 0.0;
+  for (size_t r = threadIdx.x; r < N3; r += 1024) {
+    const double r0 = rho[r], r1 = rho[N3 + r], r2 = rho[2 * N3 + r], r3 = rho[3 * N3 + r];
+    const double n = r0 + r1, mx = 2.0 * r2, my = -2.0 * r3, mz = r0 - r1;
+    acc[0] += vloc[r] * n;
+    acc[1] += vH[r] * n;
+    acc[2] += exc[r];
+    acc[3] += mx; acc[4] += my; acc[5] += mz;
+    acc[6] += n;
+    acc[7] += Bx * mx + By * my + Bz * mz;
+    acc[8] += r0 * vxc4[r] + r1 * vxc4[N3 + r] + r2 * vxc4[2 * N3 + r] + r3 * vxc4[3 * N3 + r];
+    acc[9] += (isfinite(r0) && isfinite(r1) && isfinite(r2) && isfinite(r3)) ? 0.0 : 1.0;
+  }
+  for (int i = 0; i < 10; ++i) {
+    const double t = block_sum<1024>(acc[i], sh);
+    if (threadIdx.x == 0) out[i] = t;
+  }
+}
+cudaError_t launch_field_sums(cudaStream_t st, size_t N3, const double* rho, const double* vloc, const double* vH,
+                              const double* exc, const double* vxc4, const double* /*V*/, const double* B, double* out) {
+  k_field_sums<<<1, 1024, 0, st>>>(N3, rho, vloc, vH, exc, vxc4, B[0], B[1], B[2], out);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(1024) k_max_abs_diff(size_t n, const double* a, const double* b, double* out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += 1024) m = fmax(m, fabs(a[i] - b[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 32; ++w) t = fmax(t, sh[w]);
+    *out = t;
+  }
+}
+cudaError_t launch_max_abs_diff(cudaStream_t st, size_t n, const double* a, const double* b, double* out) {
+  k_max_abs_diff<<<1, 1024, 0, st>>>(n, a, b, out);
+  return cudaGetLastError();
+}
+
+// Sets *flag when the local potential leaves [lo, hi] given the kinetic maximum and projector bound.
+__global__ void k_check_window(size_t N3, const double* __restrict__ V, double lo, double hi, double kin_max,
+                               double nl_bound, int* flag) {
+  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N3) return;
+  const double v = 0.5 * (V[r] + V[N3 + r]);
+  const double bz = 0.5 * (V[r] - V[N3 + r]), bx = 0.5 * V[2 * N3 + r], by = 0.5 * V[3 * N3 + r];
+  const double b = sqrt(bx * bx + by * by + bz * bz);
+  const bool bad = !(v - b - nl_bound >= lo) || !(v + b + nl_bound + kin_max <= hi);
+  if (bad) atomicOr(flag, 1);
+}
+cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, double lo, double hi, double kin_max,
+                                double nl_bound, int* flag) {
+  k_check_window<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, V, lo, hi, kin_max, nl_bound, flag);
+  return cudaGetLastError();
+}
+
+// ============================================================================ instantiations
+#define TDDFT_INST(R)                                                                                           \
+  template cudaError_t launch_fft_xy<R>(cudaStream_t, int, const void*, void*, int, const void*, bool);                       \
+  template cudaError_t launch_fft_z<R>(cudaStream_t, int, void*, int, const void*, int, const ZParams&);          \
+  template cudaError_t launch_proj_gather<R>(cudaStream_t, int, const void*, int, const ProjTables<R>&, double,  \
+                                             const EpiParams&, void*, void*);                                   \
+  template cudaError_t launch_epilogue<R>(cudaStream_t, int, const void*, const void*, const void*, void*, void*, \
+                                          void*, const R*, const ProjTables<R>&, const void*, int,              \
+                                          const EpiParams&);                                                    \
+  template cudaError_t launch_density<R>(cudaStream_t, size_t, const void*, int, const double*, double*);        \
+  template cudaError_t launch_convert_in<R>(cudaStream_t, size_t, const double2*, void*);                        \
+  template cudaError_t launch_convert_out<R>(cudaStream_t, size_t, const void*, double2*);                       \
+  template cudaError_t launch_band_dot<R>(cudaStream_t, size_t, int, const void*, const void*, double*);         \
+  template cudaError_t launch_nl_energy<R>(cudaStream_t, int, int, const void*, const void*, double*);
+
+TDDFT_INST(float)
+TDDFT_INST(double)
+
+}  // namespace tddft

@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 CPU oracle on the
+same seeded inputs (element-wise), plus invariants at the full cluster size.
+
+Tolerances (stated target): FP64 |dn|, |dm|, |dpsi| <= 1e-10 relative to the oracle's
+max-norm and |dE| <= 1e-8 Ha per step.  FP32-mixed is compared at 2e-5 relative (spinor
+storage and FFTs in FP32: a few ulp of 1.2e-7 accumulated over the Chebyshev terms)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import Oracle, System
+from oracle.tddft import FieldTable
+from paper_2506_21908_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def run_pair(lib, wl, psi0, nsteps, bounds, precision=0, **kw):
+    from paper_2506_21908_gb300 import _lib
+    h = _lib.TDDFT.from_workload(wl, precision=precision, e_min=bounds[0], e_max=bounds[1], **kw)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi0, 0.0)
+    o = Oracle(System.from_workload(wl), FieldTable(wl.times, wl.A, wl.B), wl.dt, psi0, bounds=bounds,
+               n_sc=kw.get("n_sc", wl.n_sc), exp_kind=kw.get("exp_kind", 0), exp_order=kw.get("exp_order", 0),
+               cheb_tol=kw.get("cheb_tol", 0) or (1e-16 if precision == 0 else 1e-9))
+    info = h.info()
+    assert (info["K_full"], info["K_half"]) == (o.K_full, o.K_half)
+    rows = []
+    for s in range(nsteps + 1):
+        if s > 0:
+            h.step(1)
+            o.step()
+        n_g, m_g, E_g, norms_g = h.observables()
+        n_o, m_o, E_o, norms_o = o.observables()
+        rows.append(dict(n=rel(n_g, n_o), m=rel(m_g, m_o), E=abs(E_g["total"] - E_o["total"]),
+                         Eg=E_g, Eo=E_o, norms=np.abs(norms_g - norms_o).max()))
+    psi_g = h.get_states()
+    h.close()
+    return rows, psi_g, o
+
+
+def test_tiny_config_full_run_fp64(lib):
+    """Tiny oracle case in full: 24^3, one atom, 4 spinors, 10 steps of dt = 0.05."""
+    wl = S.tiny()
+    psi0 = S.tiny_states(wl)
+    rows, psi_g, o = run_pair(lib, wl, psi0, wl.nsteps, (-16.0, 96.0))
+    for s, r in enumerate(rows):
+        assert r["n"] <= 1e-10 and r["m"] <= 1e-10, (s, r["n"], r["m"])
+        assert r["E"] <= 1e-8 * max(1, s), (s, r["E"])
+        for key in ("kin", "nl", "loc", "H", "xc", "Z", "xc_pot", "N"):
+            assert abs(r["Eg"][key] - r["Eo"][key]) <= 1e-8 * max(1, s) + 1e-12 * abs(r["Eo"][key]), key
+    assert rel(psi_g, o.psi) <= 1e-10
+
+
+@pytest.mark.parametrize("n,nstates,nk", [(16, 5, 2), (12, 3, 1), (24, 2, 1)])
+def test_multi_atom_soc_kpoints_fields_fp64(lib, n, nstates, nk):
+    """Several atoms with SOC, k-points, laser (velocity gauge) and static B; radix-2 and
+    radix-3 grids; odd state counts."""
+    wl = S.small_parity(n=n, nstates=nstates, nk=nk, natoms=3)
+    psi0 = S.small_parity_states(wl)
+    rows, psi_g, o = run_pair(lib, wl, psi0, 3, (-20.0, 0.6 * 3 * (math.pi * n / 9.0) ** 2 + 20.0))
+    for s, r in enumerate(rows):
+        assert r["n"] <= 1e-10 and r["m"] <= 1e-10, (s, r)
+        assert r["E"] <= 1e-8 * max(1, s)
+    assert rel(psi_g, o.psi) <= 1e-10
+
+
+def test_auto_spectral_window_and_orders_match_oracle(lib):
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=3, nk=2, natoms=3)
+    psi0 = S.small_parity_states(wl)
+    h = _lib.TDDFT.from_workload(wl)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi0)
+    info = h.info()
+    h.close()
+    o = Oracle(System.from_workload(wl), FieldTable(wl.times, wl.A, wl.B), wl.dt, psi0)
+    assert info["e_min"] == pytest.approx(o.emin, rel=1e-10)
+    assert info["e_max"] == pytest.approx(o.emax, rel=1e-10)
+    assert (info["K_full"], info["K_half"]) == (o.K_full, o.K_half)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
+def test_hamiltonian_apply_and_hermiticity(lib, precision, tol):
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=3, nk=2, natoms=3)
+    psi0 = S.small_parity_states(wl)
+    h = _lib.TDDFT.from_workload(wl, precision=precision, e_min=-20, e_max=100)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi0, 0.1)
+    rng = np.random.default_rng(11)
+    phi = (rng.normal(size=psi0.shape) + 1j * rng.normal(size=psi0.shape)) * 0.05
+    hpsi = h.apply_hamiltonian(psi0)
+    hphi = h.apply_hamiltonian(phi)
+    V = h.get_potential()
+    h.close()
+    s = System.from_workload(wl)
+    o = Oracle(s, FieldTable(wl.times, wl.A, wl.B), wl.dt, psi0, t0=0.1, bounds=(-20, 100))
+    A, _ = o.f.at(0.1)
+    assert rel(V, o.V) <= (1e-12 if precision == 0 else 1e-6)
+    assert rel(hpsi, s.apply_h(psi0, o.V, A)) <= tol
+    assert rel(hphi, s.apply_h(phi, o.V, A)) <= tol
+    for ik in range(wl.nk):
+        for i in range(wl.nstates):
+            a = np.vdot(phi[ik, i], hpsi[ik, i])
+            b = np.vdot(hphi[ik, i], psi0[ik, i])
+            assert abs(a - b) <= 10 * tol * abs(a)
+
+
+def test_fp32_mixed_step_tracks_oracle(lib):
+    wl = S.small_parity(n=16, nstates=5, nk=2, natoms=3)
+    psi0 = S.small_parity_states(wl)
+    rows, psi_g, o = run_pair(lib, wl, psi0, 3, (-20.0, 100.0), precision=1)
+    for r in rows:
+        assert r["n"] <= 2e-5 and r["m"] <= 2e-5, r
+        assert r["norms"] <= 1e-5
+
+
+def test_taylor_variant_fp64(lib):
+    wl = S.small_parity(n=12, nstates=3, nk=1, natoms=2)
+    wl.dt = 0.01
+    psi0 = S.small_parity_states(wl)
+    rows, psi_g, o = run_pair(lib, wl, psi0, 2, (-20.0, 100.0), exp_kind=1, exp_order=4)
+    for r in rows:
+        assert r["n"] <= 1e-10 and r["m"] <= 1e-10
+    assert rel(psi_g, o.psi) <= 1e-10
+
+
+def test_larmor_uniform_gas_gpu_closed_form(lib):
+    """No atoms (empty projector set), uniform spinor gas, static B, XC off: M precesses at
+    2 mu_B |B| (Eq. magrot), on the GPU, against the closed form."""
+    from paper_2506_21908_gb300 import _lib
+    from tests._systems import rotate
+    n, L = 8, 6.0
+    B = np.array([0.4, 0.0, 0.3])
+    times = np.arange(11) * 0.1
+    g = np.fft.fftfreq(n) * n * 2 * math.pi / L
+    iz, iy, ix = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.stack([ix, iy, iz], -1) * L / n
+    chi = S.spinor_along(0.6, 0.2)
+    psi = np.empty((1, 3, 2, n, n, n), np.complex128)
+    for i, G in enumerate([(0, 0, 0), (g[1], 0, 0), (0, g[2], g[1])]):
+        pw = np.exp(1j * (r @ np.array(G))) / math.sqrt(L ** 3)
+        psi[0, i, 0], psi[0, i, 1] = chi[0] * pw, chi[1] * pw
+    h = _lib.TDDFT([L] * 3, n, np.zeros((0, 3)), np.zeros(0, np.int32), [1.0], [1.0], [1.0], 0, [[0.0]], [[0.0]],
+                   1.0, np.zeros((1, 3)), [1.0], np.ones((1, 3)), 0.1, xc=0)
+    h.set_fields(times, np.zeros((11, 3)), np.tile(B, (11, 1)))
+    h.set_states(psi)
+    M0 = h.observables()[2]["M"]
+    for k in range(1, 9):
+        h.step(1)
+        M = h.observables()[2]["M"]
+        assert np.allclose(M, rotate(M0, B, np.linalg.norm(B) * k * 0.1), atol=1e-11)
+    h.close()
+
+
+def test_time_reversal_on_gpu(lib):
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=12, nstates=3, nk=1, natoms=2)
+    psi0 = S.small_parity_states(wl)
+    kw = dict(e_min=-20, e_max=100, n_sc=60, sc_tol=1e-14)
+    h = _lib.TDDFT.from_workload(wl, **kw)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi0, 0.0)
+    h.step(2)
+    psi2 = h.get_states()
+    h.close()
+    wl.dt = -wl.dt
+    h = _lib.TDDFT.from_workload(wl, **kw)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi2, 2 * abs(wl.dt))
+    h.step(2)
+    back = h.get_states()
+    h.close()
+    assert rel(back, psi0) <= 1e-10
+
+
+def test_error_paths_on_device(lib):
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=8, nstates=1, nk=1, natoms=1)
+    h = _lib.TDDFT.from_workload(wl)
+    with pytest.raises(_lib.TddftError) as e:
+        h.step(1)
+    assert e.value.status == -4
+    with pytest.raises(_lib.TddftError):
+        h.get_states()
+    h.close()

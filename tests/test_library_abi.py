@@ -1,0 +1,70 @@
+"""CPU checks of the C-ABI library: it loads, exports every entry point that
+include/tddft.h declares, and reports errors without a GPU (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tddft.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tddft_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def cpu_lib():
+    from paper_2506_21908_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2506_21908_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def test_header_declares_binding_exports():
+    from paper_2506_21908_gb300 import _lib
+    assert _declared() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(cpu_lib):
+    for name in _declared():
+        assert hasattr(cpu_lib, name), name
+
+
+def _gpu_present():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(_gpu_present(), reason="checks the no-device error path")
+def test_create_without_device_returns_error_not_crash(cpu_lib):
+    from paper_2506_21908_gb300 import _lib, synthetic as S
+    wl = S.small_parity(n=8, nstates=1, nk=1, natoms=1)
+    with pytest.raises(_lib.TddftError) as e:
+        _lib.TDDFT.from_workload(wl)
+    assert e.value.status in (-2, -3)
+    assert cpu_lib.tddft_last_error(None)
+
+
+def test_argument_validation_before_device_use(cpu_lib):
+    """Unsupported grids and cells are refused with a status, before any allocation."""
+    from paper_2506_21908_gb300 import _lib, synthetic as S
+    wl = S.small_parity(n=8, nstates=1, nk=1, natoms=1)
+    with pytest.raises(_lib.TddftError) as e:
+        _lib.TDDFT(wl.L, 10, wl.pos, wl.species, wl.Z, wl.rc_loc, wl.width, wl.lmax, wl.D, wl.lam, wl.r_cut,
+                   wl.kpts, wl.kw, wl.occ, wl.dt)
+    assert e.value.status == -7
+    with pytest.raises(_lib.TddftError) as e:
+        _lib.TDDFT(wl.L, 8, wl.pos, wl.species, wl.Z, wl.rc_loc, wl.width, wl.lmax, wl.D, wl.lam, 6.0,
+                   wl.kpts, wl.kw, wl.occ, wl.dt)
+    assert e.value.status == -1
+    with pytest.raises(_lib.TddftError) as e:
+        _lib.TDDFT(wl.L, 8, wl.pos, wl.species, wl.Z, wl.rc_loc, wl.width, 3, wl.D, wl.lam, wl.r_cut,
+                   wl.kpts, wl.kw, wl.occ, wl.dt)
+    assert e.value.status == -7
