@@ -200,8 +200,33 @@ tddft_status tddft_info(tddft_handle h, int* K_full, int* K_half, double* e_min,
 tddft_status tddft_profile(tddft_handle h, int enable);
 tddft_status tddft_profile_read(tddft_handle h, int ncls, double* ms, long long* count, double* bytes);
 
-/* Message describing the last failure on this handle (or the last failed create when
- * h is NULL).  The string stays valid until the next call on the handle. */
+/* Allocation-free Hartree (Poisson) solve; the paper has no counterpart to this entry
+ * point.  For callers that cannot allocate device memory -- code running during CUDA
+ * stream capture, frameworks that reserve all device memory up front, or loops that
+ * cannot afford an allocation's implicit synchronisation.
+ *
+ * Computes v_H(r) = sum_{G != 0} 4 pi n(G) / |G|^2 exp(i G.r) / N^3 (G = 0 term dropped), the
+ * same Hartree potential the library adds to V_v, for a real density n[N^3] on an n x n x n
+ * grid of the orthorhombic cell with side lengths L[3] (bohr).  n_dev and vH_dev are device
+ * pointers (FP64, [z][y][x]) on the current device; the caller owns both; work is queued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) and the call returns without
+ * synchronising.
+ *
+ * It allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  Its scratch
+ * is one file-scope static device array of 64^3 + 64 complex FP64 values (4 MiB + 1 KiB),
+ * present on every GPU that loads the library until the process exits.  Hence n must be one
+ * of 8, 12, 16, 24, 32, 48, 64; larger grids return TDDFT_ERR_ARG.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call on a device shares the array, so calls that overlap on the
+ * GPU (different streams, or host threads) race with each other; each call overwrites the
+ * part it uses before reading it, so nothing carries over from earlier calls.
+ * Errors: TDDFT_ERR_ARG (null pointer, unsupported n, non-positive L), TDDFT_ERR_CUDA;
+ * tddft_last_error(NULL) describes the failure. */
+tddft_status tddft_hartree_noalloc(const double* n_dev, double* vH_dev, int n, const double* L, void* stream);
+
+/* Message describing the last failure on this handle (or, when h is NULL, the last failed
+ * tddft_create or tddft_hartree_noalloc).  The string stays valid until the next call on
+ * the handle. */
 const char* tddft_last_error(tddft_handle h);
 
 /* Release the handle and all its device memory.  NULL is accepted. */

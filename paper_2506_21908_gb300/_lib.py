@@ -21,7 +21,8 @@ KERNEL_CLASSES = ["fft_xy", "fft_z_kinetic", "epilogue", "proj_gather", "density
 # Every entry point declared in include/tddft.h (checked by the CPU tests).
 EXPORTS = ["tddft_create", "tddft_set_fields", "tddft_set_states", "tddft_get_states", "tddft_step",
            "tddft_observables", "tddft_get_potential", "tddft_apply_hamiltonian", "tddft_set_stream",
-           "tddft_info", "tddft_profile", "tddft_profile_read", "tddft_last_error", "tddft_destroy"]
+           "tddft_info", "tddft_profile", "tddft_profile_read", "tddft_last_error", "tddft_destroy",
+           "tddft_hartree_noalloc"]
 
 
 class TddftError(RuntimeError):
@@ -82,6 +83,7 @@ def load(path=LIB_PATH):
         "tddft_info": [vp, vp, vp, vp, vp, vp],
         "tddft_profile": [vp, i],
         "tddft_profile_read": [vp, i, vp, vp, vp],
+        "tddft_hartree_noalloc": [vp, vp, i, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -262,3 +264,14 @@ class TDDFT:
             self.close()
         except Exception:
             pass
+
+
+def hartree_noalloc(n_dev, vH_dev, L, stream=None):
+    """Allocation-free Hartree solve on device tensors (float64, shape (n, n, n)), queued on
+    ``stream`` (a raw cudaStream_t value; None = legacy default stream)."""
+    lib = load()
+    n = int(n_dev.shape[-1])
+    L = _f64(L)
+    st = lib.tddft_hartree_noalloc(_ptr(n_dev), _ptr(vH_dev), n, _ptr(L), ctypes.c_void_p(stream or 0))
+    if st != 0:
+        raise TddftError(st, lib.tddft_last_error(None).decode())

@@ -152,6 +152,11 @@ int chebyshev_order(double z, double tol) {
 
 }  // namespace
 
+namespace tddft {
+// Message for failures that have no handle (tddft_create, tddft_hartree_noalloc).
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace tddft
+
 // =================================================================== context
 
 struct tddft_ctx {
