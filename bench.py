@@ -158,6 +158,9 @@ def run_ours(args):
 
     wl = cluster_workload(args.warmup + args.steps + 64)
     psi0 = make_states(wl)
+    if args.states:
+        psi0 = np.ascontiguousarray(psi0[:, :args.states])
+        wl.occ = wl.occ[:, :args.states]
     ups = wl.updates_per_step
     stream = torch.cuda.current_stream().cuda_stream
 
@@ -166,15 +169,13 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    from paper_2506_21908_gb300.replicas import aggregate
+
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return aggregate(0.0, x)[1]
 
     # ---------------- mixed precision (the headline)
-    h = _lib.TDDFT.from_workload(wl, precision=_lib.FP32_MIXED, stream=stream)
+    h = _lib.TDDFT.from_workload(wl, precision=_lib.FP32_MIXED, proj_mode=args.proj, stream=stream)
     h.set_fields(wl.times, wl.A, wl.B)
     psi_dev = torch.from_numpy(psi0).to("cuda")
     h.set_states(psi_dev, 0.0)
@@ -196,9 +197,9 @@ def run_ours(args):
     h.profile(False)
     launches = h.info()["launches"] - l0
     clocks = clk.stop()
-    ms = max_over_ranks(ms)
-    ms_step = ms / args.steps
-    value = ups * world / (ms_step / 1e3)
+    total_units, sec = aggregate(ups * args.steps, ms / 1e3)  # replicas: sum of units, max of time
+    ms_step = sec * 1e3 / args.steps
+    value = total_units / sec
     _, _, E_mixed, _ = h.observables(fields=False, check=False)
     M_mixed = E_mixed["M"]
 
@@ -268,6 +269,35 @@ def run_ours(args):
         fp64 = {"value": ups / (ms64 / 1e3), "ms_per_step": ms64, "speedup_mixed_vs_fp64": (ups / (ms_step / 1e3)) / (ups / (ms64 / 1e3)),
                 "dm_per_atom_muB": dm, "steps_compared": nst, "K_fp64": None}
 
+    # ---------------- adjoint gradient (differentiation workload, bounded horizon)
+    adjoint = None
+    if not args.no_adjoint:
+        from paper_2506_21908_gb300 import synthetic as S
+        from paper_2506_21908_gb300.autograd import MagnetizationFromPulse, PulseBasis, mz_seed
+        nst = args.adj_steps
+        dwl = S.cluster(n=48, nsteps=nst, laser=False)
+        dpsi = S.cluster_states(dwl)
+        basis = PulseBasis(dwl.times, 64, mode="laser", omega=0.057)
+        a0 = np.random.default_rng(20250624).uniform(0.0, 0.01, 64)
+        res = {}
+        for prec, name in ((_lib.FP32_MIXED, "fp32_mixed"), (_lib.FP64, "fp64")):
+            hd = _lib.TDDFT.from_workload(dwl, precision=prec, stream=stream)
+            a = torch.tensor(a0, requires_grad=True)
+            barrier()
+            t0 = time.perf_counter()
+            L = MagnetizationFromPulse.apply(a, hd, dpsi, basis, nst, mz_seed(48, dwl.L), args.adj_ckpt)
+            L.backward()
+            barrier()
+            dt_g = max_over_ranks(time.perf_counter() - t0)
+            res[name] = {"seconds": dt_g, "grad_per_s": 1.0 / dt_g, "loss": float(L.detach()),
+                         "grad_norm": float(a.grad.norm())}
+            hd.close()
+        g32 = None
+        adjoint = {"workload": "13-atom cluster, 48^3, 104 spinors, 64-sample laser envelope, L = M_z(T)",
+                   "steps": nst, "ckpt_every": args.adj_ckpt, "per_precision": res,
+                   "grad_per_s_500_steps_est": {k: 1.0 / (v["seconds"] * 500.0 / nst) for k, v in res.items()},
+                   "what": "forward + discrete-adjoint backward of the whole horizon, one 64-parameter gradient"}
+
     if rank != 0:
         return
     out = {
@@ -277,9 +307,11 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "precision": "FP32-mixed (c64 spinors/FFT/potential/projectors; "
                    "f64 density, XC, Hartree, energies)", "grid": 64, "spinors": 104, "K_full": info["K_full"],
                    "K_half": info["K_half"], "l2": "inputs larger than L2: 436 MB spinor array per pass",
+                   "projector_contraction": {1: "FP32 CUDA cores", 2: "TF32 tensor cores (tcgen05)",
+                                             3: "3xTF32 tensor cores (tcgen05)"}[args.proj],
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "fp64": fp64,
+        "clocks": clocks, "fp64": fp64, "adjoint": adjoint,
     }
     print(json.dumps(out))
     if dist is not None:
@@ -317,6 +349,13 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--proj", type=int, default=1,
+                    help="projector contraction: 1 FP32 CUDA cores, 2 TF32 tensor cores, 3 TF32x3 tensor cores")
+    ap.add_argument("--adj-steps", type=int, default=20)
+    ap.add_argument("--adj-ckpt", type=int, default=10)
+    ap.add_argument("--states", type=int, default=0,
+                    help="propagate only the first N spinors (small profiling case; not the headline)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -57,7 +57,10 @@ typedef enum {
 
 enum { TDDFT_FP64 = 0, TDDFT_FP32_MIXED = 1 };
 enum { TDDFT_EXP_CHEBYSHEV = 0, TDDFT_EXP_TAYLOR = 1 };
-enum { TDDFT_PROJ_FP64 = 0, TDDFT_PROJ_FP32 = 1 };
+/* Projector contraction: FP64 / FP32 on the CUDA cores, or on the tensor cores (tcgen05,
+ * FP32-mixed precision with lmax = 2) as one TF32 product or as the split 3 x TF32 product
+ * (hi*hi + hi*lo + lo*hi, close to FP32 accuracy); FP32 accumulation in every case. */
+enum { TDDFT_PROJ_FP64 = 0, TDDFT_PROJ_FP32 = 1, TDDFT_PROJ_TF32 = 2, TDDFT_PROJ_TF32X3 = 3 };
 
 /* Energies returned by tddft_observables, indices into E[TDDFT_NE]. */
 enum {
@@ -108,7 +111,9 @@ typedef struct {
 /* Run parameters.
  *   precision : TDDFT_FP64, or TDDFT_FP32_MIXED (spinors, FFTs, potential apply and projectors
  *               in FP32; density, XC, Hartree, energies and norms in FP64)
- *   proj_mode : TDDFT_PROJ_FP64 / TDDFT_PROJ_FP32 (ignored in FP64 precision)
+ *   proj_mode : TDDFT_PROJ_FP64 / TDDFT_PROJ_FP32 / TDDFT_PROJ_TF32 / TDDFT_PROJ_TF32X3 (the CUDA-core
+ *               modes follow the precision; the tensor-core modes need FP32-mixed and lmax = 2,
+ *               else TDDFT_ERR_UNSUPPORTED)
  *   nk, kpts[nk][3] (1/bohr, cartesian), kw[nk] (weights)
  *   nstates   : propagated spinors per k-point; occ[nk][nstates] occupations f
  *   dt        : time step (may be negative to run backwards)
@@ -181,6 +186,31 @@ tddft_status tddft_get_potential(tddft_handle h, double* V);
  * and A(t) at the current time; in and out may not alias.  A diagnostic of the operator
  * that tddft_step exponentiates. */
 tddft_status tddft_apply_hamiltonian(tddft_handle h, const void* in, void* out, int on_device);
+
+/* Discrete adjoint of the propagation (reverse mode).  Starting from the current state, runs
+ * nsteps forward steps (leaving the handle at the end state, as tddft_step would), evaluates
+ * L = sum_r dL_drho[c][r] rho_v[c](r) on the final spin density 4-vector rho_v =
+ * {rho_uu, rho_dd, Re rho_ud, Im rho_ud} (host array [4][N_g]; L = M_z = int m_z dV is
+ * dL_drho = dV {1, -1, 0, 0}), and returns loss = L and the exact derivatives of L with respect
+ * to every entry of the field table set by tddft_set_fields: dL_dA[nt][3], dL_dB[nt][3] (host;
+ * either may be NULL).  The derivative follows every operation of the forward step: both
+ * Chebyshev series (Clenshaw-type reverse recurrence reusing the Hamiltonian kernels), the
+ * potential's dependence on the density through Hartree and the locally collinear LSDA
+ * (analytic Jacobian), the velocity-gauge kinetic term and projector phases, and the Zeeman term.
+ * Memory: spinor copies at every ckpt_every-th step (checkpoints), ckpt_every copies for the
+ * recomputed segment, and one copy per Chebyshev term of a step, allocated for the call only.
+ * Requires Chebyshev exponentials, sc_tol = 0, and two z-slabs of the grid in shared memory
+ * (n <= 64 in FP64, n <= 96 in FP32-mixed); otherwise TDDFT_ERR_UNSUPPORTED.  The paper has no
+ * adjoint; the loss and parameterisation follow the differentiation workload of this library. */
+tddft_status tddft_backward(tddft_handle h, int nsteps, int ckpt_every, const double* dL_drho, double* loss,
+                            double* dL_dA, double* dL_dB);
+
+/* Per-atom magnetic moments and electron counts of the current state: m and n integrated over
+ * each atom's Voronoi cell (every grid point belongs to its nearest atom, minimum image, ties to
+ * the lowest index -- the NearestAtom rule of Algorithm 1).  M[natoms][3], N[natoms] host arrays
+ * (either may be NULL); the cells partition the cell, so the sums equal the totals of
+ * tddft_observables.  No-op without atoms. */
+tddft_status tddft_atom_moments(tddft_handle h, double* M, double* N);
 
 /* Use this CUDA stream (a cudaStream_t; NULL = legacy default stream) for all work. */
 tddft_status tddft_set_stream(tddft_handle h, void* stream);

@@ -333,6 +333,35 @@ class System:
             out[ik] = self.apply_kinetic(psi[ik], shift) + loc[ik] + self.apply_nonlocal(psi[ik], shift)
         return out
 
+    # ------------------------------------------------------- per-atom moments
+    def voronoi_owner(self):
+        """Nearest atom of every grid point (minimum image), Algorithm 1's NearestAtom rule;
+        equal distances go to the lowest atom index.  |d|^2 = (dx^2 + dy^2) + dz^2."""
+        r = self.grid.r.reshape(-1, 3)
+        best = np.full(r.shape[0], np.inf)
+        owner = np.zeros(r.shape[0], np.int64)
+        for a, R in enumerate(self.pos):
+            d = r - R
+            d = d - self.grid.L * np.round(d / self.grid.L)
+            d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+            closer = d2 < best
+            owner[closer] = a
+            best = np.where(closer, d2, best)
+        return owner
+
+    def atom_moments(self, rho):
+        """Integrals of m and n over each atom's Voronoi cell."""
+        n, m = self.n_m(rho)
+        owner = self.voronoi_owner()
+        na = len(self.pos)
+        M = np.zeros((na, 3))
+        N = np.zeros(na)
+        for a in range(na):
+            sel = owner == a
+            M[a] = m.reshape(3, -1)[:, sel].sum(axis=1) * self.grid.dV
+            N[a] = n.reshape(-1)[sel].sum() * self.grid.dV
+        return M, N
+
     # --------------------------------------------------------------- energies
     def inner(self, a, b):
         return np.vdot(a, b) * self.grid.dV

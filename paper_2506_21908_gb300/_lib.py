@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtddft.so")
 
 FP64, FP32_MIXED = 0, 1
+PROJ_FP64, PROJ_FP32, PROJ_TF32, PROJ_TF32X3 = 0, 1, 2, 3
 EXP_CHEBYSHEV, EXP_TAYLOR = 0, 1
 E_NAMES = ["kin", "nl", "loc", "H", "xc", "Z", "total", "t", "xc_pot", "N"]
 KERNEL_CLASSES = ["fft_xy", "fft_z_kinetic", "epilogue", "proj_gather", "density", "potential", "other"]
@@ -22,7 +23,7 @@ KERNEL_CLASSES = ["fft_xy", "fft_z_kinetic", "epilogue", "proj_gather", "density
 EXPORTS = ["tddft_create", "tddft_set_fields", "tddft_set_states", "tddft_get_states", "tddft_step",
            "tddft_observables", "tddft_get_potential", "tddft_apply_hamiltonian", "tddft_set_stream",
            "tddft_info", "tddft_profile", "tddft_profile_read", "tddft_last_error", "tddft_destroy",
-           "tddft_hartree_noalloc"]
+           "tddft_hartree_noalloc", "tddft_backward", "tddft_atom_moments"]
 
 
 class TddftError(RuntimeError):
@@ -84,6 +85,8 @@ def load(path=LIB_PATH):
         "tddft_profile": [vp, i],
         "tddft_profile_read": [vp, i, vp, vp, vp],
         "tddft_hartree_noalloc": [vp, vp, i, vp, vp],
+        "tddft_backward": [vp, i, i, vp, vp, vp, vp],
+        "tddft_atom_moments": [vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -156,6 +159,9 @@ class TDDFT:
         self.nk = len(kpts)
         self.nstates = occ.shape[1]
         self.precision = precision
+        self._nt = 0
+        self._L = L
+        self._natoms = len(pos)
         if stream is not None:
             self.set_stream(stream)
 
@@ -179,6 +185,7 @@ class TDDFT:
     def set_fields(self, times, A, B):
         times, A, B = _f64(times), _f64(A).reshape(-1, 3), _f64(B).reshape(-1, 3)
         self._check(self.lib.tddft_set_fields(self.h, len(times), _ptr(times), _ptr(A), _ptr(B)))
+        self._nt = len(times)
 
     @staticmethod
     def _is_dev(x):
@@ -234,6 +241,25 @@ class TDDFT:
         assert odev == dev
         self._check(self.lib.tddft_apply_hamiltonian(self.h, _ptr(arr), _ptr(oarr), dev))
         return out
+
+    def backward(self, nsteps, dL_drho, ckpt_every=50, nt=None):
+        """Run nsteps forward and the discrete adjoint; returns (L, dL/dA table, dL/dB table)."""
+        dL = _f64(dL_drho).reshape(4, -1)
+        nt = self._nt if nt is None else nt
+        dA = np.zeros((max(nt, 1), 3))
+        dB = np.zeros((max(nt, 1), 3))
+        L = ctypes.c_double()
+        self._check(self.lib.tddft_backward(self.h, int(nsteps), int(ckpt_every), _ptr(dL), ctypes.byref(L),
+                                            _ptr(dA), _ptr(dB)))
+        return L.value, dA[:nt], dB[:nt]
+
+    def atom_moments(self):
+        """Per-atom (Voronoi cell) magnetic moments [natoms][3] and electron counts [natoms]."""
+        na = self._natoms
+        M = np.zeros((max(na, 1), 3))
+        N = np.zeros(max(na, 1))
+        self._check(self.lib.tddft_atom_moments(self.h, _ptr(M), _ptr(N)))
+        return M[:na], N[:na]
 
     def info(self):
         kf, kh = ctypes.c_int(), ctypes.c_int()

@@ -13,6 +13,7 @@
 //   series 2: psi(t+dt) = Exp(-i dt/2 H[rho~, t+dt]) phi, repeated n_sc times with the
 //             corrected density, then rho(t+dt), V(t+dt).
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -178,6 +179,7 @@ struct tddft_ctx {
   double t = 0, emin = 0, emax = 0, nl_bound = 0, kin_max = 0;
   int K_full = 0, K_half = 0;
   std::vector<cd> cf_full, cf_half;
+  bool use_fused = false;  // fused term kernel (where two planes fit in shared memory)
   // device memory
   cudaStream_t st = nullptr;
   std::vector<void*> allocs;
@@ -185,6 +187,7 @@ struct tddft_ctx {
   void *cbuf = nullptr, *dcbuf = nullptr, *tw = nullptr;
   double2 *tw64 = nullptr, *hart = nullptr, *stage = nullptr;
   size_t stage_elems = 0;
+  double* rho_part = nullptr;  // band-group partial densities
   double *rho = nullptr, *rho2 = nullptr, *rho3 = nullptr, *V = nullptr, *Vnew = nullptr, *vloc = nullptr,
          *vH = nullptr, *exc = nullptr, *vxc4 = nullptr, *wf_d = nullptr, *red = nullptr, *Bd = nullptr;
   float *Vf = nullptr, *Vnewf = nullptr;
@@ -192,6 +195,10 @@ struct tddft_ctx {
   // projector tables (typed views over the raw allocations)
   int *g_ptr = nullptr, *g_idx = nullptr, *s_ptr = nullptr, *s_atom = nullptr;
   size_t n_entries = 0;
+  int* owner = nullptr;      // nearest atom of each grid point (per-atom moments)
+  double* atom_sums = nullptr;
+  float* tc_part = nullptr;  // tensor-core gather partial products
+  int* tc_err = nullptr;     // set when a tensor-core wait gave up
   void *g_tab = nullptr, *s_tab = nullptr, *Dmat = nullptr;
   // bookkeeping
   std::string err;
@@ -480,7 +487,9 @@ tddft_status potential(tddft_ctx* c, const double* rho, double tt, double* Vout,
 
 template <typename R> tddft_status density(tddft_ctx* c, const void* psi, double* rho) {
   const double by = (double)c->psi_elems() * 2 * sizeof(R) + 4.0 * c->N3 * sizeof(double);
-  return c->launch(KC_DENS, "density", [&] { return launch_density<R>(c->st, c->N3, psi, c->nkb, c->wf_d, rho); }, by);
+  return c->launch(KC_DENS, "density", [&] {
+    return launch_density<R>(c->st, c->N3, psi, c->nkb, c->wf_d, rho, c->rho_part);
+  }, by);
 }
 
 tddft_status window_check(tddft_ctx* c, const double* V) {
@@ -522,16 +531,83 @@ template <typename R> tddft_status gather(tddft_ctx* c, const void* in, const do
   fill_shifts(c, A, ep.shift);
   ProjTables<R> pt = c->tables<R>();
   const double by = (double)c->n_entries * c->nkb * 2 * 2 * sizeof(R);  // psi at the sphere points
+  if (c->prec != TDDFT_FP64 && c->proj_mode >= TDDFT_PROJ_TF32) {
+    ProjTables<float> pf = c->tables<float>();
+    return c->launch(KC_PROJ, "projector gather (tensor cores)", [&] {
+      return launch_proj_gather_tc(c->st, c->N, in, c->nk, c->nb, pf, c->dV, ep,
+                                   c->proj_mode == TDDFT_PROJ_TF32X3 ? 1 : 0, c->tc_part, c->cbuf, c->dcbuf,
+                                   c->tc_err);
+    }, by);
+  }
   return c->launch(KC_PROJ, "projector gather", [&] {
     return launch_proj_gather<R>(c->st, c->N, in, c->nkb, pt, c->dV, ep, c->cbuf, c->dcbuf);
   }, by);
 }
 
+// Fused form of one Chebyshev series: per term a projector gather of T_k, the z pass with the
+// kinetic multiply (tmp holds the xy transform of T_k), and one fused kernel that finishes the
+// inverse transform, applies the potential and projectors, updates T_{k+1} and the
+// accumulators and leaves the xy transform of T_{k+1} in tmp.
+template <typename R>
+tddft_status cheb_series_fused(tddft_ctx* c, const void* in, const R* Vr, const double A[3], void* acc1,
+                               const std::vector<cd>& cf1, int K1, void* acc2, const std::vector<cd>& cf2, int K2,
+                               EpiParams ep, void* const* slots) {
+  const int K = std::max(K1, acc2 ? K2 : 0);
+  ZParams zp{};
+  const double pi = 3.14159265358979323846;
+  for (int a = 0; a < 3; ++a) zp.gs[a] = 2.0 * pi / c->L[a];
+  zp.scale = 1.0 / (double)c->N3;
+  zp.comps_per_k = 2 * c->nb;
+  fill_shifts(c, A, zp.shift);
+  const int nbatch = 2 * c->nkb;
+  const double pass = (double)c->psi_elems() * 2 * sizeof(R);  // one read or write of a spinor array
+  ProjTables<R> pt = c->tables<R>();
+  tddft_status s;
+  if ((s = c->launch(KC_FFT_XY, "fft xy", [&] { return launch_fft_xy<R>(c->st, c->N, in, c->tmp, nbatch, c->tw, false); }, 2 * pass)))
+    return s;
+  const void* prev = in;
+  const void* cur = in;
+  for (int k = 0; k < K; ++k) {
+    if ((s = gather<R>(c, cur, A))) return s;
+    if ((s = c->launch(KC_FFT_Z, "fft z", [&] { return launch_fft_z<R>(c->st, c->N, c->tmp, nbatch, c->tw, Z_KIN, zp); }, 2 * pass)))
+      return s;
+    void* out;
+    if (slots) out = slots[k + 1];
+    else if (k == 0) out = c->Ta;
+    else if (prev == in) out = (cur == c->Ta) ? c->Tb : c->Ta;
+    else out = const_cast<void*>(prev);
+    ep.mode = (k == 0) ? EPI_FIRST : EPI_RECUR;
+    ep.use_acc1 = (k + 1 <= K1);
+    ep.use_acc2 = (acc2 != nullptr && k + 1 <= K2);
+    if (ep.use_acc1) {
+      ep.a0[0] = cf1[0].real(); ep.a0[1] = cf1[0].imag();
+      ep.a1[0] = cf1[k + 1].real(); ep.a1[1] = cf1[k + 1].imag();
+    }
+    if (ep.use_acc2) {
+      ep.b0[0] = cf2[0].real(); ep.b0[1] = cf2[0].imag();
+      ep.b1[0] = cf2[k + 1].real(); ep.b1[1] = cf2[k + 1].imag();
+    }
+    const int do_fwd = (k + 1 < K) ? 1 : 0;
+    const int nacc = ep.use_acc1 + ep.use_acc2;
+    const double streams = 3.0 + (k == 0 ? 0.0 : 1.0) + do_fwd + nacc * (k == 0 ? 1.0 : 2.0);
+    const void* tkm1 = (k == 0) ? nullptr : prev;
+    if ((s = c->launch(KC_EPI, "fused chebyshev term", [&] {
+           return launch_fused_term<R>(c->st, c->N, c->tmp, cur, tkm1, out, acc1, acc2, Vr, pt, c->dcbuf, c->nkb,
+                                       c->tw, ep, do_fwd);
+         }, streams * pass + 4.0 * c->N3 * sizeof(R))))
+      return s;
+    prev = cur;
+    cur = out;
+  }
+  return TDDFT_OK;
+}
+
 // One Chebyshev series: T_k of H~ = (H - c)/Delta applied to `in`, accumulated with
 // coefficients cf1 (orders 0..K1) into acc1 and, when acc2 is set, cf2 (0..K2) into acc2.
 template <typename R>
-tddft_status cheb_series(tddft_ctx* c, const void* in, bool vcur, const double A[3], void* acc1,
-                         const std::vector<cd>& cf1, int K1, void* acc2, const std::vector<cd>& cf2, int K2) {
+tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double A[3], void* acc1,
+                         const std::vector<cd>& cf1, int K1, void* acc2, const std::vector<cd>& cf2, int K2,
+                         void* const* slots = nullptr) {
   const int K = std::max(K1, acc2 ? K2 : 0);
   EpiParams ep{};
   ep.c = 0.5 * (c->emax + c->emin);
@@ -539,15 +615,17 @@ tddft_status cheb_series(tddft_ctx* c, const void* in, bool vcur, const double A
   ep.nstates = c->nb;
   fill_shifts(c, A, ep.shift);
   ProjTables<R> pt = c->tables<R>();
-  const R* Vr = vsel<R>(c, vcur);
   const void* prev = in;
   const void* cur = in;
   tddft_status s;
+  if (c->use_fused && fused_supported<R>(c->N))
+    return cheb_series_fused<R>(c, in, Vr, A, acc1, cf1, K1, acc2, cf2, K2, ep, slots);
   for (int k = 0; k < K; ++k) {
     if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
     if ((s = gather<R>(c, cur, A))) return s;
     void* out;
-    if (k == 0) out = c->Ta;
+    if (slots) out = slots[k + 1];
+    else if (k == 0) out = c->Ta;
     else if (prev == in) out = (cur == c->Ta) ? c->Tb : c->Ta;
     else out = const_cast<void*>(prev);
     ep.mode = (k == 0) ? EPI_FIRST : EPI_RECUR;
@@ -613,7 +691,9 @@ template <typename R> tddft_status one_step(tddft_ctx* c) {
   float* Vcf = c->prec == TDDFT_FP64 ? nullptr : c->Vf;
   tddft_status s;
   if (c->exp_kind == TDDFT_EXP_CHEBYSHEV) {
-    if ((s = cheb_series<R>(c, c->psi, true, A0, c->pred, c->cf_full, c->K_full, c->phi, c->cf_half, c->K_half))) return s;
+    if ((s = cheb_series<R>(c, c->psi, vsel<R>(c, true), A0, c->pred, c->cf_full, c->K_full, c->phi, c->cf_half,
+                            c->K_half)))
+      return s;
   } else {
     if ((s = taylor_series<R>(c, c->psi, true, A0, c->dt, c->K_full, c->pred))) return s;
     if ((s = taylor_series<R>(c, c->psi, true, A0, 0.5 * c->dt, c->K_half, c->phi))) return s;
@@ -623,7 +703,7 @@ template <typename R> tddft_status one_step(tddft_ctx* c) {
   if ((s = window_check(c, c->Vnew))) return s;
   auto half = [&]() -> tddft_status {
     if (c->exp_kind == TDDFT_EXP_CHEBYSHEV)
-      return cheb_series<R>(c, c->phi, false, A1, c->psi, c->cf_half, c->K_half, nullptr, c->cf_half, 0);
+      return cheb_series<R>(c, c->phi, vsel<R>(c, false), A1, c->psi, c->cf_half, c->K_half, nullptr, c->cf_half, 0);
     return taylor_series<R>(c, c->phi, false, A1, 0.5 * c->dt, c->K_half, c->psi);
   };
   if ((s = half())) return s;
@@ -648,6 +728,416 @@ template <typename R> tddft_status one_step(tddft_ctx* c) {
   if ((s = potential(c, c->rho, t1, c->V, Vcf))) return s;
   if ((s = window_check(c, c->V))) return s;
   c->t = t1;
+  return TDDFT_OK;
+}
+
+// =================================================================== discrete adjoint
+// Reverse mode of one_step with the cotangent convention dL = Re sum conj(xbar) dx.  The forward
+// internals of each step are recomputed from the stored psi_n with every Chebyshev term kept;
+// the Chebyshev series are reversed with the Clenshaw-type recurrence
+//   S_k = conj(a_k) ybar + f (H - c)/Delta S_{k+1} - S_{k+2},  f = 2 (k >= 1), 1 (k = 0),
+// and dH enters through the pairs Re<S_{k+1}, f/Delta dH T_k>.
+
+struct DevBuf {  // temporary device allocations owned by one backward call
+  std::vector<void*> p;
+  ~DevBuf() {
+    for (void* q : p) cudaFree(q);
+  }
+};
+
+template <typename T> tddft_status tmp_alloc(tddft_ctx* c, DevBuf& db, T** out, size_t bytes, const char* what) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    c->err = std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e);
+    return TDDFT_ERR_OOM;
+  }
+  db.p.push_back(q);
+  *out = (T*)q;
+  return TDDFT_OK;
+}
+
+struct AdjWork {
+  std::vector<void*> slots1;               // T_1..T_K1 of series 1 (index 0 unused)
+  std::vector<std::vector<void*>> slots2;  // per half-step pass: T_1..T_Kh
+  std::vector<void*> outs;                 // psi^(j) of pass j
+  void *pred = nullptr, *phi = nullptr, *Sa = nullptr, *Sb = nullptr, *tmp2 = nullptr;
+  void *PB = nullptr, *YB = nullptr, *PHIB = nullptr;
+  double *rho_n = nullptr, *V_n = nullptr;
+  float* Vf_n = nullptr;
+  std::vector<double*> rhos, Vs;
+  std::vector<float*> Vfs;
+  double *gV = nullptr, *rbar = nullptr, *gvf = nullptr, *gbf = nullptr, *part = nullptr, *agrad = nullptr;
+  void *cS = nullptr, *dcS = nullptr, *mS = nullptr, *cT = nullptr, *dcT = nullptr, *mT = nullptr;
+  size_t ncoef = 0;
+};
+
+template <typename R> const R* vptr(tddft_ctx* c, double* Vd, float* Vf) {
+  return c->prec == TDDFT_FP64 ? (const R*)Vd : (const R*)(const void*)Vf;
+}
+
+template <typename R>
+tddft_status gather_into(tddft_ctx* c, const void* in, const double A[3], void* cb, void* dcb) {
+  if (c->natoms == 0) return TDDFT_OK;
+  EpiParams ep{};
+  ep.nstates = c->nb;
+  fill_shifts(c, A, ep.shift);
+  ProjTables<R> pt = c->tables<R>();
+  return c->launch(KC_PROJ, "adjoint gather", [&] {
+    return launch_proj_gather<R>(c->st, c->N, in, c->nkb, pt, c->dV, ep, cb, dcb);
+  });
+}
+
+template <typename R>
+tddft_status gather_moments(tddft_ctx* c, const void* in, const double A[3], void* mb, size_t ncoef) {
+  if (c->natoms == 0) return TDDFT_OK;
+  EpiParams ep{};
+  ep.nstates = c->nb;
+  fill_shifts(c, A, ep.shift);
+  ProjTables<R> pt = c->tables<R>();
+  for (int a = 0; a < 3; ++a) {
+    void* dst = (char*)mb + (size_t)a * ncoef * 2 * sizeof(R);
+    tddft_status s = c->launch(KC_PROJ, "adjoint moments", [&] {
+      return launch_proj_gather_mom<R>(c->st, c->N, in, c->nkb, pt, c->dV, ep, a, dst);
+    });
+    if (s) return s;
+  }
+  return TDDFT_OK;
+}
+
+// Reverse of one Chebyshev series with terms T[0..K-1]; seeds (y1, a1 up to K1), (y2, a2 up to K2).
+// Accumulates the potential gradient into w.gV, the A-gradient into gA[3]; returns S_0 in *xbar.
+template <typename R>
+tddft_status cheb_adjoint(tddft_ctx* c, AdjWork& w, const std::vector<const void*>& T, int K, const void* y1,
+                          const std::vector<cd>& a1, int K1, const void* y2, const std::vector<cd>& a2, int K2,
+                          const R* Vr, const double A[3], double gA[3], void** xbar) {
+  EpiParams ep{};
+  ep.c = 0.5 * (c->emax + c->emin);
+  ep.inv_delta = 1.0 / (0.5 * (c->emax - c->emin));
+  ep.nstates = c->nb;
+  fill_shifts(c, A, ep.shift);
+  ZParams zp{};
+  const double pi = 3.14159265358979323846;
+  for (int a = 0; a < 3; ++a) zp.gs[a] = 2.0 * pi / c->L[a];
+  zp.scale = 1.0 / (double)c->N3;
+  zp.comps_per_k = 2 * c->nb;
+  fill_shifts(c, A, zp.shift);
+  ProjTables<R> pt = c->tables<R>();
+  const int nbatch = 2 * c->nkb;
+  const size_t n = c->psi_elems();
+  tddft_status s;
+  auto coef = [&](int k, double* ca, double* cb, int* u1, int* u2) {
+    *u1 = (y1 && k <= K1) ? 1 : 0;
+    *u2 = (y2 && k <= K2) ? 1 : 0;
+    ca[0] = ca[1] = cb[0] = cb[1] = 0.0;
+    if (*u1) { ca[0] = a1[k].real(); ca[1] = -a1[k].imag(); }
+    if (*u2) { cb[0] = a2[k].real(); cb[1] = -a2[k].imag(); }
+  };
+  if ((s = c->cuda(cudaMemsetAsync(w.agrad, 0, (3 * (size_t)c->nkb + 3) * sizeof(double), c->st), "agrad reset")))
+    return s;
+  double* agk = w.agrad + 3 * (size_t)c->nkb;  // kinetic part
+  {
+    double ca[2], cb[2];
+    int u1, u2;
+    coef(K, ca, cb, &u1, &u2);
+    if ((s = c->launch(KC_OTHER, "adjoint seed", [&] {
+           return launch_seed<R>(c->st, n, u1 ? y1 : nullptr, ca, u2 ? y2 : nullptr, cb, w.Sa);
+         })))
+      return s;
+  }
+  void* cur = w.Sa;
+  void* prev2 = nullptr;
+  for (int k = K - 1; k >= 0; --k) {
+    const void* Tk = T[k];
+    const double f = (k >= 1 ? 2.0 : 1.0) * ep.inv_delta;
+    if ((s = c->launch(KC_OTHER, "grad V", [&] { return launch_grad_v<R>(c->st, c->N3, c->nkb, cur, Tk, f, w.gV); })))
+      return s;
+    if ((s = c->launch(KC_FFT_XY, "adj fft xy", [&] { return launch_fft_xy<R>(c->st, c->N, cur, c->tmp, nbatch, c->tw, false); }))) return s;
+    if ((s = c->launch(KC_FFT_XY, "adj fft xy T", [&] { return launch_fft_xy<R>(c->st, c->N, Tk, w.tmp2, nbatch, c->tw, false); }))) return s;
+    if ((s = c->launch(KC_FFT_Z, "adj fft z current", [&] {
+           return launch_fft_z_current<R>(c->st, c->N, c->tmp, w.tmp2, nbatch, c->tw, zp, w.part);
+         })))
+      return s;
+    if ((s = c->launch(KC_OTHER, "adj current sum", [&] {
+           return launch_accum_parts(c->st, (size_t)nbatch * c->N, w.part, f / (double)c->N3, agk);
+         })))
+      return s;
+    if ((s = c->launch(KC_FFT_XY, "adj ifft xy", [&] { return launch_fft_xy<R>(c->st, c->N, c->tmp, c->tmp, nbatch, c->tw, true); }))) return s;
+    if (c->natoms > 0) {
+      if ((s = gather_into<R>(c, cur, A, w.cS, w.dcS)) || (s = gather_moments<R>(c, cur, A, w.mS, w.ncoef)) ||
+          (s = gather_into<R>(c, Tk, A, w.cT, w.dcT)) || (s = gather_moments<R>(c, Tk, A, w.mT, w.ncoef)))
+        return s;
+      const int per = c->natoms * 2 * c->nlm;
+      if ((s = c->launch(KC_OTHER, "adj nl agrad", [&] {
+             return launch_nl_agrad<R>(c->st, c->nkb, per, w.mS, w.dcT, w.dcS, w.mT, w.ncoef, 1.0 / c->dV, f, w.agrad);
+           })))
+        return s;
+    }
+    void* out = prev2 ? prev2 : (cur == w.Sa ? w.Sb : w.Sa);
+    double ca[2], cb[2];
+    int u1, u2;
+    coef(k, ca, cb, &u1, &u2);
+    ep.mode = (k >= 1) ? EPI_ADJ : EPI_ADJ0;
+    ep.use_acc1 = u1;
+    ep.use_acc2 = u2;
+    ep.a1[0] = ca[0]; ep.a1[1] = ca[1];
+    ep.b1[0] = cb[0]; ep.b1[1] = cb[1];
+    const void* s2 = prev2;
+    if ((s = c->launch(KC_EPI, "adjoint epilogue", [&] {
+           return launch_epilogue<R>(c->st, c->N, c->tmp, cur, s2, out, const_cast<void*>(y1), const_cast<void*>(y2), Vr,
+                                     pt, w.dcS, c->nkb, ep);
+         })))
+      return s;
+    prev2 = cur;
+    cur = out;
+  }
+  *xbar = cur;
+  std::vector<double> h(3 * (size_t)c->nkb + 3);
+  if ((s = c->cuda(cudaMemcpyAsync(h.data(), w.agrad, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st), "agrad read")))
+    return s;
+  if ((s = c->cuda(cudaStreamSynchronize(c->st), "agrad sync"))) return s;
+  for (int kb = 0; kb < c->nkb; ++kb)
+    for (int a = 0; a < 3; ++a) gA[a] += h[3 * kb + a];
+  for (int a = 0; a < 3; ++a) gA[a] += h[3 * (size_t)c->nkb + a];
+  return TDDFT_OK;
+}
+
+// rhobar and dL/dB from w.gV (cotangent of V_v) at density rho: XC Jacobian-transpose,
+// Hartree (symmetric convolution) and the uniform Zeeman coupling mu_B B.sigma.
+tddft_status potential_adjoint(tddft_ctx* c, AdjWork& w, const double* rho, double gB[3]) {
+  tddft_status s;
+  ZParams zp{};
+  const double pi = 3.14159265358979323846;
+  for (int a = 0; a < 3; ++a) zp.gs[a] = 2.0 * pi / c->L[a];
+  zp.scale = 1.0 / (double)c->N3;
+  if ((s = c->launch(KC_POT, "xc adjoint", [&] { return launch_xc_adjoint(c->st, c->N3, rho, w.gV, c->xc, w.rbar, w.gvf, w.gbf); }))) return s;
+  if ((s = c->launch(KC_POT, "hartree adj in", [&] { return launch_real_field_to_complex(c->st, c->N3, w.gvf, c->hart); }))) return s;
+  if ((s = c->launch(KC_POT, "hartree adj xy", [&] { return launch_fft_xy<double>(c->st, c->N, c->hart, c->hart, 1, c->tw64, false); }))) return s;
+  if ((s = c->launch(KC_POT, "hartree adj z", [&] { return launch_fft_z<double>(c->st, c->N, c->hart, 1, c->tw64, Z_POISSON, zp); }))) return s;
+  if ((s = c->launch(KC_POT, "hartree adj ixy", [&] { return launch_fft_xy<double>(c->st, c->N, c->hart, c->hart, 1, c->tw64, true); }))) return s;
+  if ((s = c->launch(KC_POT, "hartree adj add", [&] { return launch_add_hartree_adjoint(c->st, c->N3, c->hart, w.rbar); }))) return s;
+  if ((s = c->launch(KC_POT, "b sums", [&] { return launch_sum3(c->st, c->N3, w.gbf, c->red); }))) return s;
+  double h[3];
+  if ((s = c->cuda(cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->st), "b read"))) return s;
+  if ((s = c->cuda(cudaStreamSynchronize(c->st), "b sync"))) return s;
+  for (int a = 0; a < 3; ++a) gB[a] += 0.5 * h[a];  // mu_B = 1/2
+  return TDDFT_OK;
+}
+
+template <typename R>
+tddft_status density_adj(tddft_ctx* c, const void* psi, const double* rbar, const void* add, void* out) {
+  return c->launch(KC_DENS, "density adjoint", [&] {
+    return launch_density_adjoint<R>(c->st, c->N3, c->nkb, psi, rbar, c->wf_d, add, out);
+  });
+}
+
+// w.PB holds psibar_{n+1} on entry and psibar_n on exit; gradients with respect to A, B at
+// t0 and t0 + dt are added to gA0, gB0, gA1, gB1.
+template <typename R>
+tddft_status adjoint_step(tddft_ctx* c, AdjWork& w, const void* psi_n, double t0, double gA0[3], double gB0[3],
+                          double gA1[3], double gB1[3]) {
+  const double t1 = t0 + c->dt;
+  double A0[3], B0[3], A1[3], B1[3];
+  c->field_at(t0, A0, B0);
+  c->field_at(t1, A1, B1);
+  const bool f64 = c->prec == TDDFT_FP64;
+  const int K1 = std::max(c->K_full, c->K_half), Kh = c->K_half;
+  const size_t n = c->psi_elems();
+  tddft_status s;
+  // ---- recompute the step, keeping every term
+  if ((s = density<R>(c, psi_n, w.rho_n)) || (s = potential(c, w.rho_n, t0, w.V_n, f64 ? nullptr : w.Vf_n))) return s;
+  if ((s = cheb_series<R>(c, psi_n, vptr<R>(c, w.V_n, w.Vf_n), A0, w.pred, c->cf_full, c->K_full, w.phi, c->cf_half,
+                          c->K_half, w.slots1.data())))
+    return s;
+  const void* src = w.pred;
+  for (int j = 0; j <= c->n_sc; ++j) {
+    if ((s = density<R>(c, src, w.rhos[j])) || (s = potential(c, w.rhos[j], t1, w.Vs[j], f64 ? nullptr : w.Vfs[j]))) return s;
+    if ((s = cheb_series<R>(c, w.phi, vptr<R>(c, w.Vs[j], w.Vfs[j]), A1, w.outs[j], c->cf_half, Kh, nullptr, c->cf_half,
+                            0, w.slots2[j].data())))
+      return s;
+    src = w.outs[j];
+  }
+  // ---- reverse through the half-step passes at t + dt
+  const void* ybar = w.PB;
+  bool have_phibar = false;
+  for (int j = c->n_sc; j >= 0; --j) {
+    if ((s = c->cuda(cudaMemsetAsync(w.gV, 0, 4 * c->N3 * sizeof(double), c->st), "gV reset"))) return s;
+    std::vector<const void*> T(Kh);
+    T[0] = w.phi;
+    for (int k = 1; k < Kh; ++k) T[k] = w.slots2[j][k];
+    void* xbar = nullptr;
+    if ((s = cheb_adjoint<R>(c, w, T, Kh, ybar, c->cf_half, Kh, nullptr, c->cf_half, -1, vptr<R>(c, w.Vs[j], w.Vfs[j]),
+                             A1, gA1, &xbar)))
+      return s;
+    const double one[2] = {1.0, 0.0};
+    if ((s = c->launch(KC_OTHER, "phibar", [&] {
+           return launch_seed<R>(c->st, n, have_phibar ? w.PHIB : nullptr, one, xbar, one, w.PHIB);
+         })))
+      return s;
+    have_phibar = true;
+    if ((s = potential_adjoint(c, w, w.rhos[j], gB1))) return s;
+    const void* srcj = (j == 0) ? w.pred : w.outs[j - 1];
+    if ((s = density_adj<R>(c, srcj, w.rbar, nullptr, w.YB))) return s;
+    ybar = w.YB;
+  }
+  // ---- reverse through series 1 (shared terms for psi~ and phi) at t
+  if ((s = c->cuda(cudaMemsetAsync(w.gV, 0, 4 * c->N3 * sizeof(double), c->st), "gV reset"))) return s;
+  std::vector<const void*> T(K1);
+  T[0] = psi_n;
+  for (int k = 1; k < K1; ++k) T[k] = w.slots1[k];
+  void* xbar = nullptr;
+  if ((s = cheb_adjoint<R>(c, w, T, K1, w.YB, c->cf_full, c->K_full, w.PHIB, c->cf_half, c->K_half,
+                           vptr<R>(c, w.V_n, w.Vf_n), A0, gA0, &xbar)))
+    return s;
+  if ((s = potential_adjoint(c, w, w.rho_n, gB0))) return s;
+  return density_adj<R>(c, psi_n, w.rbar, xbar, w.PB);
+}
+
+// Lerp weights of the field table at time tt, matching field_at.
+void table_weights(const tddft_ctx* c, double tt, int* j0, double* w0, int* j1, double* w1) {
+  const int nt = (int)c->ft.size();
+  *j0 = *j1 = 0;
+  *w0 = *w1 = 0.0;
+  if (nt == 0) return;
+  if (tt <= c->ft[0] || nt == 1) { *j0 = 0; *w0 = 1.0; return; }
+  if (tt >= c->ft[nt - 1]) { *j0 = nt - 1; *w0 = 1.0; return; }
+  const int j = (int)(std::upper_bound(c->ft.begin(), c->ft.end(), tt) - c->ft.begin());
+  const double a = (tt - c->ft[j - 1]) / (c->ft[j] - c->ft[j - 1]);
+  *j0 = j - 1; *w0 = 1.0 - a; *j1 = j; *w1 = a;
+}
+
+void add_table(const tddft_ctx* c, double tt, const double gA[3], const double gB[3], double* dA, double* dB) {
+  int j0, j1;
+  double w0, w1;
+  table_weights(c, tt, &j0, &w0, &j1, &w1);
+  if (c->ft.empty()) return;
+  for (int a = 0; a < 3; ++a) {
+    dA[3 * j0 + a] += w0 * gA[a];
+    dB[3 * j0 + a] += w0 * gB[a];
+    if (w1 != 0.0) {
+      dA[3 * j1 + a] += w1 * gA[a];
+      dB[3 * j1 + a] += w1 * gB[a];
+    }
+  }
+}
+
+template <typename R>
+tddft_status do_backward(tddft_ctx* c, int nsteps, int ckpt, const double* dL_drho, double* loss, double* dA,
+                         double* dB) {
+  if (c->exp_kind != TDDFT_EXP_CHEBYSHEV || c->sc_tol > 0.0)
+    return c->fail(TDDFT_ERR_UNSUPPORTED, "backward needs Chebyshev exponentials and sc_tol = 0");
+  {
+    const size_t smem = (size_t)(c->N + 2 * c->N * (c->N + 1)) * 2 * sizeof(R) + 24 * sizeof(double);
+    if (smem > 227 * 1024) return c->fail(TDDFT_ERR_UNSUPPORTED, "backward: grid too large for the adjoint z pass");
+  }
+  if (ckpt < 1) ckpt = nsteps > 0 ? nsteps : 1;
+  const size_t nt = c->ft.size();
+  for (size_t i = 0; i < 3 * nt; ++i) {
+    if (dA) dA[i] = 0.0;
+    if (dB) dB[i] = 0.0;
+  }
+  std::vector<double> gAt(3 * std::max<size_t>(nt, 1), 0.0), gBt(3 * std::max<size_t>(nt, 1), 0.0);
+  DevBuf db;
+  AdjWork w;
+  const size_t pb = c->psi_elems() * 2 * sizeof(R);
+  const size_t N3 = c->N3;
+  const int K1 = std::max(c->K_full, c->K_half), Kh = c->K_half;
+  tddft_status s;
+  w.slots1.assign(K1 + 1, nullptr);
+  for (int k = 1; k <= K1; ++k)
+    if ((s = tmp_alloc(c, db, &w.slots1[k], pb, "adjoint T1"))) return s;
+  w.slots2.assign(c->n_sc + 1, std::vector<void*>(Kh + 1, nullptr));
+  w.outs.assign(c->n_sc + 1, nullptr);
+  w.rhos.assign(c->n_sc + 1, nullptr);
+  w.Vs.assign(c->n_sc + 1, nullptr);
+  w.Vfs.assign(c->n_sc + 1, nullptr);
+  for (int j = 0; j <= c->n_sc; ++j) {
+    for (int k = 1; k <= Kh; ++k)
+      if ((s = tmp_alloc(c, db, &w.slots2[j][k], pb, "adjoint T2"))) return s;
+    if ((s = tmp_alloc(c, db, &w.outs[j], pb, "adjoint out")) || (s = tmp_alloc(c, db, &w.rhos[j], 4 * N3 * 8, "adj rho")) ||
+        (s = tmp_alloc(c, db, &w.Vs[j], 4 * N3 * 8, "adj V")))
+      return s;
+    if (c->prec != TDDFT_FP64 && (s = tmp_alloc(c, db, &w.Vfs[j], 4 * N3 * 4, "adj Vf"))) return s;
+  }
+  if ((s = tmp_alloc(c, db, &w.pred, pb, "adj pred")) || (s = tmp_alloc(c, db, &w.phi, pb, "adj phi")) ||
+      (s = tmp_alloc(c, db, &w.Sa, pb, "adj Sa")) || (s = tmp_alloc(c, db, &w.Sb, pb, "adj Sb")) ||
+      (s = tmp_alloc(c, db, &w.tmp2, pb, "adj tmp2")) || (s = tmp_alloc(c, db, &w.PB, pb, "adj PB")) ||
+      (s = tmp_alloc(c, db, &w.YB, pb, "adj YB")) || (s = tmp_alloc(c, db, &w.PHIB, pb, "adj PHIB")) ||
+      (s = tmp_alloc(c, db, &w.rho_n, 4 * N3 * 8, "adj rho_n")) || (s = tmp_alloc(c, db, &w.V_n, 4 * N3 * 8, "adj V_n")) ||
+      (s = tmp_alloc(c, db, &w.gV, 4 * N3 * 8, "adj gV")) || (s = tmp_alloc(c, db, &w.rbar, 4 * N3 * 8, "adj rbar")) ||
+      (s = tmp_alloc(c, db, &w.gvf, N3 * 8, "adj gvf")) || (s = tmp_alloc(c, db, &w.gbf, 3 * N3 * 8, "adj gbf")) ||
+      (s = tmp_alloc(c, db, &w.part, (size_t)2 * c->nkb * c->N * 3 * 8, "adj part")) ||
+      (s = tmp_alloc(c, db, &w.agrad, (3 * (size_t)c->nkb + 3) * 8, "adj agrad")))
+    return s;
+  if (c->prec != TDDFT_FP64 && (s = tmp_alloc(c, db, &w.Vf_n, 4 * N3 * 4, "adj Vf_n"))) return s;
+  w.ncoef = (size_t)c->nkb * std::max(1, c->natoms) * 2 * c->nlm;
+  const size_t cb = w.ncoef * 2 * sizeof(R);
+  if ((s = tmp_alloc(c, db, &w.cS, cb, "cS")) || (s = tmp_alloc(c, db, &w.dcS, cb, "dcS")) ||
+      (s = tmp_alloc(c, db, &w.mS, 3 * cb, "mS")) || (s = tmp_alloc(c, db, &w.cT, cb, "cT")) ||
+      (s = tmp_alloc(c, db, &w.dcT, cb, "dcT")) || (s = tmp_alloc(c, db, &w.mT, 3 * cb, "mT")))
+    return s;
+  const int nck = (nsteps + ckpt - 1) / ckpt;
+  std::vector<void*> ck(std::max(nck, 1), nullptr), seg(ckpt, nullptr);
+  for (int i = 0; i < nck; ++i)
+    if ((s = tmp_alloc(c, db, &ck[i], pb, "checkpoint"))) return s;
+  for (int i = 0; i < ckpt; ++i)
+    if ((s = tmp_alloc(c, db, &seg[i], pb, "segment"))) return s;
+  // ---- forward with checkpoints
+  std::vector<double> times(nsteps + 1);
+  times[0] = c->t;
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % ckpt == 0 && (s = c->cuda(cudaMemcpyAsync(ck[n / ckpt], c->psi, pb, cudaMemcpyDeviceToDevice, c->st), "ckpt")))
+      return s;
+    if ((s = one_step<R>(c))) return s;
+    times[n + 1] = c->t;
+  }
+  // ---- loss and seed
+  std::vector<double> rho_h(4 * N3);
+  if ((s = c->cuda(cudaMemcpyAsync(rho_h.data(), c->rho, rho_h.size() * 8, cudaMemcpyDeviceToHost, c->st), "rho read")) ||
+      (s = c->cuda(cudaStreamSynchronize(c->st), "rho sync")))
+    return s;
+  double L = 0.0;
+  for (size_t i = 0; i < 4 * N3; ++i) L += dL_drho[i] * rho_h[i];
+  if (loss) *loss = L;
+  void* final_psi = nullptr;
+  if ((s = tmp_alloc(c, db, &final_psi, pb, "final psi")) ||
+      (s = c->cuda(cudaMemcpyAsync(final_psi, c->psi, pb, cudaMemcpyDeviceToDevice, c->st), "final copy")) ||
+      (s = c->cuda(cudaMemcpyAsync(w.rbar, dL_drho, 4 * N3 * 8, cudaMemcpyHostToDevice, c->st), "seed upload")) ||
+      (s = density_adj<R>(c, c->psi, w.rbar, nullptr, w.PB)))
+    return s;
+  const double t_final = c->t;
+  // ---- reverse over checkpoint segments
+  for (int sg = nck - 1; sg >= 0; --sg) {
+    const int s0 = sg * ckpt, s1 = std::min(nsteps, s0 + ckpt);
+    if ((s = c->cuda(cudaMemcpyAsync(c->psi, ck[sg], pb, cudaMemcpyDeviceToDevice, c->st), "restore")) ||
+        (s = c->cuda(cudaMemcpyAsync(seg[0], ck[sg], pb, cudaMemcpyDeviceToDevice, c->st), "seg0")))
+      return s;
+    c->t = times[s0];
+    float* Vcf = c->prec == TDDFT_FP64 ? nullptr : c->Vf;
+    if ((s = density<R>(c, c->psi, c->rho)) || (s = potential(c, c->rho, c->t, c->V, Vcf))) return s;
+    for (int n = s0; n < s1 - 1; ++n) {
+      if ((s = one_step<R>(c))) return s;
+      if ((s = c->cuda(cudaMemcpyAsync(seg[n - s0 + 1], c->psi, pb, cudaMemcpyDeviceToDevice, c->st), "seg copy"))) return s;
+    }
+    for (int n = s1 - 1; n >= s0; --n) {
+      double gA0[3] = {0, 0, 0}, gB0[3] = {0, 0, 0}, gA1[3] = {0, 0, 0}, gB1[3] = {0, 0, 0};
+      if ((s = adjoint_step<R>(c, w, seg[n - s0], times[n], gA0, gB0, gA1, gB1))) return s;
+      add_table(c, times[n], gA0, gB0, gAt.data(), gBt.data());
+      add_table(c, times[n] + c->dt, gA1, gB1, gAt.data(), gBt.data());
+    }
+  }
+  // ---- restore the forward end state
+  if ((s = c->cuda(cudaMemcpyAsync(c->psi, final_psi, pb, cudaMemcpyDeviceToDevice, c->st), "final restore"))) return s;
+  c->t = t_final;
+  {
+    float* Vcf = c->prec == TDDFT_FP64 ? nullptr : c->Vf;
+    if ((s = density<R>(c, c->psi, c->rho)) || (s = potential(c, c->rho, c->t, c->V, Vcf))) return s;
+  }
+  if ((s = c->cuda(cudaStreamSynchronize(c->st), "backward sync"))) return s;
+  for (size_t i = 0; i < 3 * nt; ++i) {
+    if (dA) dA[i] = gAt[i];
+    if (dB) dB[i] = gBt[i];
+  }
   return TDDFT_OK;
 }
 
@@ -779,9 +1269,10 @@ template <typename R> tddft_status do_observables(tddft_ctx* c, double* n, doubl
        })))
     return s;
   std::vector<double> h(16 + 5 * nkb, 0.0);
-  int flag = 0;
+  int flag = 0, tcflag = 0;
   if ((s = c->cuda(cudaMemcpyAsync(h.data(), c->red, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st), "obs read"))) return s;
   if ((s = c->cuda(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "flag read"))) return s;
+  if ((s = c->cuda(cudaMemcpyAsync(&tcflag, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st), "tc flag read"))) return s;
   std::vector<double> rho_h;
   if (n || m) {
     rho_h.resize(4 * c->N3);
@@ -821,6 +1312,7 @@ template <typename R> tddft_status do_observables(tddft_ctx* c, double* n, doubl
       m[N3 + r] = -2.0 * rho_h[3 * N3 + r];
       m[2 * N3 + r] = rho_h[r] - rho_h[N3 + r];
     }
+  if (tcflag) return c->fail(TDDFT_ERR_CUDA, "a tensor-core projector wait exceeded its iteration limit");
   if (bad) return c->fail(TDDFT_ERR_DIVERGED, "non-finite density or norm");
   if (flag) return c->fail(TDDFT_ERR_BOUND, "potential left the Chebyshev spectral window");
   return TDDFT_OK;
@@ -889,6 +1381,7 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   if (pr->precision != TDDFT_FP64 && pr->precision != TDDFT_FP32_MIXED) return c->fail(TDDFT_ERR_ARG, "bad precision");
   c->prec = pr->precision;
   c->proj_mode = pr->proj_mode;
+  if (c->proj_mode < TDDFT_PROJ_FP64 || c->proj_mode > TDDFT_PROJ_TF32X3) return c->fail(TDDFT_ERR_ARG, "bad proj_mode");
   if (pr->nk < 1 || pr->nk > kMaxK || !pr->kpts || !pr->kw) return c->fail(TDDFT_ERR_ARG, "nk must be 1..16 with kpts and kw");
   if (pr->nstates < 1 || !pr->occ) return c->fail(TDDFT_ERR_ARG, "nstates must be >= 1 with occ");
   c->nk = pr->nk;
@@ -914,6 +1407,12 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   if ((c->emin_user != 0.0 || c->emax_user != 0.0) && !(c->emax_user > c->emin_user))
     return c->fail(TDDFT_ERR_ARG, "e_max must exceed e_min");
   c->xc = pr->xc ? 1 : 0;
+  {
+    // Default: five launches per Chebyshev term (FFT passes, gather, pointwise epilogue), the
+    // faster form on this part.  TDDFT_FUSED=1 selects the fused term kernel (same results).
+    const char* e = std::getenv("TDDFT_FUSED");
+    c->use_fused = (e && e[0] == '1');
+  }
   if (atoms->natoms < 0 || (atoms->natoms > 0 && (!atoms->pos || !atoms->species))) return c->fail(TDDFT_ERR_ARG, "bad atoms");
   c->natoms = atoms->natoms;
   if (c->natoms > 0) {
@@ -926,6 +1425,8 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   }
   c->lmax = c->natoms > 0 ? pj->lmax : 0;
   c->nlm = (c->lmax + 1) * (c->lmax + 1);
+  if (c->proj_mode >= TDDFT_PROJ_TF32 && c->natoms > 0 && (c->prec == TDDFT_FP64 || c->nlm != 9))
+    return c->fail(TDDFT_ERR_UNSUPPORTED, "tensor-core projectors need FP32-mixed precision and lmax = 2");
   c->r_cut = pj->r_cut;
   c->pos.assign(atoms->pos, atoms->pos + 3 * c->natoms);
   std::vector<double> Zr(2 * std::max(1, c->natoms), 0.0);
@@ -958,6 +1459,13 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
     if ((s = c->alloc(&c->stage, c->stage_elems * sizeof(double2), "stage"))) return s;
   }
   if ((s = upload(c, &c->wf_d, c->wf, "weights"))) return s;
+  if (density_groups(N3, c->nkb) > 1 &&
+      (s = c->alloc(&c->rho_part, (size_t)density_groups(N3, c->nkb) * 4 * N3 * 8, "density partials")))
+    return s;
+  if ((s = c->alloc(&c->tc_err, 16, "tc flag")) || (s = c->cuda(cudaMemset(c->tc_err, 0, 16), "tc flag init"))) return s;
+  if (c->prec != TDDFT_FP64 && c->proj_mode >= TDDFT_PROJ_TF32 && c->natoms > 0 &&
+      (s = c->alloc(&c->tc_part, proj_tc_part_floats(c->natoms, c->nk, c->nb) * sizeof(float), "tc partials")))
+    return s;
   if ((s = c->cuda(cudaMemset(c->flag, 0, 16), "flag init"))) return s;
 
   // ---- twiddles exp(-2 pi i t / N)
@@ -980,6 +1488,15 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   double* zr_d = nullptr;
   if ((s = upload(c, &pos_d, c->pos.empty() ? std::vector<double>(3, 0.0) : c->pos, "pos")) || (s = upload(c, &zr_d, Zr, "Zr")))
     return s;
+  if (c->natoms > 0) {
+    if ((s = c->alloc(&c->owner, N3 * sizeof(int), "voronoi owner")) ||
+        (s = c->alloc(&c->atom_sums, 4 * (size_t)c->natoms * 8, "atom sums")))
+      return s;
+    if ((s = c->launch(KC_OTHER, "voronoi owner", [&] {
+           return launch_voronoi_owner(c->st, c->N, c->L, c->natoms, pos_d, c->owner);
+         })))
+      return s;
+  }
   if ((s = c->launch(KC_OTHER, "vloc G", [&] { return launch_vloc_G(c->st, c->N, c->L, c->natoms, pos_d, zr_d, c->omega, c->hart); }))) return s;
   ZParams zp{};
   if ((s = c->launch(KC_OTHER, "vloc ifft z", [&] { return launch_fft_z<double>(c->st, c->N, c->hart, 1, c->tw64, Z_INV_ONLY, zp); }))) return s;
@@ -1091,6 +1608,35 @@ tddft_status tddft_apply_hamiltonian(tddft_handle h, const void* in, void* out, 
   if (!in || !out || in == out) return h->fail(TDDFT_ERR_ARG, "bad in/out");
   if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no potential yet: call tddft_set_states first");
   return h->prec == TDDFT_FP64 ? do_apply_h<double>(h, in, out, on_device) : do_apply_h<float>(h, in, out, on_device);
+}
+
+tddft_status tddft_backward(tddft_handle h, int nsteps, int ckpt_every, const double* dL_drho, double* loss,
+                            double* dL_dA, double* dL_dB) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (nsteps < 1 || !dL_drho) return h->fail(TDDFT_ERR_ARG, "backward needs nsteps >= 1 and dL_drho");
+  if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "tddft_set_states must come first");
+  return h->prec == TDDFT_FP64 ? do_backward<double>(h, nsteps, ckpt_every, dL_drho, loss, dL_dA, dL_dB)
+                               : do_backward<float>(h, nsteps, ckpt_every, dL_drho, loss, dL_dA, dL_dB);
+}
+
+tddft_status tddft_atom_moments(tddft_handle h, double* M, double* N) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no states loaded");
+  if (h->natoms == 0) return TDDFT_OK;
+  tddft_status s = h->launch(KC_OTHER, "atom sums", [&] {
+    return launch_atom_sums(h->st, h->N3, h->natoms, h->rho, h->owner, h->atom_sums);
+  });
+  if (s) return s;
+  std::vector<double> out(4 * (size_t)h->natoms);
+  if ((s = h->cuda(cudaMemcpyAsync(out.data(), h->atom_sums, out.size() * 8, cudaMemcpyDeviceToHost, h->st), "atom read")) ||
+      (s = h->cuda(cudaStreamSynchronize(h->st), "atom sync")))
+    return s;
+  for (int a = 0; a < h->natoms; ++a) {
+    if (M)
+      for (int c = 0; c < 3; ++c) M[3 * a + c] = out[4 * a + c] * h->dV;
+    if (N) N[a] = out[4 * a + 3] * h->dV;
+  }
+  return TDDFT_OK;
 }
 
 tddft_status tddft_set_stream(tddft_handle h, void* stream) {

@@ -2,9 +2,9 @@
 //
 // A plane or slab of N x N complex values lives in shared memory with a padded row
 // stride; each pass transforms N rows of length N in place.  Every stage of a
-// mixed-radix (2, 3, 4) Stockham decomposition reads its butterflies into registers,
+// mixed-radix Stockham decomposition reads its butterflies into registers,
 // synchronises the CTA, and writes them back in sorted order, so no second buffer is
-// needed and the output is in natural order.
+// needed and the output is in natural order.  Radices 2, 3, 4 and 8 are available.
 //
 // Stage algebra (decimation in time).  After the stages with radices r_1..r_s the array
 // holds Y[j, k] = sum_t x[k + m t] w_L^{j t} at position j*m + k, L = r_1 ... r_s,
@@ -63,36 +63,66 @@ template <typename C, bool INV> struct SmallDFT<C, 4, INV> {
   }
 };
 
+template <typename C, bool INV> struct SmallDFT<C, 8, INV> {
+  // radix-2 split into two 4-point DFTs; w8^p = exp(-+ 2 pi i p / 8)
+  __device__ __forceinline__ static void run(C* v) {
+    using R = decltype(C::x);
+    const R r = (R)0.70710678118654752440;  // 1/sqrt(2)
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    SmallDFT<C, 4, INV>::run(e);
+    SmallDFT<C, 4, INV>::run(o);
+    C o1, o2, o3;
+    if (!INV) {
+      o1 = cmake<C>((o[1].x + o[1].y) * r, (o[1].y - o[1].x) * r);   // (1 - i)/sqrt2
+      o2 = cmake<C>(o[2].y, -o[2].x);                                  // -i
+      o3 = cmake<C>((o[3].y - o[3].x) * r, -(o[3].x + o[3].y) * r);  // (-1 - i)/sqrt2
+    } else {
+      o1 = cmake<C>((o[1].x - o[1].y) * r, (o[1].x + o[1].y) * r);   // (1 + i)/sqrt2
+      o2 = cmake<C>(-o[2].y, o[2].x);                                  // +i
+      o3 = cmake<C>(-(o[3].x + o[3].y) * r, (o[3].x - o[3].y) * r);  // (-1 + i)/sqrt2
+    }
+    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
+  }
+};
+
 template <int... Rs> struct RadixList {};
 template <int N> struct FFTPlan;
-template <> struct FFTPlan<8> { using type = RadixList<4, 2>; };
+template <> struct FFTPlan<8> { using type = RadixList<8>; };
 template <> struct FFTPlan<12> { using type = RadixList<4, 3>; };
 template <> struct FFTPlan<16> { using type = RadixList<4, 4>; };
-template <> struct FFTPlan<24> { using type = RadixList<4, 3, 2>; };
-template <> struct FFTPlan<32> { using type = RadixList<4, 4, 2>; };
-template <> struct FFTPlan<48> { using type = RadixList<4, 4, 3>; };
-template <> struct FFTPlan<64> { using type = RadixList<4, 4, 4>; };
-template <> struct FFTPlan<96> { using type = RadixList<4, 4, 3, 2>; };
+template <> struct FFTPlan<24> { using type = RadixList<8, 3>; };
+template <> struct FFTPlan<32> { using type = RadixList<8, 4>; };
+template <> struct FFTPlan<48> { using type = RadixList<8, 2, 3>; };
+template <> struct FFTPlan<64> { using type = RadixList<8, 8>; };
+template <> struct FFTPlan<96> { using type = RadixList<8, 4, 3>; };
 
-// One in-place radix-RAD stage over N rows of length N.  Element (row, i) sits at
-// s[row * rs + i * es].  NT threads cooperate; all of them must call this.
-template <typename C, int N, int RAD, int LSPAN, int NT, bool INV>
-__device__ __forceinline__ void fft_stage(C* s, int rs, int es, const C* tw) {
+// One in-place radix-RAD stage over NP planes of N rows of length N.  Element (row, i) of
+// plane p sits at s[p * ps + row * rs + i * es].  NT threads cooperate; all must call this.
+template <typename C, int N, int RAD, int LSPAN, int NT, bool INV, int NP>
+__device__ __forceinline__ void fft_stage(C* s, int rs, int es, int ps, const C* tw) {
   constexpr int MP = N / (LSPAN * RAD);
   constexpr int NBR = N / RAD;            // butterflies per row
-  constexpr int NBF = N * NBR;            // butterflies in the pass
+  constexpr int NBF = NP * N * NBR;       // butterflies in the pass
   constexpr int PER = (NBF + NT - 1) / NT;
   C v[PER][RAD];
-  int rowv[PER], jv[PER], kv[PER];
+  int offv[PER], jv[PER], kv[PER];
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int b = threadIdx.x + u * NT;
-    rowv[u] = -1;
+    offv[u] = -1;
     if ((NBF % NT) == 0 || b < NBF) {
-      const int row = b / NBR, bb = b - row * NBR;
+      // rows vary fastest across threads: a warp touches 32 different rows at the same
+      // position, which with the odd row pitch is free of shared-memory bank conflicts
+      const int bb = b / (NP * N), rowp = b - bb * (NP * N);
+      const int plane = rowp / N, row = rowp - plane * N;
       const int j = bb / MP, kp = bb - j * MP;
-      rowv[u] = row; jv[u] = j; kv[u] = kp;
-      const C* base = s + row * rs;
+      offv[u] = plane * ps + row * rs;
+      jv[u] = j; kv[u] = kp;
+      const C* base = s + offv[u];
 #pragma unroll
       for (int q = 0; q < RAD; ++q) {
         C x = base[(j * MP * RAD + kp + MP * q) * es];
@@ -108,9 +138,9 @@ __device__ __forceinline__ void fft_stage(C* s, int rs, int es, const C* tw) {
   __syncthreads();
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
-    if (rowv[u] >= 0) {
+    if (offv[u] >= 0) {
       SmallDFT<C, RAD, INV>::run(v[u]);
-      C* base = s + rowv[u] * rs;
+      C* base = s + offv[u];
 #pragma unroll
       for (int p = 0; p < RAD; ++p) base[((jv[u] + LSPAN * p) * MP + kv[u]) * es] = v[u][p];
     }
@@ -118,19 +148,95 @@ __device__ __forceinline__ void fft_stage(C* s, int rs, int es, const C* tw) {
   __syncthreads();
 }
 
-template <typename C, int N, int NT, bool INV, int LSPAN, int R0, int... Rest>
-__device__ __forceinline__ void fft_stages(C* s, int rs, int es, const C* tw) {
-  fft_stage<C, N, R0, LSPAN, NT, INV>(s, rs, es, tw);
-  if constexpr (sizeof...(Rest) > 0) fft_stages<C, N, NT, INV, LSPAN * R0, Rest...>(s, rs, es, tw);
+template <typename C, int N, int NT, bool INV, int NP, int LSPAN, int R0, int... Rest>
+__device__ __forceinline__ void fft_stages(C* s, int rs, int es, int ps, const C* tw) {
+  fft_stage<C, N, R0, LSPAN, NT, INV, NP>(s, rs, es, ps, tw);
+  if constexpr (sizeof...(Rest) > 0) fft_stages<C, N, NT, INV, NP, LSPAN * R0, Rest...>(s, rs, es, ps, tw);
 }
 
-template <typename C, int N, int NT, bool INV, int... Rs>
-__device__ __forceinline__ void fft_pass_impl(C* s, int rs, int es, const C* tw, RadixList<Rs...>) {
-  fft_stages<C, N, NT, INV, 1, Rs...>(s, rs, es, tw);
+template <typename C, int N, int NT, bool INV, int NP, int... Rs>
+__device__ __forceinline__ void fft_pass_impl(C* s, int rs, int es, int ps, const C* tw, RadixList<Rs...>) {
+  fft_stages<C, N, NT, INV, NP, 1, Rs...>(s, rs, es, ps, tw);
 }
 
-// Unnormalised length-N transform of N rows held in shared memory.
-template <typename C, int N, int NT, bool INV>
-__device__ __forceinline__ void fft_pass(C* s, int rs, int es, const C* tw) {
-  fft_pass_impl<C, N, NT, INV>(s, rs, es, tw, typename FFTPlan<N>::type{});
+// Unnormalised length-N transform of the N rows of NP planes held in shared memory.
+template <typename C, int N, int NT, bool INV, int NP = 1>
+__device__ __forceinline__ void fft_pass(C* s, int rs, int es, const C* tw, int ps = 0) {
+  fft_pass_impl<C, N, NT, INV, NP>(s, rs, es, ps, tw, typename FFTPlan<N>::type{});
+}
+
+// Copy an N x N plane between global memory (dense rows) and shared memory (row stride RS),
+// 16 bytes per global access.
+template <int N, int NT, int RS>
+__device__ __forceinline__ void plane_load(float2* s, const float2* __restrict__ g) {
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N * N / 2; i += NT) {
+    const float4 v = g4[i];
+    const int idx = 2 * i, row = idx / N, col = idx - row * N;
+    s[row * RS + col] = make_float2(v.x, v.y);
+    s[row * RS + col + 1] = make_float2(v.z, v.w);
+  }
+}
+template <int N, int NT, int RS>
+__device__ __forceinline__ void plane_store(float2* __restrict__ g, const float2* s) {
+  float4* g4 = reinterpret_cast<float4*>(g);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N * N / 2; i += NT) {
+    const int idx = 2 * i, row = idx / N, col = idx - row * N;
+    const float2 a = s[row * RS + col], b = s[row * RS + col + 1];
+    g4[i] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+template <int N, int NT, int RS>
+__device__ __forceinline__ void plane_load(double2* s, const double2* __restrict__ g) {
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N * N; i += NT) {
+    const int row = i / N, col = i - row * N;
+    s[row * RS + col] = g[i];
+  }
+}
+template <int N, int NT, int RS>
+__device__ __forceinline__ void plane_store(double2* __restrict__ g, const double2* s) {
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N * N; i += NT) {
+    const int row = i / N, col = i - row * N;
+    g[i] = s[row * RS + col];
+  }
+}
+// Strided variant for z slabs: row z of the slab starts at g + z * gstride (elements).
+template <int N, int NT, int RS>
+__device__ __forceinline__ void slab_load(float2* s, const float2* __restrict__ g, size_t gstride) {
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N * N / 2; i += NT) {
+    const int idx = 2 * i, row = idx / N, col = idx - row * N;
+    const float4 v = *reinterpret_cast<const float4*>(g + row * gstride + col);
+    s[row * RS + col] = make_float2(v.x, v.y);
+    s[row * RS + col + 1] = make_float2(v.z, v.w);
+  }
+}
+template <int N, int NT, int RS>
+__device__ __forceinline__ void slab_store(float2* __restrict__ g, const float2* s, size_t gstride) {
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N * N / 2; i += NT) {
+    const int idx = 2 * i, row = idx / N, col = idx - row * N;
+    const float2 a = s[row * RS + col], b = s[row * RS + col + 1];
+    *reinterpret_cast<float4*>(g + row * gstride + col) = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+template <int N, int NT, int RS>
+__device__ __forceinline__ void slab_load(double2* s, const double2* __restrict__ g, size_t gstride) {
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N * N; i += NT) {
+    const int row = i / N, col = i - row * N;
+    s[row * RS + col] = g[row * gstride + col];
+  }
+}
+template <int N, int NT, int RS>
+__device__ __forceinline__ void slab_store(double2* __restrict__ g, const double2* s, size_t gstride) {
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N * N; i += NT) {
+    const int row = i / N, col = i - row * N;
+    g[row * gstride + col] = s[row * RS + col];
+  }
 }

@@ -26,7 +26,7 @@ struct ZParams {
 enum ZMode { Z_KIN = 0, Z_POISSON = 1, Z_INV_ONLY = 2 };
 
 // Chebyshev / Taylor epilogue modes.
-enum EpiMode { EPI_APPLY = 0, EPI_FIRST = 1, EPI_RECUR = 2, EPI_TAYLOR = 3 };
+enum EpiMode { EPI_APPLY = 0, EPI_FIRST = 1, EPI_RECUR = 2, EPI_TAYLOR = 3, EPI_ADJ = 4, EPI_ADJ0 = 5 };
 
 struct EpiParams {
   int mode;
@@ -36,6 +36,7 @@ struct EpiParams {
   int use_acc1, use_acc2;
   double shift[kMaxK][3];       // k + A(t), for projector phases
   int nstates;
+  int dc_staged;                // fused kernel: D c copied to shared memory (set by its launcher)
 };
 
 // Device-side projector tables.
@@ -63,9 +64,18 @@ template <typename R>
 cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* Tk, const void* Tkm1,
                             void* Tout, void* acc1, void* acc2, const R* V, const ProjTables<R>& pt,
                             const void* dc, int nkb, const EpiParams& ep);
+// Fused inverse-xy FFT + Chebyshev epilogue + forward-xy FFT of T_{k+1} (FIRST/RECUR modes).
+template <typename R> bool fused_supported(int N);
+template <typename R>
+cudaError_t launch_fused_term(cudaStream_t st, int N, void* tmp, const void* Tk, const void* Tkm1, void* Tout,
+                              void* acc1, void* acc2, const R* V, const ProjTables<R>& pt, const void* dc, int nkb,
+                              const void* tw, const EpiParams& ep, int do_fwd);
+// rho_v of all spinors; part (density_groups(N3, nkb) x 4 x N3 doubles, may be null) lets the
+// band sum run as several groups reduced in a fixed order.
+int density_groups(size_t N3, int nkb);
 template <typename R>
 cudaError_t launch_density(cudaStream_t st, size_t N3, const void* psi, int nkb, const double* wf,
-                           double* rho);
+                           double* rho, double* part);
 cudaError_t launch_potential(cudaStream_t st, size_t N3, const double* rho, const double* vH,
                              const double* vloc, const double* B, int xc, double* V, float* Vf,
                              double* exc, double* vxc4);
@@ -88,5 +98,40 @@ cudaError_t launch_field_sums(cudaStream_t st, size_t N3, const double* rho, con
 cudaError_t launch_max_abs_diff(cudaStream_t st, size_t n, const double* a, const double* b, double* out);
 cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, double lo, double hi,
                                 double kin_max, double nl_bound, int* flag);
+
+// Tensor-core projector contraction (tcgen05 kind::tf32), FP32-mixed path, l <= 2.
+cudaError_t launch_proj_gather_tc(cudaStream_t st, int N, const void* psi, int nk, int nstates,
+                                  const ProjTables<float>& pt, double dV, const EpiParams& ep, int split3,
+                                  float* part, void* c_out, void* dc_out, int* err);
+size_t proj_tc_part_floats(int natoms, int nk, int nstates);
+
+// Voronoi (nearest-atom) cells and per-atom sums of m and n.
+cudaError_t launch_voronoi_owner(cudaStream_t st, int N, const double* L, int natoms, const double* pos, int* owner);
+cudaError_t launch_atom_sums(cudaStream_t st, size_t N3, int natoms, const double* rho, const int* owner, double* out);
+
+// ---------------------------------------------------------------- adjoint launchers
+template <typename R>
+cudaError_t launch_proj_gather_mom(cudaStream_t st, int N, const void* psi, int nkb, const ProjTables<R>& pt,
+                                   double dV, const EpiParams& ep, int alpha, void* m_out);
+template <typename R>
+cudaError_t launch_grad_v(cudaStream_t st, size_t N3, int nkb, const void* S, const void* T, double f, double* gV);
+template <typename R>
+cudaError_t launch_fft_z_current(cudaStream_t st, int N, void* U, const void* W, int nbatch, const void* tw,
+                                 const ZParams& zp, double* part);
+template <typename R>
+cudaError_t launch_nl_agrad(cudaStream_t st, int nkb, int ncoef, const void* mS, const void* dcT, const void* dcS,
+                            const void* mT, size_t mstride, double inv_dV, double f, double* out);
+cudaError_t launch_xc_adjoint(cudaStream_t st, size_t N3, const double* rho, const double* gV, int xc, double* rbar,
+                              double* gvf, double* gbf);
+cudaError_t launch_add_hartree_adjoint(cudaStream_t st, size_t N3, const double2* h, double* rbar);
+cudaError_t launch_real_field_to_complex(cudaStream_t st, size_t N3, const double* in, double2* out);
+cudaError_t launch_sum3(cudaStream_t st, size_t N3, const double* g, double* out);
+cudaError_t launch_accum_parts(cudaStream_t st, size_t count, const double* part, double f, double* out3);
+template <typename R>
+cudaError_t launch_density_adjoint(cudaStream_t st, size_t N3, int nkb, const void* psi, const double* rbar,
+                                   const double* wf, const void* add, void* out);
+template <typename R>
+cudaError_t launch_seed(cudaStream_t st, size_t n, const void* y1, const double a[2], const void* y2,
+                        const double b[2], void* out);
 
 }  // namespace tddft

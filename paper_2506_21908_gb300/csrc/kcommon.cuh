@@ -1,0 +1,43 @@
+// Small device helpers shared by the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace tddft {
+
+template <int N> struct FFTThreads { static constexpr int value = (N >= 96) ? 512 : 256; };
+
+// Minimum resident CTAs per SM requested from the register allocator: several CTAs of the
+// FP32 passes up to 64^3 fit without spills; FP64 and 96^3 variants keep their registers.
+template <typename R, int N> struct FFTMinBlocks { static constexpr int value = 1; };
+template <int N> struct FFTMinBlocks<float, N> { static constexpr int value = (N <= 64) ? 1024 / FFTThreads<N>::value : 1; };
+template <typename R, int N> struct FusedMinBlocks { static constexpr int value = 1; };
+template <int N> struct FusedMinBlocks<float, N> { static constexpr int value = (N <= 64) ? 2 : 1; };
+
+template <int N> __device__ __forceinline__ int freq(int i) { return i < N / 2 ? i : i - N; }
+
+#define TDDFT_DISPATCH_N(N, CALL)          \
+  switch (N) {                             \
+    case 8: { constexpr int NN = 8; return CALL; }   \
+    case 12: { constexpr int NN = 12; return CALL; } \
+    case 16: { constexpr int NN = 16; return CALL; } \
+    case 24: { constexpr int NN = 24; return CALL; } \
+    case 32: { constexpr int NN = 32; return CALL; } \
+    case 48: { constexpr int NN = 48; return CALL; } \
+    case 64: { constexpr int NN = 64; return CALL; } \
+    case 96: { constexpr int NN = 96; return CALL; } \
+    default: return cudaErrorInvalidValue;           \
+  }
+
+template <typename R> __device__ __forceinline__ void sincos_r(R x, R* s, R* c);
+template <> __device__ __forceinline__ void sincos_r<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+template <> __device__ __forceinline__ void sincos_r<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+
+}  // namespace tddft

@@ -1,0 +1,63 @@
+// Point-wise Hamiltonian helpers shared by the epilogue kernels: the 2x2 spin-matrix local
+// potential [[v + b_z, b_x - i b_y], [b_x + i b_y, v - b_z]] from the 4-vector
+// V_v = [v + b_z, v - b_z, 2 b_x, -2 b_y] (Eq. potential4) and the projector scatter
+// sum_a sum_p beta_p(d) exp(-i (k+A).d) (D c)_p (Eq. Vps with the L.S blocks).
+#pragma once
+#include "fft.cuh"
+#include "impl.cuh"
+#include "kcommon.cuh"
+
+namespace tddft {
+
+template <typename C> struct Pair { C a, b; };
+__device__ __forceinline__ Pair<float2> ld2(const float2* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void st2(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ Pair<double2> ld2(const double2* p) { return {p[0], p[1]}; }
+__device__ __forceinline__ void st2(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
+
+// phase exp(-i arg): FP32 reduces the argument to [-pi, pi] and uses the fast intrinsic
+__device__ __forceinline__ void phase_sincos(float x, float* sn, float* cs) {
+  const float r = x - 6.28318530717958647692f * rintf(x * 0.15915494309189533577f);
+  __sincosf(r, sn, cs);
+}
+__device__ __forceinline__ void phase_sincos(double x, double* sn, double* cs) { sincos(x, sn, cs); }
+
+// Hamiltonian at one point for both spinor components: (hu, hd) holds the kinetic part on
+// entry; the 2x2 local potential and the projector scatter are added.
+template <typename R, int NLM>
+__device__ __forceinline__ void h_point(typename CT<R>::type& hu, typename CT<R>::type& hd, typename CT<R>::type pu,
+                                        typename CT<R>::type pd, R V0, R V1, R hx, R hy, size_t r,
+                                        const ProjTables<R>& pt, const typename CT<R>::type* dcb, R sx, R sy, R sz) {
+  using C = typename CT<R>::type;
+  constexpr int TAB = 3 + NLM;
+  hu = cmake<C>(hu.x + V0 * pu.x + hx * pd.x - hy * pd.y, hu.y + V0 * pu.y + hx * pd.y + hy * pd.x);
+  hd = cmake<C>(hd.x + V1 * pd.x + hx * pu.x + hy * pu.y, hd.y + V1 * pd.y + hx * pu.y - hy * pu.x);
+  if (NLM > 0) {
+    const int e0 = pt.s_ptr[r], e1 = pt.s_ptr[r + 1];
+    for (int e = e0; e < e1; ++e) {
+      const int a = pt.s_atom[e];
+      const R* t = pt.s_tab + (size_t)e * TAB;
+      const C* dca = dcb + (size_t)a * 2 * NLM;  // this spinor's D c of atom a
+      R vux = 0, vuy = 0, vdx = 0, vdy = 0;
+#pragma unroll
+      for (int p = 0; p < NLM; ++p) {
+        const R bp = t[3 + p];
+        const C cu = dca[2 * p], cd = dca[2 * p + 1];
+        vux += bp * cu.x; vuy += bp * cu.y;
+        vdx += bp * cd.x; vdy += bp * cd.y;
+      }
+      R sn, cs;
+      phase_sincos(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);
+      hu.x += vux * cs + vuy * sn; hu.y += vuy * cs - vux * sn;
+      hd.x += vdx * cs + vdy * sn; hd.y += vdy * cs - vdx * sn;
+    }
+  }
+}
+
+
+}  // namespace tddft

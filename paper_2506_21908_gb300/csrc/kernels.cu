@@ -14,15 +14,16 @@
 
 #include "fft.cuh"
 #include "impl.cuh"
+#include "kcommon.cuh"
+#include "kepi.cuh"
 
 namespace tddft {
 
-template <int N> struct FFTThreads { static constexpr int value = (N >= 96) ? 512 : 256; };
 
 // ============================================================================ FFT passes
 
 template <typename R, int N, bool INV>
-__global__ void __launch_bounds__(FFTThreads<N>::value)
+__global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::value)
 k_fft_xy(const typename CT<R>::type* src, typename CT<R>::type* dst, const typename CT<R>::type* __restrict__ twg) {
   using C = typename CT<R>::type;
   constexpr int NT = FFTThreads<N>::value;
@@ -32,17 +33,43 @@ k_fft_xy(const typename CT<R>::type* src, typename CT<R>::type* dst, const typen
   C* s = tw + N;
   const size_t base = ((size_t)blockIdx.y * N + blockIdx.x) * (size_t)(N * N);
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
-  for (int i = threadIdx.x; i < N * N; i += NT) s[(i / N) * RS + (i % N)] = src[base + i];
+  plane_load<N, NT, RS>(s, src + base);
   __syncthreads();
   fft_pass<C, N, NT, INV>(s, RS, 1, tw);  // along x (rows: y)
   fft_pass<C, N, NT, INV>(s, 1, RS, tw);  // along y (rows: x)
-  for (int i = threadIdx.x; i < N * N; i += NT) dst[base + i] = s[(i / N) * RS + (i % N)];
+  plane_store<N, NT, RS>(dst + base, s);
 }
 
-template <int N> __device__ __forceinline__ int freq(int i) { return i < N / 2 ? i : i - N; }
+
+// Per-axis multiplier tables for the z pass: the kinetic factor 1/2 |G + s|^2 scale is
+// tx[x] + ty[y] + tz[z] with ta[i] = 1/2 (g_a f(i) + s_a)^2 scale (computed in FP64, stored in R).
+template <typename R, int N, int MODE>
+__device__ __forceinline__ void z_tables(R* tx, R* tz, R* ty, const ZParams& zp, int y, int k) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    if (MODE == Z_KIN) {
+      const double qx = zp.gs[0] * freq<N>(i) + zp.shift[k][0];
+      const double qz = zp.gs[2] * freq<N>(i) + zp.shift[k][2];
+      tx[i] = (R)(0.5 * qx * qx * zp.scale);
+      tz[i] = (R)(0.5 * qz * qz * zp.scale);
+    } else {
+      const double gx = zp.gs[0] * freq<N>(i), gz = zp.gs[2] * freq<N>(i);
+      tx[i] = (R)(gx * gx);
+      tz[i] = (R)(gz * gz);
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (MODE == Z_KIN) {
+      const double qy = zp.gs[1] * freq<N>(y) + zp.shift[k][1];
+      *ty = (R)(0.5 * qy * qy * zp.scale);
+    } else {
+      const double gy = zp.gs[1] * freq<N>(y);
+      *ty = (R)(gy * gy);
+    }
+  }
+}
 
 template <typename R, int N, int MODE>
-__global__ void __launch_bounds__(FFTThreads<N>::value)
+__global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::value)
 k_fft_z(typename CT<R>::type* __restrict__ data, const typename CT<R>::type* __restrict__ twg, ZParams zp) {
   using C = typename CT<R>::type;
   constexpr int NT = FFTThreads<N>::value;
@@ -50,39 +77,34 @@ k_fft_z(typename CT<R>::type* __restrict__ data, const typename CT<R>::type* __r
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s = tw + N;
+  R* tx = reinterpret_cast<R*>(s + N * RS);
+  R* tz = tx + N;
+  R* ty = tz + N;
   const int y = blockIdx.x;
   const int b = blockIdx.y;
   const size_t base = (size_t)b * N * N * N + (size_t)y * N;
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
-  for (int i = threadIdx.x; i < N * N; i += NT) {
-    const int z = i / N, x = i - z * N;
-    s[z * RS + x] = data[base + (size_t)z * N * N + x];
-  }
+  if (MODE != Z_INV_ONLY) z_tables<R, N, MODE>(tx, tz, ty, zp, y, (MODE == Z_KIN) ? b / zp.comps_per_k : 0);
+  slab_load<N, NT, RS>(s, data + base, (size_t)N * N);
   __syncthreads();
   if (MODE != Z_INV_ONLY) {
     fft_pass<C, N, NT, false>(s, 1, RS, tw);  // along z (rows: x)
-    const double gy = zp.gs[1] * freq<N>(y);
-    const int k = (MODE == Z_KIN) ? b / zp.comps_per_k : 0;
+    const R tyv = *ty;
     for (int i = threadIdx.x; i < N * N; i += NT) {
       const int z = i / N, x = i - z * N;
-      const double gx = zp.gs[0] * freq<N>(x), gz = zp.gs[2] * freq<N>(z);
-      double m;
+      R m;
       if (MODE == Z_KIN) {
-        const double qx = gx + zp.shift[k][0], qy = gy + zp.shift[k][1], qz = gz + zp.shift[k][2];
-        m = 0.5 * (qx * qx + qy * qy + qz * qz) * zp.scale;
+        m = tx[x] + tyv + tz[z];
       } else {
-        const double g2 = gx * gx + gy * gy + gz * gz;
-        m = g2 > 0.0 ? 4.0 * 3.14159265358979323846 / g2 * zp.scale : 0.0;
+        const double g2 = (double)tx[x] + (double)tyv + (double)tz[z];
+        m = (R)(g2 > 0.0 ? 4.0 * 3.14159265358979323846 / g2 * zp.scale : 0.0);
       }
-      s[z * RS + x] = cscale(s[z * RS + x], (R)m);
+      s[z * RS + x] = cscale(s[z * RS + x], m);
     }
     __syncthreads();
   }
   fft_pass<C, N, NT, true>(s, 1, RS, tw);
-  for (int i = threadIdx.x; i < N * N; i += NT) {
-    const int z = i / N, x = i - z * N;
-    data[base + (size_t)z * N * N + x] = s[z * RS + x];
-  }
+  slab_store<N, NT, RS>(data + base, s, (size_t)N * N);
 }
 
 template <typename R, int N>
@@ -93,10 +115,12 @@ static cudaError_t fft_xy_n(cudaStream_t st, const void* src, void* data, int nb
   if (inv) {
     auto kf = k_fft_xy<R, N, true>;
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     kf<<<grid, FFTThreads<N>::value, smem, st>>>((const C*)src, (C*)data, (const C*)tw);
   } else {
     auto kf = k_fft_xy<R, N, false>;
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     kf<<<grid, FFTThreads<N>::value, smem, st>>>((const C*)src, (C*)data, (const C*)tw);
   }
   return cudaGetLastError();
@@ -105,9 +129,10 @@ static cudaError_t fft_xy_n(cudaStream_t st, const void* src, void* data, int nb
 template <typename R, int N, int MODE>
 static cudaError_t fft_z_nm(cudaStream_t st, void* data, int nbatch, const void* tw, const ZParams& zp) {
   using C = typename CT<R>::type;
-  const size_t smem = (size_t)(N + N * (N + 1)) * sizeof(C);
+  const size_t smem = (size_t)(N + N * (N + 1)) * sizeof(C) + (2 * N + 2) * sizeof(R);
   auto kf = k_fft_z<R, N, MODE>;
   cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   kf<<<dim3(N, nbatch), FFTThreads<N>::value, smem, st>>>((C*)data, (const C*)tw, zp);
   return cudaGetLastError();
 }
@@ -121,18 +146,6 @@ static cudaError_t fft_z_n(cudaStream_t st, void* data, int nbatch, const void* 
   }
 }
 
-#define TDDFT_DISPATCH_N(N, CALL)          \
-  switch (N) {                             \
-    case 8: { constexpr int NN = 8; return CALL; }   \
-    case 12: { constexpr int NN = 12; return CALL; } \
-    case 16: { constexpr int NN = 16; return CALL; } \
-    case 24: { constexpr int NN = 24; return CALL; } \
-    case 32: { constexpr int NN = 32; return CALL; } \
-    case 48: { constexpr int NN = 48; return CALL; } \
-    case 64: { constexpr int NN = 64; return CALL; } \
-    case 96: { constexpr int NN = 96; return CALL; } \
-    default: return cudaErrorInvalidValue;           \
-  }
 
 template <typename R>
 cudaError_t launch_fft_xy(cudaStream_t st, int N, const void* src, void* data, int nbatch, const void* tw, bool inv) {
@@ -145,19 +158,10 @@ cudaError_t launch_fft_z(cudaStream_t st, int N, void* data, int nbatch, const v
 
 // ============================================================================ projectors
 
-template <typename R> __device__ __forceinline__ void sincos_r(R x, R* s, R* c);
-template <> __device__ __forceinline__ void sincos_r<float>(float x, float* s, float* c) { sincosf(x, s, c); }
-template <> __device__ __forceinline__ void sincos_r<double>(double x, double* s, double* c) { sincos(x, s, c); }
-
-template <typename R>
-__device__ __forceinline__ R warp_sum(R v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // One CTA per (atom, spinor): c[p][sigma] = sum_e beta_p exp(+i s.d) psi_sigma(r_e) dV, then D c.
-template <typename R, int NLM>
+// MOM < 0: projections c and D c.  MOM = a in {0, 1, 2}: moment projections
+// sum_e d_a beta_p exp(+i s.d) psi(r_e) dV only (written to c_out).
+template <typename R, int NLM, int MOM>
 __global__ void __launch_bounds__(256)
 k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTables<R> pt, R dV, EpiParams ep,
               typename CT<R>::type* __restrict__ c_out, typename CT<R>::type* __restrict__ dc_out) {
@@ -180,8 +184,12 @@ k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTable
     R sn, cs;
     sincos_r<R>(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);
     const C u = up[r], d = dn[r];
-    const R pux = u.x * cs - u.y * sn, puy = u.x * sn + u.y * cs;  // u exp(+i arg)
-    const R pdx = d.x * cs - d.y * sn, pdy = d.x * sn + d.y * cs;
+    R pux = u.x * cs - u.y * sn, puy = u.x * sn + u.y * cs;  // u exp(+i arg)
+    R pdx = d.x * cs - d.y * sn, pdy = d.x * sn + d.y * cs;
+    if (MOM >= 0) {
+      const R wgt = t[MOM];
+      pux *= wgt; puy *= wgt; pdx *= wgt; pdy *= wgt;
+    }
 #pragma unroll
     for (int p = 0; p < NLM; ++p) {
       const R bp = t[3 + p];
@@ -210,6 +218,7 @@ k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTable
     cv[threadIdx.x] = c;
     c_out[((size_t)kb * pt.natoms + a) * 2 * NLM + threadIdx.x] = c;
   }
+  if (MOM >= 0) return;
   __syncthreads();
   if (threadIdx.x < 2 * NLM) {
     const R* D = pt.Dmat + ((size_t)a * 2 * NLM + threadIdx.x) * 2 * NLM * 2;
@@ -231,16 +240,44 @@ cudaError_t launch_proj_gather(cudaStream_t st, int N, const void* psi, int nkb,
   dim3 grid(pt.natoms, nkb);
   const size_t N3 = (size_t)N * N * N;
   switch (pt.nlm) {
-    case 1: k_proj_gather<R, 1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
-    case 4: k_proj_gather<R, 4><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
-    case 9: k_proj_gather<R, 9><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
+    case 1: k_proj_gather<R, 1, -1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
+    case 4: k_proj_gather<R, 4, -1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
+    case 9: k_proj_gather<R, 9, -1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
+template <typename R, int NLM>
+static cudaError_t gather_mom_nlm(cudaStream_t st, dim3 grid, const void* psi, size_t N3, const ProjTables<R>& pt,
+                                  double dV, const EpiParams& ep, int alpha, void* m_out) {
+  using C = typename CT<R>::type;
+  switch (alpha) {
+    case 0: k_proj_gather<R, NLM, 0><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)m_out, nullptr); break;
+    case 1: k_proj_gather<R, NLM, 1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)m_out, nullptr); break;
+    default: k_proj_gather<R, NLM, 2><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)m_out, nullptr); break;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_proj_gather_mom(cudaStream_t st, int N, const void* psi, int nkb, const ProjTables<R>& pt,
+                                   double dV, const EpiParams& ep, int alpha, void* m_out) {
+  if (pt.natoms == 0) return cudaSuccess;
+  dim3 grid(pt.natoms, nkb);
+  const size_t N3 = (size_t)N * N * N;
+  switch (pt.nlm) {
+    case 1: return gather_mom_nlm<R, 1>(st, grid, psi, N3, pt, dV, ep, alpha, m_out);
+    case 4: return gather_mom_nlm<R, 4>(st, grid, psi, N3, pt, dV, ep, alpha, m_out);
+    case 9: return gather_mom_nlm<R, 9>(st, grid, psi, N3, pt, dV, ep, alpha, m_out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // ============================================================================ epilogue
 
+// Two neighbouring grid points of one spinor per thread (16-byte accesses); the spinor's D c
+// for every atom is staged in shared memory when it is small.
 template <typename R, int NLM>
 __global__ void __launch_bounds__(256)
 k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::type* Tk,
@@ -248,82 +285,117 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
            typename CT<R>::type* acc2, const R* __restrict__ V, size_t N3, ProjTables<R> pt,
            const typename CT<R>::type* __restrict__ dc, EpiParams ep) {
   using C = typename CT<R>::type;
-  constexpr int TAB = 3 + NLM;
-  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= N3) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* dcs = reinterpret_cast<C*>(smem_raw);
   const int kb = blockIdx.y;
   const int k = kb / ep.nstates;
-  const size_t ou = (size_t)(2 * kb) * N3 + r, od = ou + N3;
-  const C pu = Tk[ou], pd = Tk[od];
-  const R V0 = V[r], V1 = V[N3 + r], hx = (R)0.5 * V[2 * N3 + r], hy = (R)0.5 * V[3 * N3 + r];
-  // [[v + b_z, b_x - i b_y], [b_x + i b_y, v - b_z]] with b_x = V2/2, b_y = -V3/2
-  C ku = kin[ou], kd = kin[od];
-  C hu = cmake<C>(ku.x + V0 * pu.x + hx * pd.x - hy * pd.y, ku.y + V0 * pu.y + hx * pd.y + hy * pd.x);
-  C hd = cmake<C>(kd.x + V1 * pd.x + hx * pu.x + hy * pu.y, kd.y + V1 * pd.y + hx * pu.y - hy * pu.x);
-  if (NLM > 0) {
-    const int e0 = pt.s_ptr[r], e1 = pt.s_ptr[r + 1];
-    const R sx = (R)ep.shift[k][0], sy = (R)ep.shift[k][1], sz = (R)ep.shift[k][2];
-    for (int e = e0; e < e1; ++e) {
-      const int a = pt.s_atom[e];
-      const R* t = pt.s_tab + (size_t)e * TAB;
-      const C* dca = dc + ((size_t)kb * pt.natoms + a) * 2 * NLM;
-      R vux = 0, vuy = 0, vdx = 0, vdy = 0;
-#pragma unroll
-      for (int p = 0; p < NLM; ++p) {
-        const R bp = t[3 + p];
-        const C cu = dca[2 * p], cd = dca[2 * p + 1];
-        vux += bp * cu.x; vuy += bp * cu.y;
-        vdx += bp * cd.x; vdy += bp * cd.y;
-      }
-      R sn, cs;
-      sincos_r<R>(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);  // exp(-i arg) = cs - i sn
-      hu.x += vux * cs + vuy * sn; hu.y += vuy * cs - vux * sn;
-      hd.x += vdx * cs + vdy * sn; hd.y += vdy * cs - vdx * sn;
-    }
+  const int ncoef = pt.natoms * 2 * NLM;
+  const C* dcg = dc + (size_t)kb * ncoef;
+  if (NLM > 0 && ep.dc_staged) {
+    for (int i = threadIdx.x; i < ncoef; i += blockDim.x) dcs[i] = dcg[i];
+    __syncthreads();
   }
+  const C* dcb = (NLM > 0 && ep.dc_staged) ? dcs : dcg;
+  const size_t r = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (r >= N3) return;
+  const size_t ou = (size_t)(2 * kb) * N3 + r, od = ou + N3;
+  const Pair<C> pu2 = ld2(Tk + ou), pd2 = ld2(Tk + od);
+  const Pair<C> ku2 = ld2(kin + ou), kd2 = ld2(kin + od);
+  const C pu[2] = {pu2.a, pu2.b}, pd[2] = {pd2.a, pd2.b};
+  C hu[2] = {ku2.a, ku2.b}, hd[2] = {kd2.a, kd2.b};
+  {
+    const C v0 = *reinterpret_cast<const C*>(V + r), v1 = *reinterpret_cast<const C*>(V + N3 + r);
+    const C v2 = *reinterpret_cast<const C*>(V + 2 * N3 + r), v3 = *reinterpret_cast<const C*>(V + 3 * N3 + r);
+    const R sx = (R)ep.shift[k][0], sy = (R)ep.shift[k][1], sz = (R)ep.shift[k][2];
+    h_point<R, NLM>(hu[0], hd[0], pu[0], pd[0], v0.x, v1.x, (R)0.5 * v2.x, (R)0.5 * v3.x, r, pt, dcb, sx, sy, sz);
+    h_point<R, NLM>(hu[1], hd[1], pu[1], pd[1], v0.y, v1.y, (R)0.5 * v2.y, (R)0.5 * v3.y, r + 1, pt, dcb, sx, sy, sz);
+  }
+  auto cmulr = [](C a, R cr, R ci) { return cmake<C>(cr * a.x - ci * a.y, cr * a.y + ci * a.x); };
   if (ep.mode == EPI_APPLY) {
-    Tout[ou] = hu;
-    Tout[od] = hd;
+    st2(Tout + ou, hu[0], hu[1]);
+    st2(Tout + od, hd[0], hd[1]);
     return;
   }
-  C tu, td;
   if (ep.mode == EPI_TAYLOR) {
     const R cr = (R)ep.a1[0], ci = (R)ep.a1[1];
-    tu = cmake<C>(cr * hu.x - ci * hu.y, cr * hu.y + ci * hu.x);
-    td = cmake<C>(cr * hd.x - ci * hd.y, cr * hd.y + ci * hd.x);
-    Tout[ou] = tu; Tout[od] = td;
-    C au = acc1[ou], ad = acc1[od];
-    acc1[ou] = cadd(au, tu); acc1[od] = cadd(ad, td);
+    C tu[2], td[2];
+    for (int j = 0; j < 2; ++j) { tu[j] = cmulr(hu[j], cr, ci); td[j] = cmulr(hd[j], cr, ci); }
+    st2(Tout + ou, tu[0], tu[1]);
+    st2(Tout + od, td[0], td[1]);
+    const Pair<C> au = ld2(acc1 + ou), ad = ld2(acc1 + od);
+    st2(acc1 + ou, cadd(au.a, tu[0]), cadd(au.b, tu[1]));
+    st2(acc1 + od, cadd(ad.a, td[0]), cadd(ad.b, td[1]));
     return;
   }
   const R cc = (R)ep.c, id = (R)ep.inv_delta;
-  if (ep.mode == EPI_FIRST) {
-    tu = cmake<C>((hu.x - cc * pu.x) * id, (hu.y - cc * pu.y) * id);
-    td = cmake<C>((hd.x - cc * pd.x) * id, (hd.y - cc * pd.y) * id);
-  } else {
-    const C qu = Tkm1[ou], qd = Tkm1[od];
-    tu = cmake<C>((R)2 * (hu.x - cc * pu.x) * id - qu.x, (R)2 * (hu.y - cc * pu.y) * id - qu.y);
-    td = cmake<C>((R)2 * (hd.x - cc * pd.x) * id - qd.x, (R)2 * (hd.y - cc * pd.y) * id - qd.y);
-  }
-  Tout[ou] = tu;
-  Tout[od] = td;
-  auto upd = [&](C* acc, const double* c0, const double* c1) {
-    const R ar = (R)c1[0], ai = (R)c1[1];
-    C nu = cmake<C>(ar * tu.x - ai * tu.y, ar * tu.y + ai * tu.x);
-    C nd = cmake<C>(ar * td.x - ai * td.y, ar * td.y + ai * td.x);
-    if (ep.mode == EPI_FIRST) {
-      const R br = (R)c0[0], bi = (R)c0[1];
-      nu = cadd(nu, cmake<C>(br * pu.x - bi * pu.y, br * pu.y + bi * pu.x));
-      nd = cadd(nd, cmake<C>(br * pd.x - bi * pd.y, br * pd.y + bi * pd.x));
-    } else {
-      nu = cadd(nu, acc[ou]);
-      nd = cadd(nd, acc[od]);
+  if (ep.mode == EPI_ADJ || ep.mode == EPI_ADJ0) {
+    // Clenshaw-type adjoint recurrence: S_k = f (H - c)/Delta S_{k+1} - S_{k+2} + seeds,
+    // f = 2 (k >= 1) or 1 (k = 0); Tk holds S_{k+1}, Tkm1 holds S_{k+2} (may be null),
+    // acc1/acc2 hold the seed cotangents with coefficients a1, b1.
+    const R fct = (ep.mode == EPI_ADJ) ? (R)2 : (R)1;
+    C su[2], sd[2];
+    for (int j = 0; j < 2; ++j) {
+      su[j] = cmake<C>(fct * (hu[j].x - cc * pu[j].x) * id, fct * (hu[j].y - cc * pu[j].y) * id);
+      sd[j] = cmake<C>(fct * (hd[j].x - cc * pd[j].x) * id, fct * (hd[j].y - cc * pd[j].y) * id);
     }
-    acc[ou] = nu;
-    acc[od] = nd;
+    if (Tkm1) {
+      const Pair<C> qu = ld2(Tkm1 + ou), qd = ld2(Tkm1 + od);
+      su[0] = csub(su[0], qu.a); su[1] = csub(su[1], qu.b);
+      sd[0] = csub(sd[0], qd.a); sd[1] = csub(sd[1], qd.b);
+    }
+    if (ep.use_acc1) {
+      const Pair<C> yu = ld2(acc1 + ou), yd = ld2(acc1 + od);
+      const R ar = (R)ep.a1[0], ai = (R)ep.a1[1];
+      su[0] = cadd(su[0], cmulr(yu.a, ar, ai)); su[1] = cadd(su[1], cmulr(yu.b, ar, ai));
+      sd[0] = cadd(sd[0], cmulr(yd.a, ar, ai)); sd[1] = cadd(sd[1], cmulr(yd.b, ar, ai));
+    }
+    if (ep.use_acc2) {
+      const Pair<C> yu = ld2(acc2 + ou), yd = ld2(acc2 + od);
+      const R br = (R)ep.b1[0], bi = (R)ep.b1[1];
+      su[0] = cadd(su[0], cmulr(yu.a, br, bi)); su[1] = cadd(su[1], cmulr(yu.b, br, bi));
+      sd[0] = cadd(sd[0], cmulr(yd.a, br, bi)); sd[1] = cadd(sd[1], cmulr(yd.b, br, bi));
+    }
+    st2(Tout + ou, su[0], su[1]);
+    st2(Tout + od, sd[0], sd[1]);
+    return;
+  }
+  const bool first = ep.mode == EPI_FIRST;
+  C tu[2], td[2];
+  if (first) {
+    for (int j = 0; j < 2; ++j) {
+      tu[j] = cmake<C>((hu[j].x - cc * pu[j].x) * id, (hu[j].y - cc * pu[j].y) * id);
+      td[j] = cmake<C>((hd[j].x - cc * pd[j].x) * id, (hd[j].y - cc * pd[j].y) * id);
+    }
+  } else {
+    const Pair<C> qu = ld2(Tkm1 + ou), qd = ld2(Tkm1 + od);
+    const C qus[2] = {qu.a, qu.b}, qds[2] = {qd.a, qd.b};
+    for (int j = 0; j < 2; ++j) {
+      tu[j] = cmake<C>((R)2 * (hu[j].x - cc * pu[j].x) * id - qus[j].x, (R)2 * (hu[j].y - cc * pu[j].y) * id - qus[j].y);
+      td[j] = cmake<C>((R)2 * (hd[j].x - cc * pd[j].x) * id - qds[j].x, (R)2 * (hd[j].y - cc * pd[j].y) * id - qds[j].y);
+    }
+  }
+  st2(Tout + ou, tu[0], tu[1]);
+  st2(Tout + od, td[0], td[1]);
+  auto upd = [&](C* acc, R c0r, R c0i, R c1r, R c1i) {
+    C nu[2], nd[2];
+    for (int j = 0; j < 2; ++j) {
+      nu[j] = cmulr(tu[j], c1r, c1i);
+      nd[j] = cmulr(td[j], c1r, c1i);
+      if (first) {
+        nu[j] = cadd(nu[j], cmulr(pu[j], c0r, c0i));
+        nd[j] = cadd(nd[j], cmulr(pd[j], c0r, c0i));
+      }
+    }
+    if (!first) {
+      const Pair<C> au = ld2(acc + ou), ad = ld2(acc + od);
+      nu[0] = cadd(nu[0], au.a); nu[1] = cadd(nu[1], au.b);
+      nd[0] = cadd(nd[0], ad.a); nd[1] = cadd(nd[1], ad.b);
+    }
+    st2(acc + ou, nu[0], nu[1]);
+    st2(acc + od, nd[0], nd[1]);
   };
-  if (ep.use_acc1) upd(acc1, ep.a0, ep.a1);
-  if (ep.use_acc2) upd(acc2, ep.b0, ep.b1);
+  if (ep.use_acc1) upd(acc1, (R)ep.a0[0], (R)ep.a0[1], (R)ep.a1[0], (R)ep.a1[1]);
+  if (ep.use_acc2) upd(acc2, (R)ep.b0[0], (R)ep.b0[1], (R)ep.b1[0], (R)ep.b1[1]);
 }
 
 template <typename R>
@@ -332,14 +404,18 @@ cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void*
                             const EpiParams& ep) {
   using C = typename CT<R>::type;
   const size_t N3 = (size_t)N * N * N;
-  dim3 grid((unsigned)((N3 + 255) / 256), nkb);
+  dim3 grid((unsigned)((N3 / 2 + 255) / 256), nkb);
   const int nlm = pt.natoms > 0 ? pt.nlm : 0;
-#define EPI_ARGS (const C*)kin, (const C*)Tk, (const C*)Tkm1, (C*)Tout, (C*)acc1, (C*)acc2, V, N3, pt, (const C*)dc, ep
+  EpiParams epx = ep;
+  const size_t dcb = (size_t)pt.natoms * 2 * nlm * sizeof(C);
+  epx.dc_staged = (nlm > 0 && dcb <= 16 * 1024) ? 1 : 0;
+  const size_t smem = epx.dc_staged ? dcb : 0;
+#define EPI_ARGS (const C*)kin, (const C*)Tk, (const C*)Tkm1, (C*)Tout, (C*)acc1, (C*)acc2, V, N3, pt, (const C*)dc, epx
   switch (nlm) {
-    case 0: k_epilogue<R, 0><<<grid, 256, 0, st>>>(EPI_ARGS); break;
-    case 1: k_epilogue<R, 1><<<grid, 256, 0, st>>>(EPI_ARGS); break;
-    case 4: k_epilogue<R, 4><<<grid, 256, 0, st>>>(EPI_ARGS); break;
-    case 9: k_epilogue<R, 9><<<grid, 256, 0, st>>>(EPI_ARGS); break;
+    case 0: k_epilogue<R, 0><<<grid, 256, smem, st>>>(EPI_ARGS); break;
+    case 1: k_epilogue<R, 1><<<grid, 256, smem, st>>>(EPI_ARGS); break;
+    case 4: k_epilogue<R, 4><<<grid, 256, smem, st>>>(EPI_ARGS); break;
+    case 9: k_epilogue<R, 9><<<grid, 256, smem, st>>>(EPI_ARGS); break;
     default: return cudaErrorInvalidValue;
   }
 #undef EPI_ARGS
@@ -348,31 +424,65 @@ cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void*
 
 // ============================================================================ density
 
+// Band group g = blockIdx.y sums bands [kb0, kb1) for two neighbouring points per thread and
+// writes its partial 4-vector; with one group it writes rho directly.  The groups are then
+// added in a fixed order (deterministic result).
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_density(const typename CT<R>::type* __restrict__ psi, size_t N3, int nkb, const double* __restrict__ wf,
-          double* __restrict__ rho) {
-  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+k_density(const typename CT<R>::type* __restrict__ psi, size_t N3, int nkb, int ngroups,
+          const double* __restrict__ wf, double* __restrict__ out) {
+  const size_t r = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
   if (r >= N3) return;
-  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  for (int kb = 0; kb < nkb; ++kb) {
-    const auto u = psi[(size_t)(2 * kb) * N3 + r];
-    const auto d = psi[(size_t)(2 * kb + 1) * N3 + r];
-    const double ux = u.x, uy = u.y, dx = d.x, dy = d.y, w = wf[kb];
-    s0 += w * (ux * ux + uy * uy);
-    s1 += w * (dx * dx + dy * dy);
-    s2 += w * (ux * dx + uy * dy);   // Re(u conj d)
-    s3 += w * (uy * dx - ux * dy);   // Im(u conj d)
+  const int g = blockIdx.y;
+  const int kb0 = (int)(((long long)nkb * g) / ngroups), kb1 = (int)(((long long)nkb * (g + 1)) / ngroups);
+  double s[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+#pragma unroll 4
+  for (int kb = kb0; kb < kb1; ++kb) {
+    const Pair<typename CT<R>::type> u = ld2(psi + (size_t)(2 * kb) * N3 + r);
+    const Pair<typename CT<R>::type> d = ld2(psi + (size_t)(2 * kb + 1) * N3 + r);
+    const double w = wf[kb];
+    const double ux[2] = {(double)u.a.x, (double)u.b.x}, uy[2] = {(double)u.a.y, (double)u.b.y};
+    const double dx[2] = {(double)d.a.x, (double)d.b.x}, dy[2] = {(double)d.a.y, (double)d.b.y};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      s[j][0] += w * (ux[j] * ux[j] + uy[j] * uy[j]);
+      s[j][1] += w * (dx[j] * dx[j] + dy[j] * dy[j]);
+      s[j][2] += w * (ux[j] * dx[j] + uy[j] * dy[j]);  // Re(u conj d)
+      s[j][3] += w * (uy[j] * dx[j] - ux[j] * dy[j]);  // Im(u conj d)
+    }
   }
-  rho[r] = s0;
-  rho[N3 + r] = s1;
-  rho[2 * N3 + r] = s2;
-  rho[3 * N3 + r] = s3;
+  double* o = out + (size_t)g * 4 * N3;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) *reinterpret_cast<double2*>(o + c * N3 + r) = make_double2(s[0][c], s[1][c]);
+}
+
+__global__ void k_density_reduce(size_t n, int ngroups, const double* __restrict__ part, double* __restrict__ rho) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t = 0.0;
+  for (int g = 0; g < ngroups; ++g) t += part[(size_t)g * n + i];
+  rho[i] = t;
+}
+
+int density_groups(size_t N3, int nkb) {
+  // enough resident threads to hide the load latency: about 6e5 threads
+  const size_t per = N3 / 2;
+  int g = (int)((600000 + per - 1) / per);
+  if (g > nkb) g = nkb;
+  if (g > 16) g = 16;
+  return g < 1 ? 1 : g;
 }
 
 template <typename R>
-cudaError_t launch_density(cudaStream_t st, size_t N3, const void* psi, int nkb, const double* wf, double* rho) {
-  k_density<R><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>((const typename CT<R>::type*)psi, N3, nkb, wf, rho);
+cudaError_t launch_density(cudaStream_t st, size_t N3, const void* psi, int nkb, const double* wf, double* rho,
+                           double* part) {
+  const int G = part ? density_groups(N3, nkb) : 1;
+  const size_t nthreads = N3 / 2;
+  dim3 grid((unsigned)((nthreads + 255) / 256), G);
+  k_density<R><<<grid, 256, 0, st>>>((const typename CT<R>::type*)psi, N3, nkb, G, wf, G == 1 ? rho : part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || G == 1) return e;
+  k_density_reduce<<<(unsigned)((4 * N3 + 255) / 256), 256, 0, st>>>(4 * N3, G, part, rho);
   return cudaGetLastError();
 }
 
@@ -658,6 +768,66 @@ cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, dou
   return cudaGetLastError();
 }
 
+// ============================================================================ per-atom moments
+// Nearest atom of every grid point (minimum image), Algorithm 1's NearestAtom rule; equal
+// distances go to the lowest atom index.  Every operation is explicitly rounded (no fused
+// multiply-add) so that ties resolve the same way as in a plain IEEE evaluation of
+// d = x h - R, d -= L rint(d / L), |d|^2 = (dx^2 + dy^2) + dz^2.
+__global__ void k_voronoi_owner(int N, double hx, double hy, double hz, double Lx, double Ly, double Lz, int natoms,
+                                const double* __restrict__ pos, int* __restrict__ owner) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t N3 = (size_t)N * N * N;
+  if (i >= N3) return;
+  const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((size_t)N * N));
+  const double rx = __dmul_rn((double)x, hx), ry = __dmul_rn((double)y, hy), rz = __dmul_rn((double)z, hz);
+  double best = 1e300;
+  int own = 0;
+  for (int a = 0; a < natoms; ++a) {
+    double dx = __dsub_rn(rx, pos[3 * a]), dy = __dsub_rn(ry, pos[3 * a + 1]), dz = __dsub_rn(rz, pos[3 * a + 2]);
+    dx = __dsub_rn(dx, __dmul_rn(Lx, rint(__ddiv_rn(dx, Lx))));
+    dy = __dsub_rn(dy, __dmul_rn(Ly, rint(__ddiv_rn(dy, Ly))));
+    dz = __dsub_rn(dz, __dmul_rn(Lz, rint(__ddiv_rn(dz, Lz))));
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (d2 < best) {
+      best = d2;
+      own = a;
+    }
+  }
+  owner[i] = own;
+}
+cudaError_t launch_voronoi_owner(cudaStream_t st, int N, const double* L, int natoms, const double* pos, int* owner) {
+  const size_t N3 = (size_t)N * N * N;
+  k_voronoi_owner<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N, L[0] / N, L[1] / N, L[2] / N, L[0], L[1], L[2],
+                                                               natoms, pos, owner);
+  return cudaGetLastError();
+}
+
+// out[a] = {sum m_x, sum m_y, sum m_z, sum n} over the points owned by atom a (one CTA per atom,
+// fixed order; multiply by dV on the host).
+__global__ void __launch_bounds__(256) k_atom_sums(size_t N3, const double* __restrict__ rho,
+                                                   const int* __restrict__ owner, double* __restrict__ out) {
+  __shared__ double sh[8];
+  const int a = blockIdx.x;
+  double acc[4] = {0, 0, 0, 0};
+  for (size_t r = threadIdx.x; r < N3; r += 256) {
+    if (owner[r] != a) continue;
+    const double r0 = rho[r], r1 = rho[N3 + r], r2 = rho[2 * N3 + r], r3 = rho[3 * N3 + r];
+    acc[0] += 2.0 * r2;
+    acc[1] += -2.0 * r3;
+    acc[2] += r0 - r1;
+    acc[3] += r0 + r1;
+  }
+  for (int c = 0; c < 4; ++c) {
+    const double t = block_sum<256>(acc[c], sh);
+    if (threadIdx.x == 0) out[4 * a + c] = t;
+    __syncthreads();
+  }
+}
+cudaError_t launch_atom_sums(cudaStream_t st, size_t N3, int natoms, const double* rho, const int* owner, double* out) {
+  k_atom_sums<<<natoms, 256, 0, st>>>(N3, rho, owner, out);
+  return cudaGetLastError();
+}
+
 // ============================================================================ instantiations
 #define TDDFT_INST(R)                                                                                           \
   template cudaError_t launch_fft_xy<R>(cudaStream_t, int, const void*, void*, int, const void*, bool);                       \
@@ -667,11 +837,14 @@ cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, dou
   template cudaError_t launch_epilogue<R>(cudaStream_t, int, const void*, const void*, const void*, void*, void*, \
                                           void*, const R*, const ProjTables<R>&, const void*, int,              \
                                           const EpiParams&);                                                    \
-  template cudaError_t launch_density<R>(cudaStream_t, size_t, const void*, int, const double*, double*);        \
+  template cudaError_t launch_density<R>(cudaStream_t, size_t, const void*, int, const double*, double*,         \
+                                         double*);                                                                \
   template cudaError_t launch_convert_in<R>(cudaStream_t, size_t, const double2*, void*);                        \
   template cudaError_t launch_convert_out<R>(cudaStream_t, size_t, const void*, double2*);                       \
   template cudaError_t launch_band_dot<R>(cudaStream_t, size_t, int, const void*, const void*, double*);         \
-  template cudaError_t launch_nl_energy<R>(cudaStream_t, int, int, const void*, const void*, double*);
+  template cudaError_t launch_nl_energy<R>(cudaStream_t, int, int, const void*, const void*, double*);          \
+  template cudaError_t launch_proj_gather_mom<R>(cudaStream_t, int, const void*, int, const ProjTables<R>&,      \
+                                                 double, const EpiParams&, int, void*);
 
 TDDFT_INST(float)
 TDDFT_INST(double)

@@ -190,3 +190,70 @@ def test_error_paths_on_device(lib):
     with pytest.raises(_lib.TddftError):
         h.get_states()
     h.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-5)])
+def test_fused_term_path_matches_oracle(lib, precision, tol, monkeypatch):
+    """The fused Chebyshev term kernel (inverse xy FFT + epilogue + forward xy FFT in one launch)
+    gives the same results as the default five-launch term."""
+    monkeypatch.setenv("TDDFT_FUSED", "1")
+    wl = S.small_parity(n=16, nstates=3, nk=2, natoms=3)
+    psi0 = S.small_parity_states(wl)
+    rows, psi_g, o = run_pair(lib, wl, psi0, 2, (-20.0, 100.0), precision=precision)
+    for r in rows:
+        assert r["n"] <= tol and r["m"] <= tol
+
+
+def test_largest_grid_fp64_96(lib):
+    """Maximum grid (96^3) in FP64, one atom with SOC."""
+    wl = S.small_parity(n=96, nstates=1, nk=1, natoms=1, field=False)
+    Lc = 24.0
+    wl.L = np.array([Lc, Lc, Lc])
+    wl.pos = np.array([[12.1, 11.9, 12.3]])
+    wl.r_cut = 3.0
+    wl.dt = 0.01
+    g = np.fft.fftfreq(96) * 96 * 2 * math.pi / Lc
+    rng = np.random.default_rng(2)
+    psi0 = np.zeros((1, 1, 2, 96, 96, 96), np.complex128)
+    iz, iy, ix = np.meshgrid(np.arange(96), np.arange(96), np.arange(96), indexing="ij")
+    r = np.stack([ix, iy, iz], -1) * Lc / 96
+    d2 = ((r - wl.pos[0]) ** 2).sum(-1)
+    base = np.exp(-d2 / 4.0) * (1 + 0.3 * np.cos(r[..., 0] * g[3]))
+    psi0[0, 0, 0] = base * (0.8 + 0.1j)
+    psi0[0, 0, 1] = base * (0.3 - 0.5j) * np.exp(1j * r[..., 1] * g[2])
+    psi0 /= math.sqrt((np.abs(psi0) ** 2).sum() * Lc ** 3 / 96 ** 3)
+    # kinetic maximum 1/2 * 3 (pi / h)^2 = 237 Ha at h = 0.25 bohr
+    rows, psi_g, o = run_pair(lib, wl, psi0, 1, (-30.0, 270.0))
+    for r_ in rows:
+        assert r_["n"] <= 1e-10 and r_["m"] <= 1e-10
+    assert rel(psi_g, o.psi) <= 1e-10
+
+
+@pytest.mark.parametrize("proj_mode,tol", [(3, 2e-5), (2, 3e-3)])
+@pytest.mark.parametrize("nstates", [5, 40])
+def test_tensor_core_projectors_apply_h(lib, proj_mode, tol, nstates):
+    """tcgen05 projector contraction (TF32 x3 and TF32) in the FP32-mixed Hamiltonian against the
+    oracle; 5 states give one ragged 64-component tile, 40 states two tiles per k-point."""
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=nstates, nk=2, natoms=3)
+    psi0 = S.small_parity_states(wl)
+    h = _lib.TDDFT.from_workload(wl, precision=1, proj_mode=proj_mode, e_min=-20, e_max=100)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi0, 0.1)
+    hpsi = h.apply_hamiltonian(psi0)
+    h.close()
+    s = System.from_workload(wl)
+    o = Oracle(s, FieldTable(wl.times, wl.A, wl.B), wl.dt, psi0, t0=0.1, bounds=(-20, 100))
+    A, _ = o.f.at(0.1)
+    ref = s.apply_h(psi0, o.V, A)
+    vnl = np.stack([s.apply_nonlocal(psi0[ik], wl.kpts[ik] + A) for ik in range(wl.nk)])
+    # the error budget is set by the non-local part
+    assert np.abs(hpsi - ref).max() <= tol * np.abs(vnl).max() + 2e-5 * np.abs(ref).max()
+
+
+def test_tensor_core_projectors_step_parity(lib):
+    wl = S.small_parity(n=16, nstates=5, nk=2, natoms=3)
+    psi0 = S.small_parity_states(wl)
+    rows, psi_g, o = run_pair(lib, wl, psi0, 2, (-20.0, 100.0), precision=1, proj_mode=3)
+    for r in rows:
+        assert r["n"] <= 2e-5 and r["m"] <= 2e-5, r

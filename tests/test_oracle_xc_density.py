@@ -100,3 +100,20 @@ def test_rho_v_and_magnetisation_identities():
     rv = nn * np.array([(1 + mm[2]) / 2, (1 - mm[2]) / 2, mm[0] / 2, -mm[1] / 2])
     n2, m2 = System.n_m(rv)
     assert n2 == pytest.approx(nn) and np.allclose(m2, M)
+
+
+def test_voronoi_atom_moments_partition_the_totals():
+    """Per-atom moments over nearest-atom cells (Algorithm 1's NearestAtom) add up to M and N;
+    the ownership matches a brute-force nearest-atom search over all periodic images."""
+    from tests._systems import parity_system
+    wl, s, psi = parity_system(n=12, nstates=3, nk=1, natoms=3)
+    rho = s.rho_v(psi)
+    M, N = s.atom_moments(rho)
+    n, m = System.n_m(rho)
+    assert np.allclose(M.sum(axis=0), m.sum(axis=(1, 2, 3)) * s.grid.dV, atol=1e-13)
+    assert N.sum() == pytest.approx(n.sum() * s.grid.dV, rel=1e-13)
+    owner = s.voronoi_owner()
+    r = s.grid.r.reshape(-1, 3)
+    shifts = np.array([[i, j, k] for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)]) * s.grid.L
+    dist = np.stack([np.min(np.linalg.norm(r[:, None, :] - (R + shifts)[None], axis=2), axis=1) for R in s.pos])
+    assert np.all(dist[owner, np.arange(len(r))] <= dist.min(axis=0) + 1e-12)
