@@ -137,6 +137,36 @@ def time_oracle(nbands, steps, warm=0):
 
 
 # --------------------------------------------------------------------------- ours
+def kernel_source_hash():
+    """SHA-256 over the CUDA sources, to tie a stored ncu traffic figure to the kernels it measured."""
+    import hashlib
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2506_21908_gb300", "csrc")
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel_class, units_per_launch):
+    """DRAM bytes (read + write) per launch of `kernel_class` from the committed ncu summary
+    profiles/traffic_<class>_cluster64_fp32mixed.txt (bytes per spinor-gridpoint unit, averaged over
+    the launches of one step), scaled to this launch size; None when there is no summary or the
+    kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic_%s_cluster64_fp32mixed.txt" % kernel_class)
+    if not os.path.exists(path):
+        return None, "no ncu summary for this kernel"
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith((" ", "#")):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256") != kernel_source_hash():
+        return None, "kernels changed since the ncu capture (%s)" % os.path.basename(path)
+    return float(kv["dram_bytes_per_unit"]) * units_per_launch, os.path.basename(path)
+
+
 def run_ours(args):
     import torch
     rank, world, local = env_rank()
@@ -217,8 +247,9 @@ def run_ours(args):
     avg_ms = pk["ms"] / max(pk["launches"], 1)
     bytes_per_launch = pk["bytes"] / max(pk["launches"], 1)
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    traffic, traffic_src = measured_traffic(dom, wl.nk * psi0.shape[1] * wl.ng)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_source": peak_src, "traffic": None,
+                "frac": achieved / hbm, "peak_source": peak_src, "traffic": traffic, "traffic_source": traffic_src,
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                 "share": pk["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9)}
     kernels = {k: {"ms_total": v["ms"], "launches": v["launches"],

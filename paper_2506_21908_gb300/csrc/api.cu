@@ -180,6 +180,7 @@ struct tddft_ctx {
   int K_full = 0, K_half = 0;
   std::vector<cd> cf_full, cf_half;
   bool use_fused = false;  // fused term kernel (where two planes fit in shared memory)
+  bool use_cluster = false;  // one-kernel kinetic term on 16-CTA clusters (FP32, n = 32, 48, 64)
   // device memory
   cudaStream_t st = nullptr;
   std::vector<void*> allocs;
@@ -519,6 +520,10 @@ template <typename R> tddft_status kinetic(tddft_ctx* c, const void* in, void* o
   const int nbatch = 2 * c->nkb;
   const double by = 2.0 * nbatch * (double)c->N3 * 2 * sizeof(R);
   tddft_status s;
+  if (c->use_cluster && c->prec != TDDFT_FP64 && kinetic_cluster_supported(c->N))
+    return c->launch(KC_FFT_Z, "kinetic cluster", [&] {
+      return launch_kinetic_cluster(c->st, c->N, in, out, nbatch, c->tw, zp);
+    }, by);
   if ((s = c->launch(KC_FFT_XY, "fft xy", [&] { return launch_fft_xy<R>(c->st, c->N, in, out, nbatch, c->tw, false); }, by))) return s;
   if ((s = c->launch(KC_FFT_Z, "fft z", [&] { return launch_fft_z<R>(c->st, c->N, out, nbatch, c->tw, Z_KIN, zp); }, by))) return s;
   return c->launch(KC_FFT_XY, "ifft xy", [&] { return launch_fft_xy<R>(c->st, c->N, out, out, nbatch, c->tw, true); }, by);
@@ -602,6 +607,30 @@ tddft_status cheb_series_fused(tddft_ctx* c, const void* in, const R* Vr, const 
   return TDDFT_OK;
 }
 
+// Accumulation schedule of one series acc = sum_{i <= Ka} cf[i] T_i in the unfused recurrence:
+// epilogue k has T_{k-1}, T_k and T_{k+1} in registers, so the accumulator is touched only
+// when three terms are pending or T_{k+1} is its last term (one read-modify-write per three
+// terms instead of one per term).  `done` is the first term not yet added; the first update
+// writes without reading.  Coefficients go to cm (T_{k-1}), c0 (T_k) and c1 (T_{k+1}).
+static void acc_schedule(int k, int Ka, const std::vector<cd>& cf, int& done, int& use, int& init, double* cm,
+                         double* c0, double* c1) {
+  use = 0;
+  init = 0;
+  cm[0] = cm[1] = c0[0] = c0[1] = c1[0] = c1[1] = 0.0;
+  const int last = k + 1;
+  if (done > Ka || last > Ka) return;
+  if (last - done + 1 < 3 && last != Ka) return;
+  use = 1;
+  init = (done == 0);
+  double* slot[3] = {cm, c0, c1};
+  for (int i = done; i <= last; ++i) {
+    double* d = slot[i - (k - 1)];
+    d[0] = cf[i].real();
+    d[1] = cf[i].imag();
+  }
+  done = last + 1;
+}
+
 // One Chebyshev series: T_k of H~ = (H - c)/Delta applied to `in`, accumulated with
 // coefficients cf1 (orders 0..K1) into acc1 and, when acc2 is set, cf2 (0..K2) into acc2.
 template <typename R>
@@ -620,6 +649,7 @@ tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double
   tddft_status s;
   if (c->use_fused && fused_supported<R>(c->N))
     return cheb_series_fused<R>(c, in, Vr, A, acc1, cf1, K1, acc2, cf2, K2, ep, slots);
+  int done1 = 0, done2 = 0;
   for (int k = 0; k < K; ++k) {
     if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
     if ((s = gather<R>(c, cur, A))) return s;
@@ -629,19 +659,12 @@ tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double
     else if (prev == in) out = (cur == c->Ta) ? c->Tb : c->Ta;
     else out = const_cast<void*>(prev);
     ep.mode = (k == 0) ? EPI_FIRST : EPI_RECUR;
-    ep.use_acc1 = (k + 1 <= K1);
-    ep.use_acc2 = (acc2 != nullptr && k + 1 <= K2);
-    if (ep.use_acc1) {
-      ep.a0[0] = cf1[0].real(); ep.a0[1] = cf1[0].imag();
-      ep.a1[0] = cf1[k + 1].real(); ep.a1[1] = cf1[k + 1].imag();
-    }
-    if (ep.use_acc2) {
-      ep.b0[0] = cf2[0].real(); ep.b0[1] = cf2[0].imag();
-      ep.b1[0] = cf2[k + 1].real(); ep.b1[1] = cf2[k + 1].imag();
-    }
+    acc_schedule(k, K1, cf1, done1, ep.use_acc1, ep.init1, ep.am, ep.a0, ep.a1);
+    if (acc2) acc_schedule(k, K2, cf2, done2, ep.use_acc2, ep.init2, ep.bm, ep.b0, ep.b1);
+    else ep.use_acc2 = 0;
     const void* tkm1 = (k == 0) ? nullptr : prev;
-    const int nacc = ep.use_acc1 + ep.use_acc2;
-    const double streams = 3.0 + (k == 0 ? 0.0 : 1.0) + nacc * (k == 0 ? 1.0 : 2.0);
+    const double streams = 3.0 + (k == 0 ? 0.0 : 1.0) + (ep.use_acc1 ? (ep.init1 ? 1.0 : 2.0) : 0.0) +
+                           (ep.use_acc2 ? (ep.init2 ? 1.0 : 2.0) : 0.0);
     const double by = streams * c->psi_elems() * 2 * sizeof(R) + 4.0 * c->N3 * sizeof(R);
     if ((s = c->launch(KC_EPI, "chebyshev epilogue", [&] {
            return launch_epilogue<R>(c->st, c->N, c->tmp, cur, tkm1, out, acc1, acc2, Vr, pt, c->dcbuf, c->nkb, ep);
@@ -1412,6 +1435,10 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
     // faster form on this part.  TDDFT_FUSED=1 selects the fused term kernel (same results).
     const char* e = std::getenv("TDDFT_FUSED");
     c->use_fused = (e && e[0] == '1');
+    // TDDFT_CLUSTER=1 selects the one-kernel cluster kinetic term (same results; slower on
+    // this part than the three passes, which overlap HBM traffic and shared-memory FFTs better).
+    const char* f = std::getenv("TDDFT_CLUSTER");
+    c->use_cluster = f && f[0] == '1';
   }
   if (atoms->natoms < 0 || (atoms->natoms > 0 && (!atoms->pos || !atoms->species))) return c->fail(TDDFT_ERR_ARG, "bad atoms");
   c->natoms = atoms->natoms;

@@ -165,27 +165,23 @@ __device__ __forceinline__ void fft_pass(C* s, int rs, int es, const C* tw, int 
   fft_pass_impl<C, N, NT, INV, NP>(s, rs, es, ps, tw, typename FFTPlan<N>::type{});
 }
 
-// Copy an N x N plane between global memory (dense rows) and shared memory (row stride RS),
-// 16 bytes per global access.
+// Copy an N x N plane between global memory (dense rows) and shared memory (odd row stride RS).
+// Consecutive lanes take consecutive elements (8-byte accesses): with the odd pitch a 16-byte
+// access per lane would hit shared memory at a 2-element stride and conflict 4 ways.
 template <int N, int NT, int RS>
 __device__ __forceinline__ void plane_load(float2* s, const float2* __restrict__ g) {
-  const float4* g4 = reinterpret_cast<const float4*>(g);
-#pragma unroll 4
-  for (int i = threadIdx.x; i < N * N / 2; i += NT) {
-    const float4 v = g4[i];
-    const int idx = 2 * i, row = idx / N, col = idx - row * N;
-    s[row * RS + col] = make_float2(v.x, v.y);
-    s[row * RS + col + 1] = make_float2(v.z, v.w);
+#pragma unroll 8
+  for (int i = threadIdx.x; i < N * N; i += NT) {
+    const int row = i / N, col = i - row * N;
+    s[row * RS + col] = g[i];
   }
 }
 template <int N, int NT, int RS>
 __device__ __forceinline__ void plane_store(float2* __restrict__ g, const float2* s) {
-  float4* g4 = reinterpret_cast<float4*>(g);
-#pragma unroll 4
-  for (int i = threadIdx.x; i < N * N / 2; i += NT) {
-    const int idx = 2 * i, row = idx / N, col = idx - row * N;
-    const float2 a = s[row * RS + col], b = s[row * RS + col + 1];
-    g4[i] = make_float4(a.x, a.y, b.x, b.y);
+#pragma unroll 8
+  for (int i = threadIdx.x; i < N * N; i += NT) {
+    const int row = i / N, col = i - row * N;
+    g[i] = s[row * RS + col];
   }
 }
 template <int N, int NT, int RS>
@@ -204,24 +200,39 @@ __device__ __forceinline__ void plane_store(double2* __restrict__ g, const doubl
     g[i] = s[row * RS + col];
   }
 }
-// Strided variant for z slabs: row z of the slab starts at g + z * gstride (elements).
+// Strided variant for z slabs: row z of the slab starts at g + z * gstride (elements).  With an
+// even pitch (RS = N, used by the z pass, whose FFT accesses are conflict-free for any pitch)
+// 16-byte accesses are used on both sides; otherwise 8-byte accesses as in plane_load.
 template <int N, int NT, int RS>
 __device__ __forceinline__ void slab_load(float2* s, const float2* __restrict__ g, size_t gstride) {
+  if constexpr (RS % 2 == 0) {
 #pragma unroll 4
-  for (int i = threadIdx.x; i < N * N / 2; i += NT) {
-    const int idx = 2 * i, row = idx / N, col = idx - row * N;
-    const float4 v = *reinterpret_cast<const float4*>(g + row * gstride + col);
-    s[row * RS + col] = make_float2(v.x, v.y);
-    s[row * RS + col + 1] = make_float2(v.z, v.w);
+    for (int i = threadIdx.x; i < N * N / 2; i += NT) {
+      const int idx = 2 * i, row = idx / N, col = idx - row * N;
+      *reinterpret_cast<float4*>(s + row * RS + col) = *reinterpret_cast<const float4*>(g + row * gstride + col);
+    }
+  } else {
+#pragma unroll 8
+    for (int i = threadIdx.x; i < N * N; i += NT) {
+      const int row = i / N, col = i - row * N;
+      s[row * RS + col] = g[row * gstride + col];
+    }
   }
 }
 template <int N, int NT, int RS>
 __device__ __forceinline__ void slab_store(float2* __restrict__ g, const float2* s, size_t gstride) {
+  if constexpr (RS % 2 == 0) {
 #pragma unroll 4
-  for (int i = threadIdx.x; i < N * N / 2; i += NT) {
-    const int idx = 2 * i, row = idx / N, col = idx - row * N;
-    const float2 a = s[row * RS + col], b = s[row * RS + col + 1];
-    *reinterpret_cast<float4*>(g + row * gstride + col) = make_float4(a.x, a.y, b.x, b.y);
+    for (int i = threadIdx.x; i < N * N / 2; i += NT) {
+      const int idx = 2 * i, row = idx / N, col = idx - row * N;
+      *reinterpret_cast<float4*>(g + row * gstride + col) = *reinterpret_cast<const float4*>(s + row * RS + col);
+    }
+  } else {
+#pragma unroll 8
+    for (int i = threadIdx.x; i < N * N; i += NT) {
+      const int row = i / N, col = i - row * N;
+      g[row * gstride + col] = s[row * RS + col];
+    }
   }
 }
 template <int N, int NT, int RS>
@@ -240,3 +251,64 @@ __device__ __forceinline__ void slab_store(double2* __restrict__ g, const double
     g[row * gstride + col] = s[row * RS + col];
   }
 }
+
+// ---------------------------------------------------------------------------- two-factor form
+//
+// A length-N line with N = R1 R2 is transformed by two register DFTs and one exchange through
+// shared memory (Cooley-Tukey with n = n0 + R1 n1, K = K0 + R2 K1):
+//     X[K0 + R2 K1] = sum_{n0} w_{R1}^{n0 K1} ( w_N^{n0 K0} sum_{n1} x[n0 + R1 n1] w_{R2}^{n1 K0} ).
+// "A side": one work item per (line, n0) holds the R2 values x[n0 + R1 n1]; a DFT of length R2
+// and the twiddle w_N^{n0 K0} give the exchange values E[K0][n0].  "B side": one item per
+// (line, K0) holds E[K0][0..R1) and a DFT of length R1 gives X[K0 + R2 K1].  The inverse runs
+// the same two steps backwards (B side first, conjugate twiddle), so a forward and an inverse
+// transform share the exchange layout.  The first and last steps can read and write global
+// memory directly, leaving one shared-memory round trip per axis.
+
+template <typename C, bool INV> struct SmallDFT<C, 6, INV> {
+  // 6 = 2 x 3: three-point DFTs over n1 (n = n0 + 2 n1), twiddle w6^{n0 k0}, two-point DFTs over n0
+  __device__ __forceinline__ static void run(C* v) {
+    using R = decltype(C::x);
+    const R h = (R)0.8660254037844386467637;  // sin(pi/3)
+    C a[3] = {v[0], v[2], v[4]};
+    C b[3] = {v[1], v[3], v[5]};
+    SmallDFT<C, 3, INV>::run(a);
+    SmallDFT<C, 3, INV>::run(b);
+    const R sg = INV ? (R)1 : (R)-1;  // w6 = 1/2 + sg i h, w6^2 = -1/2 + sg i h
+    const C b1 = cmul(b[1], cmake<C>((R)0.5, sg * h));
+    const C b2 = cmul(b[2], cmake<C>((R)-0.5, sg * h));
+    v[0] = cadd(a[0], b[0]); v[3] = csub(a[0], b[0]);
+    v[1] = cadd(a[1], b1);   v[4] = csub(a[1], b1);
+    v[2] = cadd(a[2], b2);   v[5] = csub(a[2], b2);
+  }
+};
+
+template <int N> struct TwoFactor { static constexpr bool ok = false; };
+template <> struct TwoFactor<16> { static constexpr bool ok = true; static constexpr int R1 = 4, R2 = 4; };
+template <> struct TwoFactor<24> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 3; };
+template <> struct TwoFactor<32> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 4; };
+template <> struct TwoFactor<48> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 6; };
+template <> struct TwoFactor<64> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 8; };
+
+// A side, forward: v[n1] = x[n0 + R1 n1] -> v[K0] = E[K0][n0].
+template <typename C, int N, bool INV> struct TF;
+template <typename C, int N> struct TF<C, N, false> {
+  static constexpr int R1 = TwoFactor<N>::R1, R2 = TwoFactor<N>::R2;
+  __device__ __forceinline__ static void a_side(C* v, int n0, const C* tw) {
+    SmallDFT<C, R2, false>::run(v);
+#pragma unroll
+    for (int k0 = 1; k0 < R2; ++k0) v[k0] = cmul(v[k0], tw[k0 * n0]);
+  }
+  // B side, forward: u[n0] = E[K0][n0] -> u[K1] = X[K0 + R2 K1].
+  __device__ __forceinline__ static void b_side(C* u, int, const C*) { SmallDFT<C, R1, false>::run(u); }
+};
+template <typename C, int N> struct TF<C, N, true> {
+  static constexpr int R1 = TwoFactor<N>::R1, R2 = TwoFactor<N>::R2;
+  // B side, inverse: u[K1] = X[K0 + R2 K1] -> u[n0] = E[K0][n0] (conjugate twiddle).
+  __device__ __forceinline__ static void b_side(C* u, int k0, const C* tw) {
+    SmallDFT<C, R1, true>::run(u);
+#pragma unroll
+    for (int n0 = 1; n0 < R1; ++n0) u[n0] = cmulc(u[n0], tw[k0 * n0]);
+  }
+  // A side, inverse: v[K0] = E[K0][n0] -> v[n1] = x[n0 + R1 n1].
+  __device__ __forceinline__ static void a_side(C* v, int, const C*) { SmallDFT<C, R2, true>::run(v); }
+};

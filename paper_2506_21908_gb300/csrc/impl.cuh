@@ -31,9 +31,11 @@ enum EpiMode { EPI_APPLY = 0, EPI_FIRST = 1, EPI_RECUR = 2, EPI_TAYLOR = 3, EPI_
 struct EpiParams {
   int mode;
   double c, inv_delta;          // H~ = (H - c) / Delta
-  double a0[2], a1[2];          // accumulator 1 coefficients (k = 0 and current k), complex
+  double a0[2], a1[2];          // accumulator 1 coefficients on T_k and T_{k+1}, complex
   double b0[2], b1[2];          // accumulator 2 coefficients
+  double am[2], bm[2];          // unfused recurrence: coefficients on T_{k-1} (accumulators 1, 2)
   int use_acc1, use_acc2;
+  int init1, init2;             // unfused recurrence: write the accumulator without reading it
   double shift[kMaxK][3];       // k + A(t), for projector phases
   int nstates;
   int dc_staged;                // fused kernel: D c copied to shared memory (set by its launcher)
@@ -64,6 +66,12 @@ template <typename R>
 cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* Tk, const void* Tkm1,
                             void* Tout, void* acc1, void* acc2, const R* V, const ProjTables<R>& pt,
                             const void* dc, int nkb, const EpiParams& ep);
+// Whole kinetic term of each spinor component in one kernel (16-CTA clusters, FP32, n in
+// {32, 48, 64}): out = IFFT(1/2 |G + k + A|^2 FFT(in)).
+bool kinetic_cluster_supported(int N);
+cudaError_t launch_kinetic_cluster(cudaStream_t st, int N, const void* in, void* out, int nbatch, const void* tw,
+                                   const ZParams& zp);
+
 // Fused inverse-xy FFT + Chebyshev epilogue + forward-xy FFT of T_{k+1} (FIRST/RECUR modes).
 template <typename R> bool fused_supported(int N);
 template <typename R>

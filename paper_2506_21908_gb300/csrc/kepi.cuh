@@ -20,6 +20,30 @@ __device__ __forceinline__ void st2(float2* p, float2 a, float2 b) {
 __device__ __forceinline__ Pair<double2> ld2(const double2* p) { return {p[0], p[1]}; }
 __device__ __forceinline__ void st2(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
 
+// One row of a projector table (3 + NLM values: d, beta).  Rows whose size is a multiple of
+// 16 bytes start on 16-byte boundaries (the table is one allocation) and are read as vectors.
+template <typename R, int TAB>
+__device__ __forceinline__ void load_row(const R* __restrict__ t, R* v) {
+  if constexpr (sizeof(R) == 4 && TAB % 4 == 0) {
+    const float4* t4 = reinterpret_cast<const float4*>(t);
+#pragma unroll
+    for (int i = 0; i < TAB / 4; ++i) {
+      const float4 q = __ldg(t4 + i);
+      v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+    }
+  } else if constexpr (sizeof(R) == 8 && TAB % 2 == 0) {
+    const double2* t2 = reinterpret_cast<const double2*>(t);
+#pragma unroll
+    for (int i = 0; i < TAB / 2; ++i) {
+      const double2 q = __ldg(t2 + i);
+      v[2 * i] = q.x; v[2 * i + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < TAB; ++i) v[i] = __ldg(t + i);
+  }
+}
+
 // phase exp(-i arg): FP32 reduces the argument to [-pi, pi] and uses the fast intrinsic
 __device__ __forceinline__ void phase_sincos(float x, float* sn, float* cs) {
   const float r = x - 6.28318530717958647692f * rintf(x * 0.15915494309189533577f);
@@ -41,15 +65,16 @@ __device__ __forceinline__ void h_point(typename CT<R>::type& hu, typename CT<R>
     const int e0 = pt.s_ptr[r], e1 = pt.s_ptr[r + 1];
     for (int e = e0; e < e1; ++e) {
       const int a = pt.s_atom[e];
-      const R* t = pt.s_tab + (size_t)e * TAB;
-      const C* dca = dcb + (size_t)a * 2 * NLM;  // this spinor's D c of atom a
+      R t[TAB];
+      load_row<R, TAB>(pt.s_tab + (size_t)e * TAB, t);
+      const C* dca = dcb + (size_t)a * 2 * NLM;  // this spinor's D c of atom a, (up, dn) per p
       R vux = 0, vuy = 0, vdx = 0, vdy = 0;
 #pragma unroll
       for (int p = 0; p < NLM; ++p) {
         const R bp = t[3 + p];
-        const C cu = dca[2 * p], cd = dca[2 * p + 1];
-        vux += bp * cu.x; vuy += bp * cu.y;
-        vdx += bp * cd.x; vdy += bp * cd.y;
+        const Pair<C> cc = ld2(dca + 2 * p);
+        vux += bp * cc.a.x; vuy += bp * cc.a.y;
+        vdx += bp * cc.b.x; vdy += bp * cc.b.y;
       }
       R sn, cs;
       phase_sincos(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);
@@ -58,6 +83,7 @@ __device__ __forceinline__ void h_point(typename CT<R>::type& hu, typename CT<R>
     }
   }
 }
+
 
 
 }  // namespace tddft

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::valu
 k_fft_z(typename CT<R>::type* __restrict__ data, const typename CT<R>::type* __restrict__ twg, ZParams zp) {
   using C = typename CT<R>::type;
   constexpr int NT = FFTThreads<N>::value;
-  constexpr int RS = N + 1;
+  // dense slab [z][x]: the z transforms run with x fastest across lanes, conflict-free at any pitch
+  constexpr int RS = N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s = tw + N;
@@ -107,11 +108,276 @@ k_fft_z(typename CT<R>::type* __restrict__ data, const typename CT<R>::type* __r
   slab_store<N, NT, RS>(data + base, s, (size_t)N * N);
 }
 
+// ---------------------------------------------------------------- two-factor passes (N = R1 R2)
+//
+// Row pitch of the xy plane: congruent to 8 modulo 16 elements, so that the in-row exchange
+// (8 lanes per row, rotated columns) and the column accesses are both free of bank conflicts.
+template <int N> struct TFPitch { static constexpr int value = (N % 16 == 8) ? N : (N % 16 == 0 ? N + 8 : N + 1); };
+
+// xy transform of one z-plane with one shared-memory exchange per axis: the x transform's A side
+// reads global memory directly, the y transform's B side writes it directly (forward); the
+// inverse runs the steps in the opposite order.  Column of the in-row exchange: K0 R1 + (n0 +
+// K0) mod R1 (a rotation, so that the 8 lanes of a row hit distinct banks on both sides).
+template <typename R, int N, bool INV>
+__global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::value)
+k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const typename CT<R>::type* __restrict__ twg) {
+  using C = typename CT<R>::type;
+  using T = TF<C, N, INV>;
+  constexpr int NT = FFTThreads<N>::value;
+  constexpr int R1 = TwoFactor<N>::R1, R2 = TwoFactor<N>::R2;
+  constexpr int RS = TFPitch<N>::value;
+  constexpr int IA = N * R1, IB = N * R2;                 // A / B items of one axis
+  constexpr int PA = (IA + NT - 1) / NT, PB = (IB + NT - 1) / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + N;
+  const size_t base = ((size_t)blockIdx.y * N + blockIdx.x) * (size_t)(N * N);
+  const C* g = src + base;
+  C* o = dst + base;
+  for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+  __syncthreads();
+  C v[PA][R2];
+  C u[PB][R1];
+  if (!INV) {
+    // x, A side: item (y, n0), n0 fastest
+#pragma unroll
+    for (int p = 0; p < PA; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IA % NT == 0 || i < IA) {
+        const int y = i / R1, n0 = i - y * R1;
+#pragma unroll
+        for (int q = 0; q < R2; ++q) v[p][q] = g[y * N + n0 + R1 * q];
+        T::a_side(v[p], n0, tw);
+#pragma unroll
+        for (int k0 = 0; k0 < R2; ++k0) s[y * RS + k0 * R1 + (n0 + k0) % R1] = v[p][k0];
+      }
+    }
+    __syncthreads();
+    // x, B side: item (y, K0)
+#pragma unroll
+    for (int p = 0; p < PB; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IB % NT == 0 || i < IB) {
+        const int y = i / R2, k0 = i - y * R2;
+#pragma unroll
+        for (int n0 = 0; n0 < R1; ++n0) u[p][n0] = s[y * RS + k0 * R1 + (n0 + k0) % R1];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PB; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IB % NT == 0 || i < IB) {
+        const int y = i / R2, k0 = i - y * R2;
+        T::b_side(u[p], k0, tw);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) s[y * RS + k0 + R2 * k1] = u[p][k1];
+      }
+    }
+    __syncthreads();
+    // y, A side: item (x, n0), x fastest
+#pragma unroll
+    for (int p = 0; p < PA; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IA % NT == 0 || i < IA) {
+        const int n0 = i / N, x = i - n0 * N;
+#pragma unroll
+        for (int q = 0; q < R2; ++q) v[p][q] = s[(n0 + R1 * q) * RS + x];
+        T::a_side(v[p], n0, tw);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PA; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IA % NT == 0 || i < IA) {
+        const int n0 = i / N, x = i - n0 * N;
+#pragma unroll
+        for (int k0 = 0; k0 < R2; ++k0) s[(k0 * R1 + n0) * RS + x] = v[p][k0];
+      }
+    }
+    __syncthreads();
+    // y, B side: item (x, K0) -> global
+#pragma unroll
+    for (int p = 0; p < PB; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IB % NT == 0 || i < IB) {
+        const int k0 = i / N, x = i - k0 * N;
+#pragma unroll
+        for (int n0 = 0; n0 < R1; ++n0) u[p][n0] = s[(k0 * R1 + n0) * RS + x];
+        T::b_side(u[p], k0, tw);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) o[(k0 + R2 * k1) * N + x] = u[p][k1];
+      }
+    }
+  } else {
+    // y, B side from global: item (x, K0)
+#pragma unroll
+    for (int p = 0; p < PB; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IB % NT == 0 || i < IB) {
+        const int k0 = i / N, x = i - k0 * N;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) u[p][k1] = g[(k0 + R2 * k1) * N + x];
+        T::b_side(u[p], k0, tw);
+#pragma unroll
+        for (int n0 = 0; n0 < R1; ++n0) s[(k0 * R1 + n0) * RS + x] = u[p][n0];
+      }
+    }
+    __syncthreads();
+    // y, A side: item (x, n0)
+#pragma unroll
+    for (int p = 0; p < PA; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IA % NT == 0 || i < IA) {
+        const int n0 = i / N, x = i - n0 * N;
+#pragma unroll
+        for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[(k0 * R1 + n0) * RS + x];
+        T::a_side(v[p], n0, tw);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PA; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IA % NT == 0 || i < IA) {
+        const int n0 = i / N, x = i - n0 * N;
+#pragma unroll
+        for (int n1 = 0; n1 < R2; ++n1) s[(n0 + R1 * n1) * RS + x] = v[p][n1];
+      }
+    }
+    __syncthreads();
+    // x, B side: item (y, K0)
+#pragma unroll
+    for (int p = 0; p < PB; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IB % NT == 0 || i < IB) {
+        const int y = i / R2, k0 = i - y * R2;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) u[p][k1] = s[y * RS + k0 + R2 * k1];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PB; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IB % NT == 0 || i < IB) {
+        const int y = i / R2, k0 = i - y * R2;
+        T::b_side(u[p], k0, tw);
+#pragma unroll
+        for (int n0 = 0; n0 < R1; ++n0) s[y * RS + k0 * R1 + (n0 + k0) % R1] = u[p][n0];
+      }
+    }
+    __syncthreads();
+    // x, A side -> global: item (y, n0)
+#pragma unroll
+    for (int p = 0; p < PA; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (IA % NT == 0 || i < IA) {
+        const int y = i / R1, n0 = i - y * R1;
+#pragma unroll
+        for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[y * RS + k0 * R1 + (n0 + k0) % R1];
+        T::a_side(v[p], n0, tw);
+#pragma unroll
+        for (int n1 = 0; n1 < R2; ++n1) o[y * N + n0 + R1 * n1] = v[p][n1];
+      }
+    }
+  }
+}
+
+// z transform + kinetic multiply + inverse z transform of one y-slab, one exchange each way:
+// A side (x, n0) reads global memory along z, B side (x, K0) transforms, multiplies by
+// tx[x] + ty + tz[kz] and transforms back in registers, A side writes global memory.
+template <typename R, int N>
+__global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::value)
+k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type* __restrict__ twg, ZParams zp) {
+  using C = typename CT<R>::type;
+  using TFW = TF<C, N, false>;
+  using TIN = TF<C, N, true>;
+  constexpr int NT = FFTThreads<N>::value;
+  constexpr int R1 = TwoFactor<N>::R1, R2 = TwoFactor<N>::R2;
+  constexpr int IA = N * R1, IB = N * R2;
+  constexpr int PA = (IA + NT - 1) / NT, PB = (IB + NT - 1) / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s = tw + N;                                  // [K0 R1 + n0][x], dense
+  R* tx = reinterpret_cast<R*>(s + N * N);
+  R* tz = tx + N;
+  R* ty = tz + N;
+  const int y = blockIdx.x;
+  const int b = blockIdx.y;
+  C* g = data + (size_t)b * N * N * N + (size_t)y * N;
+  constexpr size_t ZS = (size_t)N * N;
+  for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
+  z_tables<R, N, Z_KIN>(tx, tz, ty, zp, y, b / zp.comps_per_k);
+  C v[PA][R2];
+#pragma unroll
+  for (int p = 0; p < PA; ++p) {
+    const int i = threadIdx.x + p * NT;
+    if (IA % NT == 0 || i < IA) {
+      const int n0 = i / N, x = i - n0 * N;
+#pragma unroll
+      for (int q = 0; q < R2; ++q) v[p][q] = g[(size_t)(n0 + R1 * q) * ZS + x];
+    }
+  }
+  __syncthreads();  // tables
+#pragma unroll
+  for (int p = 0; p < PA; ++p) {
+    const int i = threadIdx.x + p * NT;
+    if (IA % NT == 0 || i < IA) {
+      const int n0 = i / N, x = i - n0 * N;
+      TFW::a_side(v[p], n0, tw);
+#pragma unroll
+      for (int k0 = 0; k0 < R2; ++k0) s[(k0 * R1 + n0) * N + x] = v[p][k0];
+    }
+  }
+  __syncthreads();
+  const R tyv = *ty;
+#pragma unroll
+  for (int p = 0; p < PB; ++p) {
+    const int i = threadIdx.x + p * NT;
+    if (IB % NT == 0 || i < IB) {
+      const int k0 = i / N, x = i - k0 * N;
+      C u[R1];
+#pragma unroll
+      for (int n0 = 0; n0 < R1; ++n0) u[n0] = s[(k0 * R1 + n0) * N + x];
+      TFW::b_side(u, k0, tw);
+      const R txy = tx[x] + tyv;
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) u[k1] = cscale(u[k1], txy + tz[k0 + R2 * k1]);
+      TIN::b_side(u, k0, tw);
+#pragma unroll
+      for (int n0 = 0; n0 < R1; ++n0) s[(k0 * R1 + n0) * N + x] = u[n0];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < PA; ++p) {
+    const int i = threadIdx.x + p * NT;
+    if (IA % NT == 0 || i < IA) {
+      const int n0 = i / N, x = i - n0 * N;
+#pragma unroll
+      for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[(k0 * R1 + n0) * N + x];
+      TIN::a_side(v[p], n0, tw);
+#pragma unroll
+      for (int n1 = 0; n1 < R2; ++n1) g[(size_t)(n0 + R1 * n1) * ZS + x] = v[p][n1];
+    }
+  }
+}
+
 template <typename R, int N>
 static cudaError_t fft_xy_n(cudaStream_t st, const void* src, void* data, int nbatch, const void* tw, bool inv) {
   using C = typename CT<R>::type;
-  const size_t smem = (size_t)(N + N * (N + 1)) * sizeof(C);
   dim3 grid(N, nbatch);
+  if constexpr (TwoFactor<N>::ok) {
+    const size_t smem2 = (size_t)(N + N * TFPitch<N>::value) * sizeof(C);
+    auto kf = inv ? k_fft_xy2<R, N, true> : k_fft_xy2<R, N, false>;
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    kf<<<grid, FFTThreads<N>::value, smem2, st>>>((const C*)src, (C*)data, (const C*)tw);
+    return cudaGetLastError();
+  }
+  const size_t smem = (size_t)(N + N * (N + 1)) * sizeof(C);
   if (inv) {
     auto kf = k_fft_xy<R, N, true>;
     cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -129,7 +395,14 @@ static cudaError_t fft_xy_n(cudaStream_t st, const void* src, void* data, int nb
 template <typename R, int N, int MODE>
 static cudaError_t fft_z_nm(cudaStream_t st, void* data, int nbatch, const void* tw, const ZParams& zp) {
   using C = typename CT<R>::type;
-  const size_t smem = (size_t)(N + N * (N + 1)) * sizeof(C) + (2 * N + 2) * sizeof(R);
+  const size_t smem = (size_t)(N + N * N) * sizeof(C) + (2 * N + 2) * sizeof(R);
+  if constexpr (MODE == Z_KIN && TwoFactor<N>::ok) {
+    auto kf = k_fft_z2_kin<R, N>;
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    kf<<<dim3(N, nbatch), FFTThreads<N>::value, smem, st>>>((C*)data, (const C*)tw, zp);
+    return cudaGetLastError();
+  }
   auto kf = k_fft_z<R, N, MODE>;
   cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
@@ -180,7 +453,8 @@ k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTable
   const int e0 = pt.g_ptr[a], e1 = pt.g_ptr[a + 1];
   for (int e = e0 + threadIdx.x; e < e1; e += 256) {
     const int r = pt.g_idx[e];
-    const R* t = pt.g_tab + (size_t)e * TAB;
+    R t[TAB];
+    load_row<R, TAB>(pt.g_tab + (size_t)e * TAB, t);
     R sn, cs;
     sincos_r<R>(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);
     const C u = up[r], d = dn[r];
@@ -276,10 +550,20 @@ cudaError_t launch_proj_gather_mom(cudaStream_t st, int N, const void* psi, int 
 
 // ============================================================================ epilogue
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Two neighbouring grid points of one spinor per thread (16-byte accesses); the spinor's D c
 // for every atom is staged in shared memory when it is small.
-template <typename R, int NLM>
-__global__ void __launch_bounds__(256)
+// AK selects the accumulator code compiled in: 0 = Chebyshev term without accumulator update,
+// 1 = Chebyshev term updating accumulator 1 only, 2 = every mode with run-time flags.  The
+// Chebyshev recurrence touches its accumulators on every third term only, so most launches take
+// the AK = 0 form, which carries the least code.  FP32 forms are held to 64 registers (four
+// CTAs per SM; the few bytes of spill in the AK = 1, 2 forms cost less than the lost occupancy).
+template <typename R, int AK> struct EpiMinBlocks { static constexpr int value = 1; };
+template <int AK> struct EpiMinBlocks<float, AK> { static constexpr int value = 4; };
+
+template <typename R, int NLM, int AK>
+__global__ void __launch_bounds__(256, EpiMinBlocks<R, AK>::value)
 k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::type* Tk,
            const typename CT<R>::type* Tkm1, typename CT<R>::type* Tout, typename CT<R>::type* acc1,
            typename CT<R>::type* acc2, const R* __restrict__ V, size_t N3, ProjTables<R> pt,
@@ -301,6 +585,19 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
   const size_t ou = (size_t)(2 * kb) * N3 + r, od = ou + N3;
   const Pair<C> pu2 = ld2(Tk + ou), pd2 = ld2(Tk + od);
   const Pair<C> ku2 = ld2(kin + ou), kd2 = ld2(kin + od);
+  // Chebyshev terms: every input is requested before any arithmetic (more loads in flight)
+  const bool cheb = AK < 2 || ep.mode == EPI_RECUR || ep.mode == EPI_FIRST;
+  const bool rec = ep.mode == EPI_RECUR;
+  const bool use1 = AK >= 1 && ep.use_acc1, use2 = AK >= 2 && ep.use_acc2;
+  const C zc = cmake<C>((R)0, (R)0);
+  Pair<C> qu0 = {zc, zc}, qd0 = {zc, zc}, au1 = {zc, zc}, ad1 = {zc, zc}, au2 = {zc, zc}, ad2 = {zc, zc};
+  // T_{k-1} and the accumulators are not needed until after the projector scatter: their
+  // lines are requested from HBM into L2 now and read into registers after the scatter, so they
+  // hold no registers across its loop.
+  const bool ld_acc1 = cheb && use1 && !ep.init1, ld_acc2 = cheb && use2 && !ep.init2;
+  if (rec) { prefetch_l2(Tkm1 + ou); prefetch_l2(Tkm1 + od); }
+  if (ld_acc1) { prefetch_l2(acc1 + ou); prefetch_l2(acc1 + od); }
+  if (ld_acc2) { prefetch_l2(acc2 + ou); prefetch_l2(acc2 + od); }
   const C pu[2] = {pu2.a, pu2.b}, pd[2] = {pd2.a, pd2.b};
   C hu[2] = {ku2.a, ku2.b}, hd[2] = {kd2.a, kd2.b};
   {
@@ -310,13 +607,16 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
     h_point<R, NLM>(hu[0], hd[0], pu[0], pd[0], v0.x, v1.x, (R)0.5 * v2.x, (R)0.5 * v3.x, r, pt, dcb, sx, sy, sz);
     h_point<R, NLM>(hu[1], hd[1], pu[1], pd[1], v0.y, v1.y, (R)0.5 * v2.y, (R)0.5 * v3.y, r + 1, pt, dcb, sx, sy, sz);
   }
+  if (rec) { qu0 = ld2(Tkm1 + ou); qd0 = ld2(Tkm1 + od); }
+  if (ld_acc1) { au1 = ld2(acc1 + ou); ad1 = ld2(acc1 + od); }
+  if (ld_acc2) { au2 = ld2(acc2 + ou); ad2 = ld2(acc2 + od); }
   auto cmulr = [](C a, R cr, R ci) { return cmake<C>(cr * a.x - ci * a.y, cr * a.y + ci * a.x); };
-  if (ep.mode == EPI_APPLY) {
+  if (AK == 2 && ep.mode == EPI_APPLY) {
     st2(Tout + ou, hu[0], hu[1]);
     st2(Tout + od, hd[0], hd[1]);
     return;
   }
-  if (ep.mode == EPI_TAYLOR) {
+  if (AK == 2 && ep.mode == EPI_TAYLOR) {
     const R cr = (R)ep.a1[0], ci = (R)ep.a1[1];
     C tu[2], td[2];
     for (int j = 0; j < 2; ++j) { tu[j] = cmulr(hu[j], cr, ci); td[j] = cmulr(hd[j], cr, ci); }
@@ -328,7 +628,7 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
     return;
   }
   const R cc = (R)ep.c, id = (R)ep.inv_delta;
-  if (ep.mode == EPI_ADJ || ep.mode == EPI_ADJ0) {
+  if (AK == 2 && (ep.mode == EPI_ADJ || ep.mode == EPI_ADJ0)) {
     // Clenshaw-type adjoint recurrence: S_k = f (H - c)/Delta S_{k+1} - S_{k+2} + seeds,
     // f = 2 (k >= 1) or 1 (k = 0); Tk holds S_{k+1}, Tkm1 holds S_{k+2} (may be null),
     // acc1/acc2 hold the seed cotangents with coefficients a1, b1.
@@ -367,8 +667,7 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
       td[j] = cmake<C>((hd[j].x - cc * pd[j].x) * id, (hd[j].y - cc * pd[j].y) * id);
     }
   } else {
-    const Pair<C> qu = ld2(Tkm1 + ou), qd = ld2(Tkm1 + od);
-    const C qus[2] = {qu.a, qu.b}, qds[2] = {qd.a, qd.b};
+    const C qus[2] = {qu0.a, qu0.b}, qds[2] = {qd0.a, qd0.b};
     for (int j = 0; j < 2; ++j) {
       tu[j] = cmake<C>((R)2 * (hu[j].x - cc * pu[j].x) * id - qus[j].x, (R)2 * (hu[j].y - cc * pu[j].y) * id - qus[j].y);
       td[j] = cmake<C>((R)2 * (hd[j].x - cc * pd[j].x) * id - qds[j].x, (R)2 * (hd[j].y - cc * pd[j].y) * id - qds[j].y);
@@ -376,26 +675,37 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
   }
   st2(Tout + ou, tu[0], tu[1]);
   st2(Tout + od, td[0], td[1]);
-  auto upd = [&](C* acc, R c0r, R c0i, R c1r, R c1i) {
+  // Accumulators take up to three terms at once (T_{k-1}, T_k, T_{k+1}, all in registers here),
+  // so the host updates each of them on every third term only.
+  auto upd = [&](C* acc, int init, const Pair<C>& au, const Pair<C>& ad, const double* cm, const double* c0,
+                 const double* c1) {
+    const R cmr = (R)cm[0], cmi = (R)cm[1], c0r = (R)c0[0], c0i = (R)c0[1], c1r = (R)c1[0], c1i = (R)c1[1];
+    const C qus[2] = {qu0.a, qu0.b}, qds[2] = {qd0.a, qd0.b};
     C nu[2], nd[2];
     for (int j = 0; j < 2; ++j) {
-      nu[j] = cmulr(tu[j], c1r, c1i);
-      nd[j] = cmulr(td[j], c1r, c1i);
-      if (first) {
-        nu[j] = cadd(nu[j], cmulr(pu[j], c0r, c0i));
-        nd[j] = cadd(nd[j], cmulr(pd[j], c0r, c0i));
+      nu[j] = cadd(cmulr(tu[j], c1r, c1i), cmulr(pu[j], c0r, c0i));
+      nd[j] = cadd(cmulr(td[j], c1r, c1i), cmulr(pd[j], c0r, c0i));
+      if (rec) {
+        nu[j] = cadd(nu[j], cmulr(qus[j], cmr, cmi));
+        nd[j] = cadd(nd[j], cmulr(qds[j], cmr, cmi));
       }
     }
-    if (!first) {
-      const Pair<C> au = ld2(acc + ou), ad = ld2(acc + od);
+    if (!init) {
       nu[0] = cadd(nu[0], au.a); nu[1] = cadd(nu[1], au.b);
       nd[0] = cadd(nd[0], ad.a); nd[1] = cadd(nd[1], ad.b);
     }
     st2(acc + ou, nu[0], nu[1]);
     st2(acc + od, nd[0], nd[1]);
   };
-  if (ep.use_acc1) upd(acc1, (R)ep.a0[0], (R)ep.a0[1], (R)ep.a1[0], (R)ep.a1[1]);
-  if (ep.use_acc2) upd(acc2, (R)ep.b0[0], (R)ep.b0[1], (R)ep.b1[0], (R)ep.b1[1]);
+  if (use1) upd(acc1, ep.init1, au1, ad1, ep.am, ep.a0, ep.a1);
+  if (use2) upd(acc2, ep.init2, au2, ad2, ep.bm, ep.b0, ep.b1);
+}
+
+template <typename R, int NLM, typename... A>
+static void epi_ak(int ak, dim3 grid, size_t smem, cudaStream_t st, A... args) {
+  if (ak == 0) k_epilogue<R, NLM, 0><<<grid, 256, smem, st>>>(args...);
+  else if (ak == 1) k_epilogue<R, NLM, 1><<<grid, 256, smem, st>>>(args...);
+  else k_epilogue<R, NLM, 2><<<grid, 256, smem, st>>>(args...);
 }
 
 template <typename R>
@@ -410,12 +720,14 @@ cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void*
   const size_t dcb = (size_t)pt.natoms * 2 * nlm * sizeof(C);
   epx.dc_staged = (nlm > 0 && dcb <= 16 * 1024) ? 1 : 0;
   const size_t smem = epx.dc_staged ? dcb : 0;
+  const bool cheb = ep.mode == EPI_FIRST || ep.mode == EPI_RECUR;
+  const int ak = !cheb ? 2 : (ep.use_acc2 ? 2 : (ep.use_acc1 ? 1 : 0));
 #define EPI_ARGS (const C*)kin, (const C*)Tk, (const C*)Tkm1, (C*)Tout, (C*)acc1, (C*)acc2, V, N3, pt, (const C*)dc, epx
   switch (nlm) {
-    case 0: k_epilogue<R, 0><<<grid, 256, smem, st>>>(EPI_ARGS); break;
-    case 1: k_epilogue<R, 1><<<grid, 256, smem, st>>>(EPI_ARGS); break;
-    case 4: k_epilogue<R, 4><<<grid, 256, smem, st>>>(EPI_ARGS); break;
-    case 9: k_epilogue<R, 9><<<grid, 256, smem, st>>>(EPI_ARGS); break;
+    case 0: epi_ak<R, 0>(ak, grid, smem, st, EPI_ARGS); break;
+    case 1: epi_ak<R, 1>(ak, grid, smem, st, EPI_ARGS); break;
+    case 4: epi_ak<R, 4>(ak, grid, smem, st, EPI_ARGS); break;
+    case 9: epi_ak<R, 9>(ak, grid, smem, st, EPI_ARGS); break;
     default: return cudaErrorInvalidValue;
   }
 #undef EPI_ARGS
@@ -436,20 +748,31 @@ k_density(const typename CT<R>::type* __restrict__ psi, size_t N3, int nkb, int 
   const int g = blockIdx.y;
   const int kb0 = (int)(((long long)nkb * g) / ngroups), kb1 = (int)(((long long)nkb * (g + 1)) / ngroups);
   double s[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  // FP32 spinors: bilinears of up to 8 bands are summed in FP32 (the inputs' own precision) and
+  // each such partial sum is added to the FP64 accumulators; FP64 spinors: FP64 throughout
+  constexpr int CH = sizeof(R) == 4 ? 8 : 1;
+  for (int kc = kb0; kc < kb1; kc += CH) {
+    R p[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    const int kend = min(kb1, kc + CH);
 #pragma unroll 4
-  for (int kb = kb0; kb < kb1; ++kb) {
-    const Pair<typename CT<R>::type> u = ld2(psi + (size_t)(2 * kb) * N3 + r);
-    const Pair<typename CT<R>::type> d = ld2(psi + (size_t)(2 * kb + 1) * N3 + r);
-    const double w = wf[kb];
-    const double ux[2] = {(double)u.a.x, (double)u.b.x}, uy[2] = {(double)u.a.y, (double)u.b.y};
-    const double dx[2] = {(double)d.a.x, (double)d.b.x}, dy[2] = {(double)d.a.y, (double)d.b.y};
+    for (int kb = kc; kb < kend; ++kb) {
+      const Pair<typename CT<R>::type> u = ld2(psi + (size_t)(2 * kb) * N3 + r);
+      const Pair<typename CT<R>::type> d = ld2(psi + (size_t)(2 * kb + 1) * N3 + r);
+      const R w = (R)wf[kb];
+      const R ux[2] = {u.a.x, u.b.x}, uy[2] = {u.a.y, u.b.y};
+      const R dx[2] = {d.a.x, d.b.x}, dy[2] = {d.a.y, d.b.y};
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      s[j][0] += w * (ux[j] * ux[j] + uy[j] * uy[j]);
-      s[j][1] += w * (dx[j] * dx[j] + dy[j] * dy[j]);
-      s[j][2] += w * (ux[j] * dx[j] + uy[j] * dy[j]);  // Re(u conj d)
-      s[j][3] += w * (uy[j] * dx[j] - ux[j] * dy[j]);  // Im(u conj d)
+      for (int j = 0; j < 2; ++j) {
+        p[j][0] += w * (ux[j] * ux[j] + uy[j] * uy[j]);
+        p[j][1] += w * (dx[j] * dx[j] + dy[j] * dy[j]);
+        p[j][2] += w * (ux[j] * dx[j] + uy[j] * dy[j]);  // Re(u conj d)
+        p[j][3] += w * (uy[j] * dx[j] - ux[j] * dy[j]);  // Im(u conj d)
+      }
     }
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s[j][c] += (double)p[j][c];
   }
   double* o = out + (size_t)g * 4 * N3;
 #pragma unroll

@@ -142,7 +142,7 @@ def test_differentiation_workload_envelope_gradient(lib):
         h.step(nst)
         return h.observables(fields=False)[2]["M"][2]
 
-    assert float(L) == pytest.approx(loss(a0), rel=1e-12)
+    assert float(L.detach()) == pytest.approx(loss(a0), rel=1e-12)
     hstep = 1e-4
     for j in rng.choice(64, size=4, replace=False):
         ap, am = a0.copy(), a0.copy()

@@ -257,3 +257,45 @@ def test_tensor_core_projectors_step_parity(lib):
     rows, psi_g, o = run_pair(lib, wl, psi0, 2, (-20.0, 100.0), precision=1, proj_mode=3)
     for r in rows:
         assert r["n"] <= 2e-5 and r["m"] <= 2e-5, r
+
+
+def test_atom_moments_match_oracle_on_symmetric_cluster(lib):
+    """Voronoi per-atom moments on the icosahedral cluster at 24^3 (many grid points are
+    equidistant from several atoms: ties must resolve identically) against the oracle."""
+    from paper_2506_21908_gb300 import _lib
+    wl = S.cluster(n=24, nsteps=2, laser=False)
+    psi0 = S.cluster_states(wl)
+    h = _lib.TDDFT.from_workload(wl)
+    h.set_states(psi0)
+    M, N = h.atom_moments()
+    _, _, E, _ = h.observables(fields=False)
+    h.close()
+    s = System.from_workload(wl)
+    Mo, No = s.atom_moments(s.rho_v(psi0))
+    assert np.abs(M - Mo).max() <= 1e-10 * np.abs(Mo).max()
+    assert np.abs(N - No).max() <= 1e-10 * np.abs(No).max()
+    assert np.allclose(M.sum(axis=0), E["M"], atol=1e-10)
+
+
+@pytest.mark.parametrize("n", [32, 48, 64])
+def test_cluster_kinetic_fp32_apply_h(lib, n, monkeypatch):
+    """FP32-mixed Hamiltonian with the one-kernel kinetic term (16-CTA clusters holding a whole
+    component in distributed shared memory) against the oracle, and against the three-pass
+    kinetic term of the same library."""
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=n, nstates=2, nk=2, natoms=2)
+    psi0 = S.small_parity_states(wl)
+    outs = []
+    for cluster in ("1", "0"):
+        monkeypatch.setenv("TDDFT_CLUSTER", cluster)
+        h = _lib.TDDFT.from_workload(wl, precision=1, e_min=-20, e_max=400)
+        h.set_fields(wl.times, wl.A, wl.B)
+        h.set_states(psi0, 0.1)
+        outs.append(h.apply_hamiltonian(psi0))
+        h.close()
+    s = System.from_workload(wl)
+    o = Oracle(s, FieldTable(wl.times, wl.A, wl.B), wl.dt, psi0, t0=0.1, bounds=(-20, 400))
+    A, _ = o.f.at(0.1)
+    ref = s.apply_h(psi0, o.V, A)
+    assert rel(outs[0], ref) <= 2e-5
+    assert rel(outs[0], outs[1]) <= 2e-6
