@@ -137,15 +137,26 @@ def time_oracle(nbands, steps, warm=0):
 
 
 # --------------------------------------------------------------------------- ours
-def kernel_source_hash():
-    """SHA-256 over the CUDA sources, to tie a stored ncu traffic figure to the kernels it measured."""
+# CUDA sources that define each kernel class (its kernels, the device helpers they inline and
+# the parameter structs they take).
+KERNEL_SOURCES = {
+    "epilogue": ("epilogue.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+    "fft_xy": ("kernels.cu", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+    "fft_z_kinetic": ("kernels.cu", "kin_cluster.cu", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+    "proj_gather": ("kernels.cu", "proj_tc.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+}
+
+
+def kernel_source_hash(kernel_class):
+    """SHA-256 over the CUDA sources of one kernel class (all of them for a class not listed),
+    to tie a stored ncu traffic figure to the kernels it measured."""
     import hashlib
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2506_21908_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(f.encode())
-            h.update(open(os.path.join(src, f), "rb").read())
+    files = KERNEL_SOURCES.get(kernel_class) or [f for f in os.listdir(src) if f.endswith((".cu", ".cuh"))]
+    for f in sorted(files):
+        h.update(f.encode())
+        h.update(open(os.path.join(src, f), "rb").read())
     return h.hexdigest()
 
 
@@ -162,7 +173,7 @@ def measured_traffic(kernel_class, units_per_launch):
         if ":" in line and not line.startswith((" ", "#")):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("source_sha256") != kernel_source_hash():
+    if kv.get("source_sha256") != kernel_source_hash(kernel_class):
         return None, "kernels changed since the ncu capture (%s)" % os.path.basename(path)
     return float(kv["dram_bytes_per_unit"]) * units_per_launch, os.path.basename(path)
 

@@ -1,0 +1,210 @@
+// The pointwise epilogue of one Chebyshev (or Taylor) term, for every spinor and grid point:
+// kinetic part (from the FFT passes) + 2x2 spin-matrix local potential (Eq. potential4,
+// Eq. zeeman_potential) + separable projector scatter with the L.S blocks (Eq. Vps, Eq.
+// Vps-soc), then T_{k+1} = 2 (H - c)/Delta T_k - T_{k-1} and the accumulator updates; also the
+// plain H apply, the Taylor update and the adjoint (Clenshaw-type) recurrence.
+#include <cstdint>
+
+#include "fft.cuh"
+#include "impl.cuh"
+#include "kcommon.cuh"
+#include "kepi.cuh"
+
+namespace tddft {
+
+// ============================================================================ epilogue
+
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Two neighbouring grid points of one spinor per thread (16-byte accesses); the spinor's D c
+// for every atom is staged in shared memory when it is small.
+// AK selects the accumulator code compiled in: 0 = Chebyshev term without accumulator update,
+// 1 = Chebyshev term updating accumulator 1 only, 2 = every mode with run-time flags.  The
+// Chebyshev recurrence touches its accumulators on every third term only, so most launches take
+// the AK = 0 form, which carries the least code.  FP32 forms are held to 64 registers (four
+// CTAs per SM; the few bytes of spill in the AK = 1, 2 forms cost less than the lost occupancy).
+template <typename R, int AK> struct EpiMinBlocks { static constexpr int value = 1; };
+template <int AK> struct EpiMinBlocks<float, AK> { static constexpr int value = 4; };
+
+template <typename R, int NLM, int AK>
+__global__ void __launch_bounds__(256, EpiMinBlocks<R, AK>::value)
+k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::type* Tk,
+           const typename CT<R>::type* Tkm1, typename CT<R>::type* Tout, typename CT<R>::type* acc1,
+           typename CT<R>::type* acc2, const R* __restrict__ V, size_t N3, ProjTables<R> pt,
+           const typename CT<R>::type* __restrict__ dc, EpiParams ep) {
+  using C = typename CT<R>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* dcs = reinterpret_cast<C*>(smem_raw);
+  const int kb = blockIdx.y;
+  const int k = kb / ep.nstates;
+  const int ncoef = pt.natoms * 2 * NLM;
+  const C* dcg = dc + (size_t)kb * ncoef;
+  if (NLM > 0 && ep.dc_staged) {
+    for (int i = threadIdx.x; i < ncoef; i += blockDim.x) dcs[i] = dcg[i];
+    __syncthreads();
+  }
+  const C* dcb = (NLM > 0 && ep.dc_staged) ? dcs : dcg;
+  const size_t r = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (r >= N3) return;
+  const size_t ou = (size_t)(2 * kb) * N3 + r, od = ou + N3;
+  const Pair<C> pu2 = ld2(Tk + ou), pd2 = ld2(Tk + od);
+  const Pair<C> ku2 = ld2(kin + ou), kd2 = ld2(kin + od);
+  // Chebyshev terms: every input is requested before any arithmetic (more loads in flight)
+  const bool cheb = AK < 2 || ep.mode == EPI_RECUR || ep.mode == EPI_FIRST;
+  const bool rec = ep.mode == EPI_RECUR;
+  const bool use1 = AK >= 1 && ep.use_acc1, use2 = AK >= 2 && ep.use_acc2;
+  const C zc = cmake<C>((R)0, (R)0);
+  Pair<C> qu0 = {zc, zc}, qd0 = {zc, zc}, au1 = {zc, zc}, ad1 = {zc, zc}, au2 = {zc, zc}, ad2 = {zc, zc};
+  // T_{k-1} and the accumulators are not needed until after the projector scatter: their
+  // lines are requested from HBM into L2 now and read into registers after the scatter, so they
+  // hold no registers across its loop.
+  const bool ld_acc1 = cheb && use1 && !ep.init1, ld_acc2 = cheb && use2 && !ep.init2;
+  if (rec) { prefetch_l2(Tkm1 + ou); prefetch_l2(Tkm1 + od); }
+  if (ld_acc1) { prefetch_l2(acc1 + ou); prefetch_l2(acc1 + od); }
+  if (ld_acc2) { prefetch_l2(acc2 + ou); prefetch_l2(acc2 + od); }
+  const C pu[2] = {pu2.a, pu2.b}, pd[2] = {pd2.a, pd2.b};
+  C hu[2] = {ku2.a, ku2.b}, hd[2] = {kd2.a, kd2.b};
+  {
+    const C v0 = *reinterpret_cast<const C*>(V + r), v1 = *reinterpret_cast<const C*>(V + N3 + r);
+    const C v2 = *reinterpret_cast<const C*>(V + 2 * N3 + r), v3 = *reinterpret_cast<const C*>(V + 3 * N3 + r);
+    const R sx = (R)ep.shift[k][0], sy = (R)ep.shift[k][1], sz = (R)ep.shift[k][2];
+    h_point<R, NLM>(hu[0], hd[0], pu[0], pd[0], v0.x, v1.x, (R)0.5 * v2.x, (R)0.5 * v3.x, r, pt, dcb, sx, sy, sz);
+    h_point<R, NLM>(hu[1], hd[1], pu[1], pd[1], v0.y, v1.y, (R)0.5 * v2.y, (R)0.5 * v3.y, r + 1, pt, dcb, sx, sy, sz);
+  }
+  if (rec) { qu0 = ld2(Tkm1 + ou); qd0 = ld2(Tkm1 + od); }
+  if (ld_acc1) { au1 = ld2(acc1 + ou); ad1 = ld2(acc1 + od); }
+  if (ld_acc2) { au2 = ld2(acc2 + ou); ad2 = ld2(acc2 + od); }
+  auto cmulr = [](C a, R cr, R ci) { return cmake<C>(cr * a.x - ci * a.y, cr * a.y + ci * a.x); };
+  if (AK == 2 && ep.mode == EPI_APPLY) {
+    st2(Tout + ou, hu[0], hu[1]);
+    st2(Tout + od, hd[0], hd[1]);
+    return;
+  }
+  if (AK == 2 && ep.mode == EPI_TAYLOR) {
+    const R cr = (R)ep.a1[0], ci = (R)ep.a1[1];
+    C tu[2], td[2];
+    for (int j = 0; j < 2; ++j) { tu[j] = cmulr(hu[j], cr, ci); td[j] = cmulr(hd[j], cr, ci); }
+    st2(Tout + ou, tu[0], tu[1]);
+    st2(Tout + od, td[0], td[1]);
+    const Pair<C> au = ld2(acc1 + ou), ad = ld2(acc1 + od);
+    st2(acc1 + ou, cadd(au.a, tu[0]), cadd(au.b, tu[1]));
+    st2(acc1 + od, cadd(ad.a, td[0]), cadd(ad.b, td[1]));
+    return;
+  }
+  const R cc = (R)ep.c, id = (R)ep.inv_delta;
+  if (AK == 2 && (ep.mode == EPI_ADJ || ep.mode == EPI_ADJ0)) {
+    // Clenshaw-type adjoint recurrence: S_k = f (H - c)/Delta S_{k+1} - S_{k+2} + seeds,
+    // f = 2 (k >= 1) or 1 (k = 0); Tk holds S_{k+1}, Tkm1 holds S_{k+2} (may be null),
+    // acc1/acc2 hold the seed cotangents with coefficients a1, b1.
+    const R fct = (ep.mode == EPI_ADJ) ? (R)2 : (R)1;
+    C su[2], sd[2];
+    for (int j = 0; j < 2; ++j) {
+      su[j] = cmake<C>(fct * (hu[j].x - cc * pu[j].x) * id, fct * (hu[j].y - cc * pu[j].y) * id);
+      sd[j] = cmake<C>(fct * (hd[j].x - cc * pd[j].x) * id, fct * (hd[j].y - cc * pd[j].y) * id);
+    }
+    if (Tkm1) {
+      const Pair<C> qu = ld2(Tkm1 + ou), qd = ld2(Tkm1 + od);
+      su[0] = csub(su[0], qu.a); su[1] = csub(su[1], qu.b);
+      sd[0] = csub(sd[0], qd.a); sd[1] = csub(sd[1], qd.b);
+    }
+    if (ep.use_acc1) {
+      const Pair<C> yu = ld2(acc1 + ou), yd = ld2(acc1 + od);
+      const R ar = (R)ep.a1[0], ai = (R)ep.a1[1];
+      su[0] = cadd(su[0], cmulr(yu.a, ar, ai)); su[1] = cadd(su[1], cmulr(yu.b, ar, ai));
+      sd[0] = cadd(sd[0], cmulr(yd.a, ar, ai)); sd[1] = cadd(sd[1], cmulr(yd.b, ar, ai));
+    }
+    if (ep.use_acc2) {
+      const Pair<C> yu = ld2(acc2 + ou), yd = ld2(acc2 + od);
+      const R br = (R)ep.b1[0], bi = (R)ep.b1[1];
+      su[0] = cadd(su[0], cmulr(yu.a, br, bi)); su[1] = cadd(su[1], cmulr(yu.b, br, bi));
+      sd[0] = cadd(sd[0], cmulr(yd.a, br, bi)); sd[1] = cadd(sd[1], cmulr(yd.b, br, bi));
+    }
+    st2(Tout + ou, su[0], su[1]);
+    st2(Tout + od, sd[0], sd[1]);
+    return;
+  }
+  const bool first = ep.mode == EPI_FIRST;
+  C tu[2], td[2];
+  if (first) {
+    for (int j = 0; j < 2; ++j) {
+      tu[j] = cmake<C>((hu[j].x - cc * pu[j].x) * id, (hu[j].y - cc * pu[j].y) * id);
+      td[j] = cmake<C>((hd[j].x - cc * pd[j].x) * id, (hd[j].y - cc * pd[j].y) * id);
+    }
+  } else {
+    const C qus[2] = {qu0.a, qu0.b}, qds[2] = {qd0.a, qd0.b};
+    for (int j = 0; j < 2; ++j) {
+      tu[j] = cmake<C>((R)2 * (hu[j].x - cc * pu[j].x) * id - qus[j].x, (R)2 * (hu[j].y - cc * pu[j].y) * id - qus[j].y);
+      td[j] = cmake<C>((R)2 * (hd[j].x - cc * pd[j].x) * id - qds[j].x, (R)2 * (hd[j].y - cc * pd[j].y) * id - qds[j].y);
+    }
+  }
+  st2(Tout + ou, tu[0], tu[1]);
+  st2(Tout + od, td[0], td[1]);
+  // Accumulators take up to three terms at once (T_{k-1}, T_k, T_{k+1}, all in registers here),
+  // so the host updates each of them on every third term only.
+  auto upd = [&](C* acc, int init, const Pair<C>& au, const Pair<C>& ad, const double* cm, const double* c0,
+                 const double* c1) {
+    const R cmr = (R)cm[0], cmi = (R)cm[1], c0r = (R)c0[0], c0i = (R)c0[1], c1r = (R)c1[0], c1i = (R)c1[1];
+    const C qus[2] = {qu0.a, qu0.b}, qds[2] = {qd0.a, qd0.b};
+    C nu[2], nd[2];
+    for (int j = 0; j < 2; ++j) {
+      nu[j] = cadd(cmulr(tu[j], c1r, c1i), cmulr(pu[j], c0r, c0i));
+      nd[j] = cadd(cmulr(td[j], c1r, c1i), cmulr(pd[j], c0r, c0i));
+      if (rec) {
+        nu[j] = cadd(nu[j], cmulr(qus[j], cmr, cmi));
+        nd[j] = cadd(nd[j], cmulr(qds[j], cmr, cmi));
+      }
+    }
+    if (!init) {
+      nu[0] = cadd(nu[0], au.a); nu[1] = cadd(nu[1], au.b);
+      nd[0] = cadd(nd[0], ad.a); nd[1] = cadd(nd[1], ad.b);
+    }
+    st2(acc + ou, nu[0], nu[1]);
+    st2(acc + od, nd[0], nd[1]);
+  };
+  if (use1) upd(acc1, ep.init1, au1, ad1, ep.am, ep.a0, ep.a1);
+  if (use2) upd(acc2, ep.init2, au2, ad2, ep.bm, ep.b0, ep.b1);
+}
+
+template <typename R, int NLM, typename... A>
+static void epi_ak(int ak, dim3 grid, size_t smem, cudaStream_t st, A... args) {
+  if (ak == 0) k_epilogue<R, NLM, 0><<<grid, 256, smem, st>>>(args...);
+  else if (ak == 1) k_epilogue<R, NLM, 1><<<grid, 256, smem, st>>>(args...);
+  else k_epilogue<R, NLM, 2><<<grid, 256, smem, st>>>(args...);
+}
+
+template <typename R>
+cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* Tk, const void* Tkm1, void* Tout,
+                            void* acc1, void* acc2, const R* V, const ProjTables<R>& pt, const void* dc, int nkb,
+                            const EpiParams& ep) {
+  using C = typename CT<R>::type;
+  const size_t N3 = (size_t)N * N * N;
+  dim3 grid((unsigned)((N3 / 2 + 255) / 256), nkb);
+  const int nlm = pt.natoms > 0 ? pt.nlm : 0;
+  EpiParams epx = ep;
+  const size_t dcb = (size_t)pt.natoms * 2 * nlm * sizeof(C);
+  epx.dc_staged = (nlm > 0 && dcb <= 16 * 1024) ? 1 : 0;
+  const size_t smem = epx.dc_staged ? dcb : 0;
+  const bool cheb = ep.mode == EPI_FIRST || ep.mode == EPI_RECUR;
+  const int ak = !cheb ? 2 : (ep.use_acc2 ? 2 : (ep.use_acc1 ? 1 : 0));
+#define EPI_ARGS (const C*)kin, (const C*)Tk, (const C*)Tkm1, (C*)Tout, (C*)acc1, (C*)acc2, V, N3, pt, (const C*)dc, epx
+  switch (nlm) {
+    case 0: epi_ak<R, 0>(ak, grid, smem, st, EPI_ARGS); break;
+    case 1: epi_ak<R, 1>(ak, grid, smem, st, EPI_ARGS); break;
+    case 4: epi_ak<R, 4>(ak, grid, smem, st, EPI_ARGS); break;
+    case 9: epi_ak<R, 9>(ak, grid, smem, st, EPI_ARGS); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef EPI_ARGS
+  return cudaGetLastError();
+}
+
+
+#define TDDFT_EPI_INST(R)                                                                                       \
+  template cudaError_t launch_epilogue<R>(cudaStream_t, int, const void*, const void*, const void*, void*, void*, \
+                                          void*, const R*, const ProjTables<R>&, const void*, int,              \
+                                          const EpiParams&);
+
+TDDFT_EPI_INST(float)
+TDDFT_EPI_INST(double)
+
+}  // namespace tddft
