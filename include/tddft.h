@@ -212,6 +212,19 @@ tddft_status tddft_backward(tddft_handle h, int nsteps, int ckpt_every, const do
  * tddft_observables.  No-op without atoms. */
 tddft_status tddft_atom_moments(tddft_handle h, double* M, double* N);
 
+/* Global spin torques at the current state and time t, the terms of dM/dt = i <[H, sigma]>
+ * summed over the occupied spinors with weights w_k f_i (M = int m dV, m = psi^dagger sigma psi):
+ *   soc[3]    spin-orbit torque of the L.S projector blocks (Eq. SOtorque):
+ *             sum_k w_k sum_i f_i sum_a c^dagger 2 i [D_a, S] c, with c = <beta~_a|psi_ki> at
+ *             k + A(t) and S = sigma / 2 on the spin index of c;
+ *   xc[3]     2 int b_xc x m dV (part of Eq. GMT; zero at every point in the locally collinear
+ *             approximation, where b_xc is parallel to m);
+ *   zeeman[3] 2 mu_B B(t) x M (Eq. magrot).
+ * The kinetic term and D_l I commute with the spin and give nothing, so the three add up to
+ * dM/dt.  Host arrays of 3 doubles, any may be NULL.  Computed in FP64 from the projections
+ * (FP32 in FP32-mixed mode) and the FP64 density and XC field; synchronises the stream. */
+tddft_status tddft_torques(tddft_handle h, double* soc, double* xc, double* zeeman);
+
 /* Use this CUDA stream (a cudaStream_t; NULL = legacy default stream) for all work. */
 tddft_status tddft_set_stream(tddft_handle h, void* stream);
 

@@ -362,6 +362,35 @@ class System:
             N[a] = n.reshape(-1)[sel].sum() * self.grid.dV
         return M, N
 
+    # ---------------------------------------------------------------- torques
+    def torques(self, psi, rho, V, parts, A, B):
+        """Global spin torques, dM/dt = i <[H, sigma]> summed over the occupied spinors:
+        the local 2x2 potential gives 2 int b x m dV (Eq. GMT), split into its XC part
+        2 int b_xc x m dV (zero in the locally collinear approximation, Eq. spincont2) and the
+        Zeeman part 2 mu_B B x M (Eq. magrot); the L.S projectors give the spin-orbit torque of
+        Eq. SOtorque, sum_k w_k sum_i f_i sum_a 2 i c^dagger [D_a, S] c with S = sigma / 2 on the
+        spin index of the projections c = <beta~|psi>.  The kinetic term and D_l I commute with
+        the spin and give nothing."""
+        g = self.grid
+        n, m = parts["n"], parts["m"]
+        bxc = parts["bxc"]
+        xc = 2.0 * np.cross(bxc.reshape(3, -1).T, m.reshape(3, -1).T).sum(axis=0) * g.dV
+        M = m.sum(axis=(1, 2, 3)) * g.dV
+        zee = 2.0 * MU_B * np.cross(np.asarray(B, np.float64), M)
+        wf = self.kw[:, None] * self.occ
+        soc = np.zeros(3)
+        for ik in range(psi.shape[0]):
+            proj = self.projections(psi[ik], self.kpts[ik] + A)
+            for a, (bt, per_l) in enumerate(proj):
+                for l, (cl, _) in enumerate(per_l):
+                    D = self.blocks[a][l]
+                    for i in range(3):
+                        Si = np.kron(np.eye(2 * l + 1), PAULI[i] / 2.0)
+                        Ti = 2j * (D @ Si - Si @ D)
+                        q = np.einsum("bp,pq,bq->b", cl.conj(), Ti, cl).real
+                        soc[i] += (wf[ik] * q).sum()
+        return dict(xc=xc, zeeman=zee, soc=soc, total=xc + zee + soc)
+
     # --------------------------------------------------------------- energies
     def inner(self, a, b):
         return np.vdot(a, b) * self.grid.dV

@@ -23,7 +23,7 @@ KERNEL_CLASSES = ["fft_xy", "fft_z_kinetic", "epilogue", "proj_gather", "density
 EXPORTS = ["tddft_create", "tddft_set_fields", "tddft_set_states", "tddft_get_states", "tddft_step",
            "tddft_observables", "tddft_get_potential", "tddft_apply_hamiltonian", "tddft_set_stream",
            "tddft_info", "tddft_profile", "tddft_profile_read", "tddft_last_error", "tddft_destroy",
-           "tddft_hartree_noalloc", "tddft_backward", "tddft_atom_moments"]
+           "tddft_hartree_noalloc", "tddft_backward", "tddft_atom_moments", "tddft_torques"]
 
 
 class TddftError(RuntimeError):
@@ -87,6 +87,7 @@ def load(path=LIB_PATH):
         "tddft_hartree_noalloc": [vp, vp, i, vp, vp],
         "tddft_backward": [vp, i, i, vp, vp, vp, vp],
         "tddft_atom_moments": [vp, vp, vp],
+        "tddft_torques": [vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -260,6 +261,13 @@ class TDDFT:
         N = np.zeros(max(na, 1))
         self._check(self.lib.tddft_atom_moments(self.h, _ptr(M), _ptr(N)))
         return M[:na], N[:na]
+
+    def torques(self):
+        """Global spin torques at the current state: dict of 3-vectors soc (L.S projectors),
+        xc (2 int b_xc x m dV), zeeman (2 mu_B B x M) and their sum total = dM/dt."""
+        soc, xc, zee = np.zeros(3), np.zeros(3), np.zeros(3)
+        self._check(self.lib.tddft_torques(self.h, _ptr(soc), _ptr(xc), _ptr(zee)))
+        return dict(soc=soc, xc=xc, zeeman=zee, total=soc + xc + zee)
 
     def info(self):
         kf, kh = ctypes.c_int(), ctypes.c_int()

@@ -196,6 +196,8 @@ struct tddft_ctx {
   // projector tables (typed views over the raw allocations)
   int *g_ptr = nullptr, *g_idx = nullptr, *s_ptr = nullptr, *s_atom = nullptr;
   size_t n_entries = 0;
+  double2* Tsoc = nullptr;   // [natoms][3][2 nlm][2 nlm] 2 i [D_a, S_i] (spin-orbit torque)
+  double* tq = nullptr;       // torque partial sums: [nkb][3] spin-orbit, then 6 field sums
   int* owner = nullptr;      // nearest atom of each grid point (per-atom moments)
   double* atom_sums = nullptr;
   float* tc_part = nullptr;  // tensor-core gather partial products
@@ -1515,6 +1517,7 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   double* zr_d = nullptr;
   if ((s = upload(c, &pos_d, c->pos.empty() ? std::vector<double>(3, 0.0) : c->pos, "pos")) || (s = upload(c, &zr_d, Zr, "Zr")))
     return s;
+  if ((s = c->alloc(&c->tq, (3 * (size_t)c->nkb + 8) * sizeof(double), "torque sums"))) return s;
   if (c->natoms > 0) {
     if ((s = c->alloc(&c->owner, N3 * sizeof(int), "voronoi owner")) ||
         (s = c->alloc(&c->atom_sums, 4 * (size_t)c->natoms * 8, "atom sums")))
@@ -1539,6 +1542,37 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
     if ((s = upload(c, &c->g_ptr, ht.g_ptr, "g_ptr")) || (s = upload(c, &c->g_idx, ht.g_idx, "g_idx")) ||
         (s = upload(c, &c->s_ptr, ht.s_ptr, "s_ptr")) || (s = upload(c, &c->s_atom, ht.s_atom, "s_atom")))
       return s;
+    {
+      // spin-orbit torque matrices 2 i (D S_i - S_i D), S_i = sigma_i / 2 on the spin index of
+      // the (projector, spin) index 2 p + sigma
+      const int M = 2 * c->nlm;
+      const cd sg[3][2][2] = {{{0.0, 1.0}, {1.0, 0.0}},
+                              {{0.0, cd(0.0, -1.0)}, {cd(0.0, 1.0), 0.0}},
+                              {{1.0, 0.0}, {0.0, -1.0}}};
+      std::vector<double> T((size_t)c->natoms * 3 * M * M * 2, 0.0);
+      for (int a = 0; a < c->natoms; ++a) {
+        const double* Da = &ht.Dmat[(size_t)a * M * M * 2];
+        auto D = [&](int r, int q) { return cd(Da[(r * M + q) * 2], Da[(r * M + q) * 2 + 1]); };
+        for (int i = 0; i < 3; ++i)
+          for (int r = 0; r < M; ++r)
+            for (int q = 0; q < M; ++q) {
+              // (D S)_{rq} = sum_s D_{r,(p_q,s)} S_{s,sigma_q};  (S D)_{rq} = sum_s S_{sigma_r,s} D_{(p_r,s),q}
+              const int pq = q / 2, sq = q % 2, pr = r / 2, sr = r % 2;
+              cd ds = 0.0, sd = 0.0;
+              for (int s2 = 0; s2 < 2; ++s2) {
+                ds += D(r, 2 * pq + s2) * 0.5 * sg[i][s2][sq];
+                sd += 0.5 * sg[i][sr][s2] * D(2 * pr + s2, q);
+              }
+              const cd t = cd(0.0, 2.0) * (ds - sd);
+              const size_t o = ((((size_t)a * 3 + i) * M + r) * M + q) * 2;
+              T[o] = t.real();
+              T[o + 1] = t.imag();
+            }
+      }
+      double* Td = nullptr;
+      if ((s = upload_typed<double>(c, reinterpret_cast<void**>(&Td), T, "soc torque"))) return s;
+      c->Tsoc = reinterpret_cast<double2*>(Td);
+    }
     if (c->prec == TDDFT_FP64) {
       if ((s = upload_typed<double>(c, &c->g_tab, ht.g_tab, "g_tab")) || (s = upload_typed<double>(c, &c->s_tab, ht.s_tab, "s_tab")) ||
           (s = upload_typed<double>(c, &c->Dmat, ht.Dmat, "D")))
@@ -1662,6 +1696,51 @@ tddft_status tddft_atom_moments(tddft_handle h, double* M, double* N) {
     if (M)
       for (int c = 0; c < 3; ++c) M[3 * a + c] = out[4 * a + c] * h->dV;
     if (N) N[a] = out[4 * a + 3] * h->dV;
+  }
+  return TDDFT_OK;
+}
+
+tddft_status tddft_torques(tddft_handle h, double* soc, double* xc, double* zeeman) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no states loaded");
+  double A[3], B[3];
+  h->field_at(h->t, A, B);
+  tddft_status s;
+  const int nkb = h->nkb;
+  const bool nl = h->natoms > 0 && h->nlm > 0;
+  if (nl) {
+    // projections of the current states at k + A(t), then c^dagger 2 i [D, S] c per spinor
+    if ((s = h->prec == TDDFT_FP64 ? gather<double>(h, h->psi, A) : gather<float>(h, h->psi, A))) return s;
+    if ((s = h->launch(KC_OTHER, "soc torque", [&] {
+           return h->prec == TDDFT_FP64
+                      ? launch_soc_torque<double>(h->st, nkb, h->natoms, 2 * h->nlm, h->cbuf, h->Tsoc, h->tq)
+                      : launch_soc_torque<float>(h->st, nkb, h->natoms, 2 * h->nlm, h->cbuf, h->Tsoc, h->tq);
+         })))
+      return s;
+  }
+  if ((s = h->launch(KC_OTHER, "xc torque", [&] { return launch_xc_torque(h->st, h->N3, h->rho, h->vxc4, h->tq + 3 * nkb); })))
+    return s;
+  std::vector<double> out(3 * (size_t)nkb + 6);
+  if ((s = h->cuda(cudaMemcpyAsync(out.data(), h->tq, out.size() * 8, cudaMemcpyDeviceToHost, h->st), "torque read")) ||
+      (s = h->cuda(cudaStreamSynchronize(h->st), "torque sync")))
+    return s;
+  double ts[3] = {0.0, 0.0, 0.0};
+  if (nl)
+    for (int kb = 0; kb < nkb; ++kb) {
+      const double w = h->wf[kb];
+      for (int i = 0; i < 3; ++i) ts[i] += w * out[3 * kb + i];
+    }
+  const double* f = out.data() + 3 * nkb;
+  const double M[3] = {f[3] * h->dV, f[4] * h->dV, f[5] * h->dV};
+  const double mu_b = 0.5;
+  for (int i = 0; i < 3; ++i) {
+    if (soc) soc[i] = ts[i];
+    if (xc) xc[i] = 2.0 * f[i] * h->dV;
+  }
+  if (zeeman) {
+    zeeman[0] = 2.0 * mu_b * (B[1] * M[2] - B[2] * M[1]);
+    zeeman[1] = 2.0 * mu_b * (B[2] * M[0] - B[0] * M[2]);
+    zeeman[2] = 2.0 * mu_b * (B[0] * M[1] - B[1] * M[0]);
   }
   return TDDFT_OK;
 }

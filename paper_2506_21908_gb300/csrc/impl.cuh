@@ -115,6 +115,13 @@ size_t proj_tc_part_floats(int natoms, int nk, int nstates);
 
 // Voronoi (nearest-atom) cells and per-atom sums of m and n.
 cudaError_t launch_voronoi_owner(cudaStream_t st, int N, const double* L, int natoms, const double* pos, int* owner);
+// Spin-orbit torque per spinor: out[kb][i] = sum_a c_a^dagger T_a^i c_a (T: [natoms][3][M][M]
+// complex FP64, M = 2 nlm); XC torque and magnetisation sums: out6 = {int b_xc x m, int m}
+// without dV.
+template <typename R>
+cudaError_t launch_soc_torque(cudaStream_t st, int nkb, int natoms, int M, const void* c, const double2* T,
+                              double* out);
+cudaError_t launch_xc_torque(cudaStream_t st, size_t N3, const double* rho, const double* vxc4, double* out6);
 cudaError_t launch_atom_sums(cudaStream_t st, size_t N3, int natoms, const double* rho, const int* owner, double* out);
 
 // ---------------------------------------------------------------- adjoint launchers

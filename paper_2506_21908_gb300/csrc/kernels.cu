@@ -836,6 +836,67 @@ cudaError_t launch_nl_energy(cudaStream_t st, int nkb, int ncoef, const void* c,
   return cudaGetLastError();
 }
 
+// Spin-orbit torque of one spinor (block kb): sum over atoms and components i of
+// Re c^dagger T^i c, the rows (atom, i, r) spread over the threads, fixed-order block sums.
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_soc_torque(int natoms, int M, const typename CT<R>::type* __restrict__ c, const double2* __restrict__ T,
+             double* out) {
+  __shared__ double sh[8];
+  const typename CT<R>::type* ck = c + (size_t)blockIdx.x * natoms * M;
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int rows = natoms * M;
+  for (int i = 0; i < 3; ++i) {
+    for (int t = threadIdx.x; t < rows; t += 256) {
+      const int a = t / M, r = t - a * M;
+      const double2* Tr = T + (((size_t)a * 3 + i) * M + r) * M;
+      const typename CT<R>::type* ca = ck + (size_t)a * M;
+      double re = 0.0, im = 0.0;  // (T c)_r
+      for (int q = 0; q < M; ++q) {
+        const double cr = (double)ca[q].x, ci = (double)ca[q].y;
+        re += Tr[q].x * cr - Tr[q].y * ci;
+        im += Tr[q].x * ci + Tr[q].y * cr;
+      }
+      acc[i] += (double)ca[r].x * re + (double)ca[r].y * im;  // Re conj(c_r) (T c)_r
+    }
+  }
+  for (int i = 0; i < 3; ++i) {
+    const double v = block_sum<256>(acc[i], sh);
+    if (threadIdx.x == 0) out[(size_t)blockIdx.x * 3 + i] = v;
+  }
+}
+template <typename R>
+cudaError_t launch_soc_torque(cudaStream_t st, int nkb, int natoms, int M, const void* c, const double2* T,
+                              double* out) {
+  k_soc_torque<R><<<nkb, 256, 0, st>>>(natoms, M, (const typename CT<R>::type*)c, T, out);
+  return cudaGetLastError();
+}
+
+// int b_xc x m and int m (without dV) from rho_v and the XC 4-vector [vbar + b_z, vbar - b_z,
+// 2 b_x, -2 b_y]; one block, fixed order.
+__global__ void __launch_bounds__(1024)
+k_xc_torque(size_t N3, const double* __restrict__ rho, const double* __restrict__ vxc4, double* out) {
+  __shared__ double sh[32];
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (size_t r = threadIdx.x; r < N3; r += 1024) {
+    const double r0 = rho[r], r1 = rho[N3 + r], r2 = rho[2 * N3 + r], r3 = rho[3 * N3 + r];
+    const double mx = 2.0 * r2, my = -2.0 * r3, mz = r0 - r1;
+    const double bz = 0.5 * (vxc4[r] - vxc4[N3 + r]), bx = 0.5 * vxc4[2 * N3 + r], by = -0.5 * vxc4[3 * N3 + r];
+    acc[0] += by * mz - bz * my;
+    acc[1] += bz * mx - bx * mz;
+    acc[2] += bx * my - by * mx;
+    acc[3] += mx; acc[4] += my; acc[5] += mz;
+  }
+  for (int i = 0; i < 6; ++i) {
+    const double t = block_sum<1024>(acc[i], sh);
+    if (threadIdx.x == 0) out[i] = t;
+  }
+}
+cudaError_t launch_xc_torque(cudaStream_t st, size_t N3, const double* rho, const double* vxc4, double* out6) {
+  k_xc_torque<<<1, 1024, 0, st>>>(N3, rho, vxc4, out6);
+  return cudaGetLastError();
+}
+
 // Field integrals (without dV): [0] v_loc n, [1] v_H n, [2] e_xc, [3..5] m, [6] n, [7] B.m,
 // [8] <rho_v, V_v^xc>, [9] count of non-finite rho values.
 __global__ void __launch_bounds__(1024)
@@ -976,6 +1037,7 @@ cudaError_t launch_atom_sums(cudaStream_t st, size_t N3, int natoms, const doubl
   template cudaError_t launch_convert_out<R>(cudaStream_t, size_t, const void*, double2*);                       \
   template cudaError_t launch_band_dot<R>(cudaStream_t, size_t, int, const void*, const void*, double*);         \
   template cudaError_t launch_nl_energy<R>(cudaStream_t, int, int, const void*, const void*, double*);          \
+  template cudaError_t launch_soc_torque<R>(cudaStream_t, int, int, int, const void*, const double2*, double*);  \
   template cudaError_t launch_proj_gather_mom<R>(cudaStream_t, int, const void*, int, const ProjTables<R>&,      \
                                                  double, const EpiParams&, int, void*);
 

@@ -304,6 +304,21 @@ def bcc_states(wl):
     return atomic_orbital_states(wl.L, wl.n, wl.pos, wl.kpts, [(0.0, 0.0)] * len(wl.pos), seed=wl.seed)
 
 
+def large(nsteps=200, seed=20250625, nstates=1024):
+    """4x4x4 bcc-like supercell (a = 5.425 bohr, 128 Z=8 atoms jittered by N(0, 0.1^2) bohr, L.S
+    0.02 Ha) in a 21.7 bohr cube on 96^3; Gamma point; `nstates` occupied spinors (1024 of
+    1088 in the full case); laser as in the cluster case."""
+    rng = np.random.default_rng(seed)
+    a = 5.425
+    pos = bcc_supercell(a, 4, jitter=0.1, rng=rng)
+    L = np.array([4 * a] * 3)
+    Z, rc, w, D, lam = _species_block(1, 2, lam=0.02)
+    dt = 0.04
+    times, A, B = laser_table(nsteps, dt)
+    return Workload("large96", L, 96, pos, np.zeros(len(pos), np.int32), Z, rc, w, 2, D, lam, 5.0,
+                    np.zeros((1, 3)), np.ones(1), np.ones((1, nstates)), dt, nsteps, seed, times, A, B)
+
+
 def small_parity(n=16, nstates=5, nk=2, seed=7, lam=0.02, lmax=2, field=True, natoms=3):
     """Small multi-feature case for element-wise parity: several atoms with SOC, two k-points,
     an odd number of states, laser plus static B."""

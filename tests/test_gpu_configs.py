@@ -1,0 +1,119 @@
+"""GPU checks at the full sizes of the benchmark configurations: the magnetic cluster (64^3,
+104 spinors; the bench workload, in the launch configuration bench.py times), the bcc supercell
+(48^3, 8 k-points x 128 spinors, static B plus laser) and the large supercell's grid and atoms
+(96^3, 128 atoms with SOC; 16 of its 1024 spinors, so that the host-side inputs stay small).
+
+The oracle cannot propagate these systems in seconds, so the checks take outputs it computes
+one spinor at a time: the potential from the density of all spinors, and H psi on sampled
+spinors (Eq. HNC-SDFT with the 2x2 potential and the L.S projectors).  A full step is checked
+through properties that hold at any size: norm and charge conservation, and agreement of the
+FP32-mixed step with the FP64 step (itself pinned element-wise to the oracle at small sizes)
+within the metric's |dM| <= 1e-5 mu_B per atom."""
+import numpy as np
+import pytest
+
+from oracle import System
+from oracle.tddft import FieldTable
+from paper_2506_21908_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+T0 = 0.3  # a time inside the field tables with A(t) != 0
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def oracle_potential(wl, psi, t0):
+    s = System.from_workload(wl)
+    f = FieldTable(wl.times, wl.A, wl.B)
+    A, B = f.at(t0)
+    V, _ = s.potential(s.rho_v(psi), B)
+    return s, V, A
+
+
+def gpu_apply(wl, psi, precision, bounds, t0=T0, proj_mode=None):
+    from paper_2506_21908_gb300 import _lib
+    h = _lib.TDDFT.from_workload(wl, precision=precision, proj_mode=proj_mode, e_min=bounds[0], e_max=bounds[1])
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi, t0)
+    hpsi = h.apply_hamiltonian(psi)
+    V = h.get_potential()
+    h.close()
+    return hpsi, V
+
+
+@pytest.fixture(scope="module")
+def cluster_case():
+    wl = S.cluster(64, nsteps=8)
+    psi = S.cluster_states(wl)
+    s, V, A = oracle_potential(wl, psi, T0)
+    sample = [0, 51, 103]
+    ref = s.apply_h(psi[:, sample], V, A)
+    return wl, psi, V, sample, ref
+
+
+@pytest.mark.parametrize("precision,tol_h,tol_v", [(0, 1e-11, 1e-11), (1, 2e-5, 1e-6)])
+def test_cluster_full_size_potential_and_sampled_h(lib, cluster_case, precision, tol_h, tol_v):
+    wl, psi, V, sample, ref = cluster_case
+    hpsi, Vg = gpu_apply(wl, psi, precision, (-20.0, 140.0))
+    assert rel(Vg, V) <= tol_v
+    assert rel(hpsi[:, sample], ref) <= tol_h
+
+
+def test_cluster_full_size_step_mixed_vs_fp64(lib, cluster_case):
+    from paper_2506_21908_gb300 import _lib
+    wl, psi, _, _, _ = cluster_case
+    out = {}
+    for prec in (_lib.FP64, _lib.FP32_MIXED):
+        h = _lib.TDDFT.from_workload(wl, precision=prec)
+        h.set_fields(wl.times, wl.A, wl.B)
+        h.set_states(psi, 0.0)
+        _, _, E0, _ = h.observables(fields=False)
+        h.step(2)
+        n, m, E, norms = h.observables()
+        h.close()
+        out[prec] = (n, m, E, norms, E0)
+    n64, m64, E64, nrm64, E064 = out[_lib.FP64]
+    n32, m32, E32, nrm32, _ = out[_lib.FP32_MIXED]
+    assert np.abs(nrm64 - 1.0).max() <= 1e-11
+    assert np.abs(nrm32 - 1.0).max() <= 1e-5
+    assert abs(E64["N"] - E064["N"]) <= 1e-9 * E064["N"]
+    dM = float(np.linalg.norm(E32["M"] - E64["M"])) / len(wl.pos)
+    assert dM <= 1e-5
+    assert rel(n32, n64) <= 1e-5
+    assert rel(m32, m64) <= 1e-4
+    assert abs(E32["total"] - E64["total"]) <= 1e-4
+
+
+def test_bcc_full_size_sampled_h_fp32_mixed(lib):
+    wl = S.bcc(nsteps=8)
+    psi = S.bcc_states(wl)
+    s, V, A = oracle_potential(wl, psi, T0)
+    hpsi, Vg = gpu_apply(wl, psi, 1, (-30.0, 400.0))
+    assert rel(Vg, V) <= 1e-6
+    sample = [0, 77, 127]
+    ref = s.apply_h(psi[:, sample], V, A)  # every k-point, three spinors each
+    assert rel(hpsi[:, sample], ref) <= 2e-5
+
+
+@pytest.fixture(scope="module")
+def large_case():
+    wl = S.large(nsteps=8, nstates=16)
+    psi = S.small_parity_states(wl)
+    s, V, A = oracle_potential(wl, psi, T0)
+    sample = [0, 9]
+    ref = s.apply_h(psi[:, sample], V, A)
+    vnl = s.apply_nonlocal(psi[0, sample], wl.kpts[0] + A)
+    return wl, psi, sample, ref, vnl
+
+
+@pytest.mark.parametrize("proj_mode,tol", [(1, 2e-5), (3, 2e-5), (2, 3e-3)])
+def test_large_grid_and_atoms_sampled_h(lib, large_case, proj_mode, tol):
+    """96^3 with all 128 atoms of the large supercell: CUDA-core FP32, TF32x3 and TF32 projector
+    contractions; the tensor-core error budget is relative to the non-local part."""
+    wl, psi, sample, ref, vnl = large_case
+    hpsi, _ = gpu_apply(wl, psi, 1, (-50.0, 450.0), proj_mode=proj_mode)
+    err = np.abs(hpsi[:, sample] - ref).max()
+    assert err <= tol * np.abs(vnl).max() + 2e-5 * np.abs(ref).max()

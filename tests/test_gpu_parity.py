@@ -299,3 +299,31 @@ def test_cluster_kinetic_fp32_apply_h(lib, n, monkeypatch):
     ref = s.apply_h(psi0, o.V, A)
     assert rel(outs[0], ref) <= 2e-5
     assert rel(outs[0], outs[1]) <= 2e-6
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-5)])
+def test_torques_match_oracle(lib, precision, tol):
+    """Global spin torques (Eq. GMT, Eq. magrot, Eq. SOtorque) at the current state against the
+    oracle's commutator formula, with SOC, two k-points, laser and static B."""
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=3, nk=2, natoms=3, lam=0.3)
+    psi0 = S.small_parity_states(wl)
+    h = _lib.TDDFT.from_workload(wl, precision=precision, e_min=-20, e_max=100)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi0, 0.1)
+    tq = h.torques()
+    h.step(1)
+    tq1 = h.torques()
+    psi1 = h.get_states()
+    h.close()
+    s = System.from_workload(wl)
+    f = FieldTable(wl.times, wl.A, wl.B)
+    for t, psi, g in ((0.1, psi0, tq), (0.1 + wl.dt, psi1, tq1)):
+        A, B = f.at(t)
+        rho = s.rho_v(psi)
+        V, parts = s.potential(rho, B)
+        ref = s.torques(psi, rho, V, parts, A, B)
+        scale = np.abs(ref["total"]).max()
+        for key in ("soc", "zeeman", "total"):
+            assert np.abs(g[key] - ref[key]).max() <= tol * scale, (key, g[key], ref[key])
+        assert np.abs(g["xc"]).max() <= 1e-10 * scale
