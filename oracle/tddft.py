@@ -35,7 +35,7 @@ import math
 import numpy as np
 from scipy import special
 
-from .xc import noncollinear_xc
+from .xc import collinear_xc, noncollinear_xc, unpolarised_xc
 
 MU_B = 0.5
 PAULI = np.array([[[0, 1], [1, 0]], [[0, -1j], [1j, 0]], [[1, 0], [0, -1]]], dtype=np.complex128)
@@ -227,7 +227,7 @@ class AtomProjectors:
 
 class System:
     def __init__(self, L, n, pos, species, Z, rc_loc, width, lmax, D, lam, r_cut,
-                 kpts, kw, occ, xc=1):
+                 kpts, kw, occ, xc=1, spin_mode=0):
         self.grid = Grid(L, n)
         self.pos = np.asarray(pos, np.float64)
         self.species = np.asarray(species, np.int64)
@@ -242,6 +242,13 @@ class System:
         self.kw = np.asarray(kw, np.float64)
         self.occ = np.asarray(occ, np.float64)
         self.xc = int(xc)
+        # 0: non-collinear (Eq. HNC-SDFT); 1: collinear, sigma_z-only potential (Eq. HSDFT);
+        # 2: spin-unpolarised (no spin field at all)
+        self.spin_mode = int(spin_mode)
+        if self.spin_mode not in (0, 1, 2):
+            raise ValueError("spin_mode must be 0, 1 or 2")
+        if self.spin_mode != 0 and np.any(self.lam != 0.0):
+            raise ValueError("spin-orbit coupling couples the spin channels: it needs the non-collinear mode")
         self.vloc = local_potential(self.grid, self.pos, self.Z[self.species], self.rc[self.species])
         self.atoms = [AtomProjectors(self.grid, R, self.width[s], self.lmax, self.r_cut)
                       for R, s in zip(self.pos, self.species)]
@@ -251,7 +258,17 @@ class System:
     @classmethod
     def from_workload(cls, wl):
         return cls(wl.L, wl.n, wl.pos, wl.species, wl.Z, wl.rc_loc, wl.width, wl.lmax, wl.D, wl.lam,
-                   wl.r_cut, wl.kpts, wl.kw, wl.occ, wl.xc)
+                   wl.r_cut, wl.kpts, wl.kw, wl.occ, wl.xc, getattr(wl, "spin_mode", 0))
+
+    def effective_B(self, B):
+        """External field seen by the spin: all of B (non-collinear), its z component along the
+        quantisation axis (collinear, Eq. HSDFT), none (unpolarised)."""
+        B = np.asarray(B, np.float64)
+        if self.spin_mode == 1:
+            return np.array([0.0, 0.0, B[2]])
+        if self.spin_mode == 2:
+            return np.zeros(3)
+        return B
 
     # ------------------------------------------------------------------ density
     def rho_v(self, psi):
@@ -276,12 +293,18 @@ class System:
         b = b_xc + mu_B B (Eq. HNC-SDFT, Eq. zeeman_potential).  Also returns the parts."""
         n, m = self.n_m(rho)
         vH = hartree_potential(self.grid, n)
-        if self.xc:
-            exc, vbar, bxc = noncollinear_xc(n, m)
-        else:
+        if not self.xc:
             exc, vbar, bxc = np.zeros_like(n), np.zeros_like(n), np.zeros_like(m)
+        elif self.spin_mode == 1:
+            exc, vbar, bz = collinear_xc(rho[0], rho[1])
+            bxc = np.stack([np.zeros_like(n), np.zeros_like(n), bz])
+        elif self.spin_mode == 2:
+            exc, vbar = unpolarised_xc(n)
+            bxc = np.zeros_like(m)
+        else:
+            exc, vbar, bxc = noncollinear_xc(n, m)
         v = self.vloc + vH + vbar
-        b = bxc + MU_B * np.asarray(B, np.float64)[:, None, None, None]
+        b = bxc + MU_B * self.effective_B(B)[:, None, None, None]
         V = np.stack([v + b[2], v - b[2], 2.0 * b[0], -2.0 * b[1]])
         return V, dict(vH=vH, exc=exc, vbar=vbar, bxc=bxc, n=n, m=m)
 
@@ -376,7 +399,7 @@ class System:
         bxc = parts["bxc"]
         xc = 2.0 * np.cross(bxc.reshape(3, -1).T, m.reshape(3, -1).T).sum(axis=0) * g.dV
         M = m.sum(axis=(1, 2, 3)) * g.dV
-        zee = 2.0 * MU_B * np.cross(np.asarray(B, np.float64), M)
+        zee = 2.0 * MU_B * np.cross(self.effective_B(B), M)
         wf = self.kw[:, None] * self.occ
         soc = np.zeros(3)
         for ik in range(psi.shape[0]):
@@ -411,7 +434,7 @@ class System:
         eloc = (self.vloc * n).sum() * g.dV
         eH = 0.5 * (parts["vH"] * n).sum() * g.dV
         exc = parts["exc"].sum() * g.dV
-        ez = MU_B * (np.asarray(B)[:, None, None, None] * m).sum() * g.dV
+        ez = MU_B * (self.effective_B(B)[:, None, None, None] * m).sum() * g.dV
         vxc4 = np.stack([parts["vbar"] + parts["bxc"][2], parts["vbar"] - parts["bxc"][2],
                          2.0 * parts["bxc"][0], -2.0 * parts["bxc"][1]])
         exc_pot = (rho * vxc4).sum() * g.dV

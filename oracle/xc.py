@@ -103,3 +103,35 @@ def noncollinear_xc(n, m):
         safe = np.where(dirok, mag, 1.0)
         b = np.where(dirok[None], bmag[None] * m / safe[None], 0.0)
     return e, vbar, b
+
+
+def collinear_xc(nu, nd):
+    """Collinear LSDA on the spin-channel densities (Eq. SDFT / Eq. HSDFT): returns (e_xc per
+    volume, vbar = (v_up + v_dn)/2, b_z = (v_up - v_dn)/2); the field is along the quantisation
+    axis only."""
+    nu = np.asarray(nu, np.float64)
+    nd = np.asarray(nd, np.float64)
+    n = nu + nd
+    e = np.zeros_like(n)
+    vbar = np.zeros_like(n)
+    bz = np.zeros_like(n)
+    ok = n >= N_THR
+    if np.any(ok):
+        ee, vu, vd = lsda(nu[ok], nd[ok])
+        e[ok] = ee
+        vbar[ok] = 0.5 * (vu + vd)
+        bz[ok] = 0.5 * (vu - vd)
+    return e, vbar, bz
+
+
+def unpolarised_xc(n):
+    """Spin-unpolarised LDA, n_up = n_dn = n/2: returns (e_xc per volume, v_xc)."""
+    n = np.asarray(n, np.float64)
+    e = np.zeros_like(n)
+    v = np.zeros_like(n)
+    ok = n >= N_THR
+    if np.any(ok):
+        ee, vu, _ = lsda(0.5 * n[ok], 0.5 * n[ok])
+        e[ok] = ee
+        v[ok] = vu
+    return e, v

@@ -54,6 +54,7 @@ class Workload:
     xc: int = 1
     n_sc: int = 1
     exp_order: int = 0
+    spin_mode: int = 0        # 0 non-collinear, 1 collinear (sigma_z only), 2 unpolarised
 
     @property
     def nk(self):
