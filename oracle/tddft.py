@@ -504,6 +504,28 @@ def exp_chebyshev(apply_h, psi, tau, emin, emax, K):
     return acc
 
 
+def exp_crank_nicolson(apply_h, psi, tau, tol=1e-14):
+    """Crank-Nicolson step (1 + i tau H / 2)^{-1} (1 - i tau H / 2) psi (the Cayley transform of
+    -i tau H), the linear system solved by GMRES on the matrix-free H to relative residual tol."""
+    from scipy.sparse.linalg import LinearOperator, gmres
+    shape = psi.shape
+    nvec = psi.size
+
+    def amul(x):
+        x = x.reshape(shape)
+        return (x + 0.5j * tau * apply_h(x)).reshape(-1)
+
+    A = LinearOperator((nvec, nvec), matvec=amul, dtype=np.complex128)
+    rhs = (psi - 0.5j * tau * apply_h(psi)).reshape(-1)
+    try:
+        x, info = gmres(A, rhs, x0=psi.reshape(-1).copy(), rtol=tol, atol=0.0, restart=200, maxiter=50)
+    except TypeError:  # scipy releases that name the relative tolerance `tol`
+        x, info = gmres(A, rhs, x0=psi.reshape(-1).copy(), tol=tol, atol=0.0, restart=200, maxiter=50)
+    if info != 0:
+        raise RuntimeError("Crank-Nicolson solve did not converge (%d)" % info)
+    return x.reshape(shape)
+
+
 def exp_taylor(apply_h, psi, tau, K):
     """Exp(-i tau H) psi ~ sum_{k<=K} (-i tau H)^k / k! psi."""
     term = psi
@@ -540,14 +562,18 @@ class Oracle:
             else:
                 self.K_full = chebyshev_order(self.dt * dlt, cheb_tol)
                 self.K_half = chebyshev_order(0.5 * self.dt * dlt, cheb_tol)
-        else:
+        elif self.exp_kind == 1:
             self.K_full = self.K_half = int(exp_order) if exp_order > 0 else 4
+        else:
+            self.K_full = self.K_half = 0  # Crank-Nicolson: an iterative solve, no fixed order
 
     def _exp(self, psi, V, t, tau, K):
         A, _ = self.f.at(t)
         h = lambda x: self.s.apply_h(x, V, A)  # noqa: E731
         if self.exp_kind == 0:
             return exp_chebyshev(h, psi, tau, self.emin, self.emax, K)
+        if self.exp_kind == 2:
+            return exp_crank_nicolson(h, psi, tau)
         return exp_taylor(h, psi, tau, K)
 
     def step(self):

@@ -111,6 +111,30 @@ def laser_table(nsteps, dt, E0=0.01, omega=0.057, fwhm_fs=10.0, pol=(1.0, 0.0, 0
     return times, A, B
 
 
+def magnetic_pulse_B(t, amp, eps, omega0, t0, tau, phi=0.0, delta_B=(0.0, 0.0, 0.0)):
+    """Uniform magnetic pulse of the paper's magnetic-drive experiments:
+    B(t) = amp eps [cos(omega0 (t - t0) + phi) exp(-(t - t0)^2 / (2 tau^2)) - 1] Theta(t - t0)
+           + delta_B Theta(t - t0),
+    with eps normalised to a unit vector and Theta(0) = 1."""
+    t = np.asarray(t, dtype=np.float64)
+    e = np.asarray(eps, np.float64)
+    e = e / np.linalg.norm(e)
+    step = (t >= t0).astype(np.float64)
+    env = np.cos(omega0 * (t - t0) + phi) * np.exp(-((t - t0) ** 2) / (2.0 * tau * tau)) - 1.0
+    return (amp * env * step)[..., None] * e + step[..., None] * np.asarray(delta_B, np.float64)
+
+
+def magnetic_pulse_table(nsteps, dt, amp=0.01, eps=(1.0, 0.0, 1.0), omega0=0.05, t0=None, tau=20.0, phi=0.0,
+                         delta_B=(0.0, 0.0, 0.0), A_table=None):
+    """Field table at every step time for the magnetic pulse (no laser unless A_table is
+    given); the pulse starts at a tenth of the run unless t0 is given."""
+    times = np.arange(nsteps + 1, dtype=np.float64) * dt
+    if t0 is None:
+        t0 = 0.1 * nsteps * dt
+    A = np.zeros((len(times), 3)) if A_table is None else np.asarray(A_table, np.float64)
+    return times, A, magnetic_pulse_B(times, amp, eps, omega0, t0, tau, phi, delta_B)
+
+
 def zero_fields(nsteps, dt):
     times = np.arange(nsteps + 1, dtype=np.float64) * dt
     return times, np.zeros((len(times), 3)), np.zeros((len(times), 3))

@@ -180,3 +180,58 @@ def test_collinear_limit_equals_two_decoupled_lsda_channels():
     for i, sg in enumerate(spins):
         assert np.abs(o.psi[0, i, sg] - phis[i]).max() < 1e-12
         assert np.abs(o.psi[0, i, 1 - sg]).max() < 1e-14
+
+
+def test_magnetic_pulse_uniform_gas_closed_form():
+    """Uniform gas, XC off, the paper's magnetic pulse B(t) = b(t) eps (delta_B along eps): all
+    H(t) commute, and the ETRS step is exact for the linearly interpolated field table, so M
+    turns about eps by 2 mu_B times the trapezoidal integral of b over the table (Eq. magrot)."""
+    s, psi = uniform_gas(nstates=3, xc=0)
+    eps = np.array([1.0, 0.0, 1.0]) / math.sqrt(2.0)
+    dt, nst = 0.1, 30
+    times, A, Bt = S.magnetic_pulse_table(nst, dt, amp=0.6, eps=eps, omega0=2.0, t0=0.45, tau=0.8,
+                                          phi=0.3, delta_B=0.2 * eps)
+    b = Bt @ eps
+    assert np.allclose(Bt, b[:, None] * eps[None, :], atol=1e-15)
+    assert b[0] == 0.0 and b[5] != 0.0
+    o = make_oracle(s, psi, times, A, Bt, dt)
+    M0 = o.observables()[2]["M"]
+    theta = 0.0
+    for k in range(1, nst + 1):
+        o.step()
+        theta += 2 * MU_B * 0.5 * dt * (b[k - 1] + b[k])
+        M = o.observables()[2]["M"]
+        assert np.allclose(M, rotate(M0, eps, theta), atol=1e-11), k
+
+
+def _dense_h(s, V, A, shape):
+    """H as a dense matrix on a tiny system, column by column."""
+    nvec = int(np.prod(shape))
+    H = np.empty((nvec, nvec), np.complex128)
+    e = np.zeros(nvec, np.complex128)
+    for j in range(nvec):
+        e[j] = 1.0
+        H[:, j] = s.apply_h(e.reshape(shape), V, A).reshape(-1)
+        e[j] = 0.0
+    return H
+
+
+def test_crank_nicolson_is_the_cayley_transform():
+    """The oracle's Crank-Nicolson step equals (1 + i tau H/2)^{-1} (1 - i tau H/2) psi from a
+    dense solve, is unitary, and differs from exp(-i tau H) psi by O(tau^3) per step."""
+    from oracle.tddft import exp_crank_nicolson
+    wl, s, psi = parity_system(n=6, nstates=1, nk=1, lam=0.2, natoms=1)
+    A = np.array([0.1, -0.05, 0.02])
+    V, _ = s.potential(s.rho_v(psi), [0.02, 0.0, 0.05])
+    H = _dense_h(s, V, A, psi.shape)
+    assert np.abs(H - H.conj().T).max() <= 1e-12 * np.abs(H).max()
+    I = np.eye(H.shape[0])
+    x = psi.reshape(-1)
+    err = {}
+    for tau in (0.04, 0.02):
+        cn = exp_crank_nicolson(lambda y: s.apply_h(y, V, A), psi, tau).reshape(-1)
+        ref = np.linalg.solve(I + 0.5j * tau * H, (I - 0.5j * tau * H) @ x)
+        assert np.abs(cn - ref).max() <= 1e-11 * np.abs(ref).max()
+        assert abs(np.vdot(cn, cn).real - np.vdot(x, x).real) <= 1e-11 * np.vdot(x, x).real
+        err[tau] = np.abs(cn - expm(-1j * tau * H) @ x).max()
+    assert 7.0 < err[0.04] / err[0.02] < 9.0
