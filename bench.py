@@ -311,6 +311,40 @@ def run_ours(args):
         fp64 = {"value": ups / (ms64 / 1e3), "ms_per_step": ms64, "speedup_mixed_vs_fp64": (ups / (ms_step / 1e3)) / (ups / (ms64 / 1e3)),
                 "dm_per_atom_muB": dm, "steps_compared": nst, "K_fp64": None}
 
+    # ---------------- propagator comparison: Taylor-4 and Crank-Nicolson against Chebyshev
+    propagators = None
+    if not args.no_propagators:
+        nst = args.warmup + args.steps
+        propagators = {"steps": nst, "reference": "Chebyshev ETRS (the headline path), same start"}
+        for name, kind in (("taylor4", _lib.EXP_TAYLOR), ("crank_nicolson", _lib.EXP_CRANK_NICOLSON)):
+            g = _lib.TDDFT.from_workload(wl, precision=_lib.FP32_MIXED, exp_kind=kind, stream=stream)
+            g.set_fields(wl.times, wl.A, wl.B)
+            g.set_states(psi0, 0.0)
+            gi = g.info()
+            terms = (gi["K_full"] + 2 * gi["K_half"]) if kind == _lib.EXP_CRANK_NICOLSON else 12
+            rec = {"K_full": gi["K_full"], "K_half": gi["K_half"], "h_applies_per_step": terms}
+            try:
+                g.step(1)
+                barrier()
+                p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                p0.record()
+                g.step(2)
+                p1.record()
+                barrier()
+                msp = p0.elapsed_time(p1) / 2
+                rec.update(ms_per_step=msp, value=ups / (msp / 1e3))
+                g.step(nst - 3)
+                _, _, Ep, nrm = g.observables(fields=False, check=False)
+                rec.update(dm_per_atom_muB_vs_chebyshev=float(np.linalg.norm(Ep["M"] - M_mixed) / len(wl.pos)),
+                           max_norm_error=float(np.abs(nrm - 1.0).max()), status=int(Ep["status"]))
+            except _lib.TddftError as err:  # e.g. Taylor-4 leaving the spectral window (unstable)
+                barrier()
+                rec.update(status=err.status, error=str(err)[:160])
+            g.close()
+            propagators[name] = rec
+        propagators["chebyshev"] = {"ms_per_step": ms_step, "K_full": info["K_full"], "K_half": info["K_half"],
+                                    "h_applies_per_step": info["K_full"] + 2 * info["K_half"]}
+
     # ---------------- adjoint gradient (differentiation workload, bounded horizon)
     adjoint = None
     if not args.no_adjoint:
@@ -353,7 +387,7 @@ def run_ours(args):
                                              3: "3xTF32 tensor cores (tcgen05)"}[args.proj],
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "fp64": fp64, "adjoint": adjoint,
+        "clocks": clocks, "fp64": fp64, "propagators": propagators, "adjoint": adjoint,
     }
     print(json.dumps(out))
     if dist is not None:
@@ -394,6 +428,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--proj", type=int, default=1,
                     help="projector contraction: 1 FP32 CUDA cores, 2 TF32 tensor cores, 3 TF32x3 tensor cores")
+    ap.add_argument("--no-propagators", action="store_true", help="skip the Taylor-4 / Crank-Nicolson comparison")
     ap.add_argument("--adj-steps", type=int, default=20)
     ap.add_argument("--adj-ckpt", type=int, default=10)
     ap.add_argument("--states", type=int, default=0,

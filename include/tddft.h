@@ -56,7 +56,8 @@ typedef enum {
 } tddft_status;
 
 enum { TDDFT_FP64 = 0, TDDFT_FP32_MIXED = 1 };
-enum { TDDFT_EXP_CHEBYSHEV = 0, TDDFT_EXP_TAYLOR = 1 };
+enum { TDDFT_EXP_CHEBYSHEV = 0, TDDFT_EXP_TAYLOR = 1, TDDFT_EXP_CRANK_NICOLSON = 2 };
+enum { TDDFT_SPIN_NONCOLLINEAR = 0, TDDFT_SPIN_COLLINEAR = 1, TDDFT_SPIN_UNPOLARISED = 2 };
 /* Projector contraction: FP64 / FP32 on the CUDA cores, or on the tensor cores (tcgen05,
  * FP32-mixed precision with lmax = 2) as one TF32 product or as the split 3 x TF32 product
  * (hi*hi + hi*lo + lo*hi, close to FP32 accuracy); FP32 accumulation in every case. */
@@ -117,15 +118,25 @@ typedef struct {
  *   nk, kpts[nk][3] (1/bohr, cartesian), kw[nk] (weights)
  *   nstates   : propagated spinors per k-point; occ[nk][nstates] occupations f
  *   dt        : time step (may be negative to run backwards)
- *   exp_kind  : TDDFT_EXP_CHEBYSHEV or TDDFT_EXP_TAYLOR
- *   exp_order : 0 = automatic (Chebyshev: smallest K with |J_k(tau Delta)| < cheb_tol for all
- *               k > K, separately for dt and dt/2); > 0 = this order for every exponential
- *               (Taylor default 4)
+ *   exp_kind  : TDDFT_EXP_CHEBYSHEV, TDDFT_EXP_TAYLOR, or TDDFT_EXP_CRANK_NICOLSON: the
+ *               Cayley transform (1 + i tau H/2)^{-1} (1 - i tau H/2) in place of exp(-i tau H),
+ *               applied through its own Chebyshev expansion on the spectral window (coefficients
+ *               by Gauss-Chebyshev quadrature of the rational function, truncated like the
+ *               exponential's; equivalent to solving the linear system to that tolerance)
+ *   exp_order : 0 = automatic (Chebyshev and Crank-Nicolson: smallest K with |a_k| < cheb_tol
+ *               for all k > K, separately for dt and dt/2); > 0 = this order for every
+ *               exponential (Taylor default 4)
  *   cheb_tol  : truncation tolerance for automatic orders (0 = 1e-16 FP64, 1e-9 FP32-mixed)
  *   n_sc      : corrector passes per step; sc_tol > 0 stops them early when
  *               max |delta rho_v| < sc_tol (that check synchronises the stream)
  *   e_min, e_max : Chebyshev spectral window; both 0 = automatic at tddft_set_states
- *   xc        : 1 = locally collinear LSDA (Slater + PW92), 0 = no exchange-correlation */
+ *   xc        : 1 = locally collinear LSDA (Slater + PW92), 0 = no exchange-correlation
+ *   spin_mode : TDDFT_SPIN_NONCOLLINEAR (default, Eq. HNC-SDFT); TDDFT_SPIN_COLLINEAR, the
+ *               sigma_z-only potential of Eq. HSDFT (LSDA on the channel densities rho_uu, rho_dd,
+ *               field along z, only B_z couples); TDDFT_SPIN_UNPOLARISED (LDA at n/2 per channel,
+ *               no spin field, B ignored).  The last two need lambda_so = 0 (L.S couples the
+ *               channels; TDDFT_ERR_ARG otherwise) and have no tddft_backward
+ *               (TDDFT_ERR_UNSUPPORTED). */
 typedef struct {
   int precision;
   int proj_mode;
@@ -143,6 +154,7 @@ typedef struct {
   double e_min;
   double e_max;
   int xc;
+  int spin_mode;
 } tddft_params;
 
 /* Create a handle on the current CUDA device: validates the inputs, builds the G mesh,
@@ -199,7 +211,7 @@ tddft_status tddft_apply_hamiltonian(tddft_handle h, const void* in, void* out, 
  * (analytic Jacobian), the velocity-gauge kinetic term and projector phases, and the Zeeman term.
  * Memory: spinor copies at every ckpt_every-th step (checkpoints), ckpt_every copies for the
  * recomputed segment, and one copy per Chebyshev term of a step, allocated for the call only.
- * Requires Chebyshev exponentials, sc_tol = 0, and two z-slabs of the grid in shared memory
+ * Requires Chebyshev or Crank-Nicolson exponentials, sc_tol = 0, and two z-slabs of the grid in shared memory
  * (n <= 64 in FP64, n <= 96 in FP32-mixed); otherwise TDDFT_ERR_UNSUPPORTED.  The paper has no
  * adjoint; the loss and parameterisation follow the differentiation workload of this library. */
 tddft_status tddft_backward(tddft_handle h, int nsteps, int ckpt_every, const double* dL_drho, double* loss,

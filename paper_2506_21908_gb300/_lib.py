@@ -14,8 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtddft.so")
 
 FP64, FP32_MIXED = 0, 1
+SPIN_NONCOLLINEAR, SPIN_COLLINEAR, SPIN_UNPOLARISED = 0, 1, 2
 PROJ_FP64, PROJ_FP32, PROJ_TF32, PROJ_TF32X3 = 0, 1, 2, 3
-EXP_CHEBYSHEV, EXP_TAYLOR = 0, 1
+EXP_CHEBYSHEV, EXP_TAYLOR, EXP_CRANK_NICOLSON = 0, 1, 2
 E_NAMES = ["kin", "nl", "loc", "H", "xc", "Z", "total", "t", "xc_pot", "N"]
 KERNEL_CLASSES = ["fft_xy", "fft_z_kinetic", "epilogue", "proj_gather", "density", "potential", "other"]
 
@@ -56,7 +57,7 @@ class Params(ctypes.Structure):
                 ("occ", ctypes.c_void_p), ("dt", ctypes.c_double), ("exp_kind", ctypes.c_int),
                 ("exp_order", ctypes.c_int), ("cheb_tol", ctypes.c_double), ("n_sc", ctypes.c_int),
                 ("sc_tol", ctypes.c_double), ("e_min", ctypes.c_double), ("e_max", ctypes.c_double),
-                ("xc", ctypes.c_int)]
+                ("xc", ctypes.c_int), ("spin_mode", ctypes.c_int)]
 
 
 _LIB = None
@@ -121,7 +122,7 @@ class TDDFT:
 
     def __init__(self, L, n, pos, species, Z, rc_loc, width, lmax, D, lam, r_cut, kpts, kw, occ, dt,
                  precision=FP64, exp_kind=EXP_CHEBYSHEV, exp_order=0, cheb_tol=0.0, n_sc=1, sc_tol=0.0,
-                 e_min=0.0, e_max=0.0, xc=1, proj_mode=None, stream=None):
+                 e_min=0.0, e_max=0.0, xc=1, proj_mode=None, stream=None, spin_mode=0):
         self.lib = load()
         self._keep = []
         L = _f64(L)
@@ -148,7 +149,7 @@ class TDDFT:
             proj_mode = 0 if precision == FP64 else 1
         prm = Params(int(precision), int(proj_mode), len(kpts), _ptr(kpts).value, _ptr(kw).value, occ.shape[1],
                      _ptr(occ).value, float(dt), int(exp_kind), int(exp_order), float(cheb_tol), int(n_sc),
-                     float(sc_tol), float(e_min), float(e_max), int(xc))
+                     float(sc_tol), float(e_min), float(e_max), int(xc), int(spin_mode))
         h = ctypes.c_void_p()
         st = self.lib.tddft_create(ctypes.byref(cell), ctypes.byref(grid), ctypes.byref(atoms), ctypes.byref(proj),
                                    ctypes.byref(prm), ctypes.byref(h))
@@ -170,6 +171,7 @@ class TDDFT:
     def from_workload(cls, wl, **kw):
         return cls(wl.L, wl.n, wl.pos, wl.species, wl.Z, wl.rc_loc, wl.width, wl.lmax, wl.D, wl.lam, wl.r_cut,
                    wl.kpts, wl.kw, wl.occ, wl.dt, xc=kw.pop("xc", wl.xc), n_sc=kw.pop("n_sc", wl.n_sc),
+                   spin_mode=kw.pop("spin_mode", getattr(wl, "spin_mode", 0)),
                    exp_order=kw.pop("exp_order", wl.exp_order), **kw)
 
     def _check(self, st):

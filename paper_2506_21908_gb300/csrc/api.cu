@@ -171,7 +171,7 @@ struct tddft_ctx {
   int nk = 0, nb = 0, nkb = 0;
   std::vector<double> kpts, kw, occ, wf;
   double dt = 0;
-  int exp_kind = 0, exp_order = 0, n_sc = 0, xc = 1;
+  int exp_kind = 0, exp_order = 0, n_sc = 0, xc = 1, spin_mode = 0;
   double cheb_tol = 0, sc_tol = 0, emin_user = 0, emax_user = 0;
   std::vector<double> ft, fA, fB;
   // propagation state
@@ -293,6 +293,13 @@ struct tddft_ctx {
       A[a] = (1.0 - w) * fA[3 * (j - 1) + a] + w * fA[3 * j + a];
       B[a] = (1.0 - w) * fB[3 * (j - 1) + a] + w * fB[3 * j + a];
     }
+  }
+  // A(t) and the external field seen by the spin: all of B (non-collinear), its component along
+  // the quantisation axis z (collinear), none (unpolarised).
+  void fields(double tt, double A[3], double B[3]) const {
+    field_at(tt, A, B);
+    if (spin_mode == TDDFT_SPIN_COLLINEAR) B[0] = B[1] = 0.0;
+    if (spin_mode == TDDFT_SPIN_UNPOLARISED) B[0] = B[1] = B[2] = 0.0;
   }
   double kinetic_max_for(const double s[3]) const {
     const double pi = 3.14159265358979323846;
@@ -480,11 +487,11 @@ tddft_status hartree(tddft_ctx* c, const double* rho) {
 // rho (4 x N3) -> V (FP64) and, in mixed precision, its FP32 copy.
 tddft_status potential(tddft_ctx* c, const double* rho, double tt, double* Vout, float* Vfout) {
   double A[3], B[3];
-  c->field_at(tt, A, B);
+  c->fields(tt, A, B);
   tddft_status s = hartree(c, rho);
   if (s) return s;
   return c->launch(KC_POT, "potential", [&] {
-    return launch_potential(c->st, c->N3, rho, c->vH, c->vloc, B, c->xc, Vout, Vfout, c->exc, c->vxc4);
+    return launch_potential(c->st, c->N3, rho, c->vH, c->vloc, B, c->xc, c->spin_mode, Vout, Vfout, c->exc, c->vxc4);
   });
 }
 
@@ -710,12 +717,12 @@ tddft_status taylor_series(tddft_ctx* c, const void* in, bool vcur, const double
 template <typename R> tddft_status one_step(tddft_ctx* c) {
   const double t0 = c->t, t1 = c->t + c->dt;
   double A0[3], B0[3], A1[3], B1[3];
-  c->field_at(t0, A0, B0);
-  c->field_at(t1, A1, B1);
+  c->fields(t0, A0, B0);
+  c->fields(t1, A1, B1);
   float* Vnf = c->prec == TDDFT_FP64 ? nullptr : c->Vnewf;
   float* Vcf = c->prec == TDDFT_FP64 ? nullptr : c->Vf;
   tddft_status s;
-  if (c->exp_kind == TDDFT_EXP_CHEBYSHEV) {
+  if (c->exp_kind != TDDFT_EXP_TAYLOR) {
     if ((s = cheb_series<R>(c, c->psi, vsel<R>(c, true), A0, c->pred, c->cf_full, c->K_full, c->phi, c->cf_half,
                             c->K_half)))
       return s;
@@ -727,7 +734,7 @@ template <typename R> tddft_status one_step(tddft_ctx* c) {
   if ((s = potential(c, c->rho2, t1, c->Vnew, Vnf))) return s;
   if ((s = window_check(c, c->Vnew))) return s;
   auto half = [&]() -> tddft_status {
-    if (c->exp_kind == TDDFT_EXP_CHEBYSHEV)
+    if (c->exp_kind != TDDFT_EXP_TAYLOR)
       return cheb_series<R>(c, c->phi, vsel<R>(c, false), A1, c->psi, c->cf_half, c->K_half, nullptr, c->cf_half, 0);
     return taylor_series<R>(c, c->phi, false, A1, 0.5 * c->dt, c->K_half, c->psi);
   };
@@ -963,8 +970,8 @@ tddft_status adjoint_step(tddft_ctx* c, AdjWork& w, const void* psi_n, double t0
                           double gA1[3], double gB1[3]) {
   const double t1 = t0 + c->dt;
   double A0[3], B0[3], A1[3], B1[3];
-  c->field_at(t0, A0, B0);
-  c->field_at(t1, A1, B1);
+  c->fields(t0, A0, B0);
+  c->fields(t1, A1, B1);
   const bool f64 = c->prec == TDDFT_FP64;
   const int K1 = std::max(c->K_full, c->K_half), Kh = c->K_half;
   const size_t n = c->psi_elems();
@@ -1049,8 +1056,8 @@ void add_table(const tddft_ctx* c, double tt, const double gA[3], const double g
 template <typename R>
 tddft_status do_backward(tddft_ctx* c, int nsteps, int ckpt, const double* dL_drho, double* loss, double* dA,
                          double* dB) {
-  if (c->exp_kind != TDDFT_EXP_CHEBYSHEV || c->sc_tol > 0.0)
-    return c->fail(TDDFT_ERR_UNSUPPORTED, "backward needs Chebyshev exponentials and sc_tol = 0");
+  if (c->exp_kind == TDDFT_EXP_TAYLOR || c->sc_tol > 0.0)
+    return c->fail(TDDFT_ERR_UNSUPPORTED, "backward needs Chebyshev or Crank-Nicolson exponentials and sc_tol = 0");
   {
     const size_t smem = (size_t)(c->N + 2 * c->N * (c->N + 1)) * 2 * sizeof(R) + 24 * sizeof(double);
     if (smem > 227 * 1024) return c->fail(TDDFT_ERR_UNSUPPORTED, "backward: grid too large for the adjoint z pass");
@@ -1190,6 +1197,40 @@ void set_orders(tddft_ctx* c) {
     };
     c->cf_full = coefs(c->dt, c->K_full);
     c->cf_half = coefs(0.5 * c->dt, c->K_half);
+  } else if (c->exp_kind == TDDFT_EXP_CRANK_NICOLSON) {
+    // Chebyshev coefficients of the Cayley transform f(E) = (1 - i tau E/2) / (1 + i tau E/2) on
+    // [emin, emax]: a_k = (2 - delta_k0)/Q sum_j f(c + Delta cos th_j) cos(k th_j), th_j = pi (j + 1/2)/Q
+    // (Gauss-Chebyshev).  f has its pole at E = 2i/tau, off the window, so a_k decays
+    // geometrically; Q = 4096 nodes leave an aliasing error far below the truncation.
+    const double tol = c->cheb_tol > 0 ? c->cheb_tol : (c->prec == TDDFT_FP64 ? 1e-16 : 1e-9);
+    const double pi = 3.14159265358979323846;
+    const int Q = 4096, KM = Q / 2;
+    auto cn = [&](double tau, int& K) {
+      std::vector<cd> fv(Q);
+      std::vector<double> th(Q);
+      for (int j = 0; j < Q; ++j) {
+        th[j] = pi * (j + 0.5) / Q;
+        const double E = cc + dlt * std::cos(th[j]);
+        fv[j] = cd(1.0, -0.5 * tau * E) / cd(1.0, 0.5 * tau * E);
+      }
+      std::vector<cd> a(KM);
+      for (int k = 0; k < KM; ++k) {
+        cd sum = 0.0;
+        for (int j = 0; j < Q; ++j) sum += fv[j] * std::cos(k * th[j]);
+        a[k] = (k == 0 ? 1.0 : 2.0) / Q * sum;
+      }
+      if (c->exp_order > 0) {
+        K = std::min(c->exp_order, KM - 1);
+      } else {
+        K = 0;
+        for (int k = KM - 1; k >= 0; --k)
+          if (std::abs(a[k]) >= tol) { K = k; break; }
+      }
+      a.resize(K + 1);
+      return a;
+    };
+    c->cf_full = cn(c->dt, c->K_full);
+    c->cf_half = cn(0.5 * c->dt, c->K_half);
   } else {
     c->K_full = c->K_half = c->exp_order > 0 ? c->exp_order : 4;
   }
@@ -1277,7 +1318,7 @@ template <typename R> tddft_status do_get_states(tddft_ctx* c, void* out, int on
 template <typename R> tddft_status do_observables(tddft_ctx* c, double* n, double* m, double* E, double* M, double* norms) {
   tddft_status s;
   double A[3], B[3];
-  c->field_at(c->t, A, B);
+  c->fields(c->t, A, B);
   const int nkb = c->nkb;
   double* dots = c->red + 16;  // [nkb][2] then [nkb][2] then [nkb]
   double* kdots = dots + 2 * nkb;
@@ -1347,7 +1388,7 @@ template <typename R> tddft_status do_apply_h(tddft_ctx* c, const void* in, void
   const size_t n = c->psi_elems();
   tddft_status s;
   double A[3], B[3];
-  c->field_at(c->t, A, B);
+  c->fields(c->t, A, B);
   // stage the input into Ta (precision R)
   if (c->prec == TDDFT_FP64) {
     if ((s = c->cuda(cudaMemcpyAsync(c->Ta, in, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st), "apply_h in"))) return s;
@@ -1421,7 +1462,8 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
     for (int b = 0; b < c->nb; ++b) c->wf[k * c->nb + b] = c->kw[k] * c->occ[k * c->nb + b];
   if (!(pr->dt != 0.0) || !std::isfinite(pr->dt)) return c->fail(TDDFT_ERR_ARG, "dt must be finite and non-zero");
   c->dt = pr->dt;
-  if (pr->exp_kind != TDDFT_EXP_CHEBYSHEV && pr->exp_kind != TDDFT_EXP_TAYLOR) return c->fail(TDDFT_ERR_ARG, "bad exp_kind");
+  if (pr->exp_kind != TDDFT_EXP_CHEBYSHEV && pr->exp_kind != TDDFT_EXP_TAYLOR && pr->exp_kind != TDDFT_EXP_CRANK_NICOLSON)
+    return c->fail(TDDFT_ERR_ARG, "bad exp_kind");
   c->exp_kind = pr->exp_kind;
   c->exp_order = std::max(0, pr->exp_order);
   c->cheb_tol = pr->cheb_tol;
@@ -1432,6 +1474,13 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   if ((c->emin_user != 0.0 || c->emax_user != 0.0) && !(c->emax_user > c->emin_user))
     return c->fail(TDDFT_ERR_ARG, "e_max must exceed e_min");
   c->xc = pr->xc ? 1 : 0;
+  c->spin_mode = pr->spin_mode;
+  if (c->spin_mode < TDDFT_SPIN_NONCOLLINEAR || c->spin_mode > TDDFT_SPIN_UNPOLARISED)
+    return c->fail(TDDFT_ERR_ARG, "spin_mode must be 0 (non-collinear), 1 (collinear) or 2 (unpolarised)");
+  if (c->spin_mode != TDDFT_SPIN_NONCOLLINEAR && pj->lambda_so)
+    for (int i = 0; i < pj->nspecies * (pj->lmax + 1); ++i)
+      if (pj->lambda_so[i] != 0.0)
+        return c->fail(TDDFT_ERR_ARG, "spin-orbit coupling couples the spin channels: it needs the non-collinear mode");
   {
     // Default: five launches per Chebyshev term (FFT passes, gather, pointwise epilogue), the
     // faster form on this part.  TDDFT_FUSED=1 selects the fused term kernel (same results).
@@ -1675,6 +1724,8 @@ tddft_status tddft_backward(tddft_handle h, int nsteps, int ckpt_every, const do
                             double* dL_dA, double* dL_dB) {
   if (!h) return TDDFT_ERR_ARG;
   if (nsteps < 1 || !dL_drho) return h->fail(TDDFT_ERR_ARG, "backward needs nsteps >= 1 and dL_drho");
+  if (h->spin_mode != TDDFT_SPIN_NONCOLLINEAR)
+    return h->fail(TDDFT_ERR_UNSUPPORTED, "the adjoint covers the non-collinear mode only");
   if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "tddft_set_states must come first");
   return h->prec == TDDFT_FP64 ? do_backward<double>(h, nsteps, ckpt_every, dL_drho, loss, dL_dA, dL_dB)
                                : do_backward<float>(h, nsteps, ckpt_every, dL_drho, loss, dL_dA, dL_dB);
@@ -1704,7 +1755,7 @@ tddft_status tddft_torques(tddft_handle h, double* soc, double* xc, double* zeem
   if (!h) return TDDFT_ERR_ARG;
   if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no states loaded");
   double A[3], B[3];
-  h->field_at(h->t, A, B);
+  h->fields(h->t, A, B);
   tddft_status s;
   const int nkb = h->nkb;
   const bool nl = h->natoms > 0 && h->nlm > 0;

@@ -85,7 +85,7 @@ template <typename R>
 cudaError_t launch_density(cudaStream_t st, size_t N3, const void* psi, int nkb, const double* wf,
                            double* rho, double* part);
 cudaError_t launch_potential(cudaStream_t st, size_t N3, const double* rho, const double* vH,
-                             const double* vloc, const double* B, int xc, double* V, float* Vf,
+                             const double* vloc, const double* B, int xc, int spin_mode, double* V, float* Vf,
                              double* exc, double* vxc4);
 cudaError_t launch_density_to_complex(cudaStream_t st, size_t N3, const double* rho, double2* out);
 cudaError_t launch_complex_real_part(cudaStream_t st, size_t N3, const double2* in, double* out, double scale);

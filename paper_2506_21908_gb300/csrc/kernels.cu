@@ -669,7 +669,7 @@ __device__ void lsda_point(double nu, double nd, double* e, double* vu, double* 
 }
 
 __global__ void k_potential(size_t N3, const double* __restrict__ rho, const double* __restrict__ vH,
-                            const double* __restrict__ vloc, double Bx, double By, double Bz, int xc,
+                            const double* __restrict__ vloc, double Bx, double By, double Bz, int xc, int mode,
                             double* __restrict__ V, float* __restrict__ Vf, double* __restrict__ exc,
                             double* __restrict__ vxc4) {
   const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -677,7 +677,17 @@ __global__ void k_potential(size_t N3, const double* __restrict__ rho, const dou
   const double r0 = rho[r], r1 = rho[N3 + r], r2 = rho[2 * N3 + r], r3 = rho[3 * N3 + r];
   const double n = r0 + r1, mx = 2.0 * r2, my = -2.0 * r3, mz = r0 - r1;
   double e = 0.0, vbar = 0.0, bx = 0.0, by = 0.0, bz = 0.0;
-  if (xc && n >= 1e-14) {
+  if (xc && n >= 1e-14 && mode == TDDFT_SPIN_COLLINEAR) {
+    // Eq. HSDFT: LSDA on the channel densities, field along the quantisation axis
+    double vu, vd;
+    lsda_point(r0, r1, &e, &vu, &vd);
+    vbar = 0.5 * (vu + vd);
+    bz = 0.5 * (vu - vd);
+  } else if (xc && n >= 1e-14 && mode == TDDFT_SPIN_UNPOLARISED) {
+    double vu, vd;
+    lsda_point(0.5 * n, 0.5 * n, &e, &vu, &vd);
+    vbar = vu;
+  } else if (xc && n >= 1e-14) {
     const double mag = sqrt(mx * mx + my * my + mz * mz);
     const double s = fmin(mag, n);
     double vu, vd;
@@ -700,8 +710,9 @@ __global__ void k_potential(size_t N3, const double* __restrict__ rho, const dou
 }
 
 cudaError_t launch_potential(cudaStream_t st, size_t N3, const double* rho, const double* vH, const double* vloc,
-                             const double* B, int xc, double* V, float* Vf, double* exc, double* vxc4) {
-  k_potential<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, rho, vH, vloc, B[0], B[1], B[2], xc, V, Vf, exc, vxc4);
+                             const double* B, int xc, int mode, double* V, float* Vf, double* exc, double* vxc4) {
+  k_potential<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, rho, vH, vloc, B[0], B[1], B[2], xc, mode, V, Vf, exc,
+                                                            vxc4);
   return cudaGetLastError();
 }
 

@@ -27,9 +27,9 @@ def _system(nk=1, xc=1, lam=0.05, n=12, nstates=2, n_sc=1, nst=2, seed=3):
     return wl, s, psi, times, A, B
 
 
-def _gpu_backward(wl, psi, times, A, B, nst, ckpt=50, precision=0):
+def _gpu_backward(wl, psi, times, A, B, nst, ckpt=50, precision=0, exp_kind=0):
     from paper_2506_21908_gb300 import _lib
-    h = _lib.TDDFT.from_workload(wl, precision=precision, e_min=BOUNDS[0], e_max=BOUNDS[1])
+    h = _lib.TDDFT.from_workload(wl, precision=precision, e_min=BOUNDS[0], e_max=BOUNDS[1], exp_kind=exp_kind)
     h.set_fields(times, A, B)
     h.set_states(psi)
     dV = float(np.prod(wl.L)) / wl.n ** 3
@@ -41,9 +41,9 @@ def _gpu_backward(wl, psi, times, A, B, nst, ckpt=50, precision=0):
     return L, dA, dB, E
 
 
-def _gpu_loss(wl, psi, times, A, B, nst):
+def _gpu_loss(wl, psi, times, A, B, nst, exp_kind=0):
     from paper_2506_21908_gb300 import _lib
-    h = _lib.TDDFT.from_workload(wl, e_min=BOUNDS[0], e_max=BOUNDS[1])
+    h = _lib.TDDFT.from_workload(wl, e_min=BOUNDS[0], e_max=BOUNDS[1], exp_kind=exp_kind)
     h.set_fields(times, A, B)
     h.set_states(psi)
     h.step(nst)
@@ -65,10 +65,12 @@ def test_gpu_adjoint_matches_oracle_adjoint(lib, nk, xc, n_sc):
     assert np.abs(dB - gB).max() <= 1e-6 * np.abs(gB).max()
 
 
-def test_gpu_adjoint_matches_finite_differences(lib):
+@pytest.mark.parametrize("exp_kind", [0, 2])
+def test_gpu_adjoint_matches_finite_differences(lib, exp_kind):
+    """Chebyshev and Crank-Nicolson exponentials (the adjoint runs on the series coefficients)."""
     nst = 3
     wl, s, psi, times, A, B = _system(nk=1, xc=1, n_sc=1, nst=nst, seed=9)
-    L, dA, dB, _ = _gpu_backward(wl, psi, times, A, B, nst)
+    L, dA, dB, _ = _gpu_backward(wl, psi, times, A, B, nst, exp_kind=exp_kind)
     rng = np.random.default_rng(0)
     h = 1e-5
     picks = [(name, int(rng.integers(0, nst + 1)), int(rng.integers(0, 3))) for name in ("A", "B") for _ in range(4)]
@@ -78,11 +80,11 @@ def test_gpu_adjoint_matches_finite_differences(lib):
         tp[j, a] += h
         tm[j, a] -= h
         if name == "A":
-            fd = (_gpu_loss(wl, psi, times, tp, B, nst) - _gpu_loss(wl, psi, times, tm, B, nst)) / (2 * h)
+            fd = (_gpu_loss(wl, psi, times, tp, B, nst, exp_kind) - _gpu_loss(wl, psi, times, tm, B, nst, exp_kind)) / (2 * h)
             g = dA[j, a]
             scale = np.abs(dA).max()
         else:
-            fd = (_gpu_loss(wl, psi, times, A, tp, nst) - _gpu_loss(wl, psi, times, A, tm, nst)) / (2 * h)
+            fd = (_gpu_loss(wl, psi, times, A, tp, nst, exp_kind) - _gpu_loss(wl, psi, times, A, tm, nst, exp_kind)) / (2 * h)
             g = dB[j, a]
             scale = np.abs(dB).max()
         assert abs(g - fd) <= 1e-4 * scale, (name, j, a, g, fd)

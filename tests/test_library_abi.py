@@ -68,3 +68,39 @@ def test_argument_validation_before_device_use(cpu_lib):
         _lib.TDDFT(wl.L, 8, wl.pos, wl.species, wl.Z, wl.rc_loc, wl.width, 3, wl.D, wl.lam, wl.r_cut,
                    wl.kpts, wl.kw, wl.occ, wl.dt)
     assert e.value.status == -7
+
+
+def _header_structs():
+    """Field names, in order, of every `typedef struct { ... } name;` in include/tddft.h."""
+    src = open(os.path.join(ROOT, "include", "tddft.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(tddft_[a-z]+)\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if decl:
+                fields.append(re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[[^\]]*\])*\s*$", decl)[0])
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_match_the_header_layout():
+    from paper_2506_21908_gb300 import _lib
+    hs = _header_structs()
+    pairs = {"tddft_cell": _lib.Cell, "tddft_grid": _lib.Grid, "tddft_atoms": _lib.Atoms,
+             "tddft_projectors": _lib.Projectors, "tddft_params": _lib.Params}
+    assert set(hs) == set(pairs)
+    for name, cls in pairs.items():
+        assert [f[0] for f in cls._fields_] == hs[name], name
+
+
+def test_spin_mode_validation_before_device_use(cpu_lib):
+    """An unknown spin mode, and spin-orbit coupling outside the non-collinear mode, are refused
+    with TDDFT_ERR_ARG before any allocation."""
+    from paper_2506_21908_gb300 import _lib, synthetic as S
+    wl = S.small_parity(n=8, nstates=1, nk=1, natoms=1, lam=0.02)
+    for mode in (1, 2, 3):
+        with pytest.raises(_lib.TddftError) as e:
+            _lib.TDDFT.from_workload(wl, spin_mode=mode)
+        assert e.value.status == -1, mode
