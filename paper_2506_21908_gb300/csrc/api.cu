@@ -203,6 +203,7 @@ struct tddft_ctx {
   float* tc_part = nullptr;  // tensor-core gather partial products
   int* tc_err = nullptr;     // set when a tensor-core wait gave up
   void *g_tab = nullptr, *s_tab = nullptr, *Dmat = nullptr;
+  void *g_row = nullptr, *s_row = nullptr, *nrm = nullptr;
   // bookkeeping
   std::string err;
   long long launches = 0;
@@ -227,6 +228,14 @@ struct tddft_ctx {
     p.s_atom = s_atom;
     p.s_tab = (const R*)s_tab;
     p.Dmat = (const R*)Dmat;
+    p.g_row = (const R*)g_row;
+    p.s_row = (const R*)s_row;
+    p.nrm = (const R*)nrm;
+    const double pi = 3.14159265358979323846;  // the constants of solid_harmonics()
+    p.yc[0] = (R)(0.5 / std::sqrt(pi));
+    p.yc[1] = (R)std::sqrt(3.0 / (4.0 * pi));
+    p.yc[2] = (R)(0.5 * std::sqrt(15.0 / pi));
+    p.yc[3] = (R)(0.25 * std::sqrt(5.0 / pi));
     return p;
   }
 
@@ -337,6 +346,8 @@ bool supported_n(int n) {
 struct HostTables {
   std::vector<int> g_ptr, g_idx, s_ptr, s_atom;
   std::vector<double> g_tab, s_tab;  // [entries][3 + nlm]
+  std::vector<double> g_row, s_row;  // [entries][4]: d, exp(-|d|^2 / (2 w^2))
+  std::vector<double> nrm;           // [natoms][4]: N_0, N_1, N_2, 0
   std::vector<double> Dmat;          // [natoms][2nlm][2nlm][2]
   double nl_bound = 0.0;
 };
@@ -347,6 +358,8 @@ tddft_status build_tables(tddft_ctx* c, const tddft_projectors* pj, const int* s
   std::vector<std::vector<Poly>> S(c->lmax + 1);
   for (int l = 0; l <= c->lmax; ++l) S[l] = solid_harmonics(l);
   ht.g_ptr.assign(c->natoms + 1, 0);
+  ht.nrm.assign(4 * (size_t)c->natoms, 0.0);
+  std::vector<std::vector<double>> per_atom_row(c->natoms);
   std::vector<std::vector<double>> per_atom_tab(c->natoms);
   std::vector<std::vector<int>> per_atom_idx(c->natoms);
   const double h[3] = {c->L[0] / N, c->L[1] / N, c->L[2] / N};
@@ -355,6 +368,7 @@ tddft_status build_tables(tddft_ctx* c, const tddft_projectors* pj, const int* s
     const double w = pj->width[s];
     double Nl[3];
     for (int l = 0; l <= c->lmax; ++l) Nl[l] = std::sqrt(2.0 / (std::tgamma(l + 1.5) * std::pow(w, 2 * l + 3)));
+    for (int l = 0; l <= c->lmax; ++l) ht.nrm[4 * (size_t)a + l] = Nl[l];
     const double* R = &c->pos[3 * a];
     std::vector<double> dz(N), dy(N), dx(N);
     for (int i = 0; i < N; ++i) {
@@ -378,6 +392,7 @@ tddft_status build_tables(tddft_ctx* c, const tddft_projectors* pj, const int* s
           per_atom_tab[a].push_back(dy[y]);
           per_atom_tab[a].push_back(dz[z]);
           const double g = std::exp(-r2 / (2.0 * w * w));
+          per_atom_row[a].insert(per_atom_row[a].end(), {dx[x], dy[y], dz[z], g});
           for (int l = 0; l <= c->lmax; ++l)
             for (int mu = 0; mu < 2 * l + 1; ++mu)
               per_atom_tab[a].push_back(Nl[l] * g * poly_eval(S[l][mu], dx[x], dy[y], dz[z]));
@@ -389,6 +404,7 @@ tddft_status build_tables(tddft_ctx* c, const tddft_projectors* pj, const int* s
   for (int a = 0; a < c->natoms; ++a) {
     ht.g_idx.insert(ht.g_idx.end(), per_atom_idx[a].begin(), per_atom_idx[a].end());
     ht.g_tab.insert(ht.g_tab.end(), per_atom_tab[a].begin(), per_atom_tab[a].end());
+    ht.g_row.insert(ht.g_row.end(), per_atom_row[a].begin(), per_atom_row[a].end());
   }
   // scatter order: counting sort by grid point, atoms ascending
   const size_t N3 = c->N3;
@@ -398,12 +414,14 @@ tddft_status build_tables(tddft_ctx* c, const tddft_projectors* pj, const int* s
   for (size_t i = 0; i < N3; ++i) ht.s_ptr[i + 1] += ht.s_ptr[i];
   ht.s_atom.assign(ne, 0);
   ht.s_tab.assign(ne * tab, 0.0);
+  ht.s_row.assign(ne * 4, 0.0);
   std::vector<int> fill(ht.s_ptr.begin(), ht.s_ptr.end() - 1);
   for (int a = 0; a < c->natoms; ++a)
     for (int e = ht.g_ptr[a]; e < ht.g_ptr[a + 1]; ++e) {
       const int dst = fill[ht.g_idx[e]]++;
       ht.s_atom[dst] = a;
       std::memcpy(&ht.s_tab[(size_t)dst * tab], &ht.g_tab[(size_t)e * tab], sizeof(double) * tab);
+      std::memcpy(&ht.s_row[(size_t)dst * 4], &ht.g_row[(size_t)e * 4], sizeof(double) * 4);
     }
   // coupling blocks D_l I + lambda_l L.S on (p = l^2 + mu + l, sigma), index 2 p + sigma
   const int M = 2 * nlm;
@@ -1622,14 +1640,17 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
       if ((s = upload_typed<double>(c, reinterpret_cast<void**>(&Td), T, "soc torque"))) return s;
       c->Tsoc = reinterpret_cast<double2*>(Td);
     }
+    // the full tables (d and the nlm projector values per entry) only feed the tensor-core
+    // gather; the CUDA-core gather and the scatter evaluate beta from the compact rows
     if (c->prec == TDDFT_FP64) {
-      if ((s = upload_typed<double>(c, &c->g_tab, ht.g_tab, "g_tab")) || (s = upload_typed<double>(c, &c->s_tab, ht.s_tab, "s_tab")) ||
-          (s = upload_typed<double>(c, &c->Dmat, ht.Dmat, "D")))
+      if ((s = upload_typed<double>(c, &c->g_row, ht.g_row, "g_row")) || (s = upload_typed<double>(c, &c->s_row, ht.s_row, "s_row")) ||
+          (s = upload_typed<double>(c, &c->nrm, ht.nrm, "nrm")) || (s = upload_typed<double>(c, &c->Dmat, ht.Dmat, "D")))
         return s;
     } else {
-      if ((s = upload_typed<float>(c, &c->g_tab, ht.g_tab, "g_tab")) || (s = upload_typed<float>(c, &c->s_tab, ht.s_tab, "s_tab")) ||
-          (s = upload_typed<float>(c, &c->Dmat, ht.Dmat, "D")))
+      if ((s = upload_typed<float>(c, &c->g_row, ht.g_row, "g_row")) || (s = upload_typed<float>(c, &c->s_row, ht.s_row, "s_row")) ||
+          (s = upload_typed<float>(c, &c->nrm, ht.nrm, "nrm")) || (s = upload_typed<float>(c, &c->Dmat, ht.Dmat, "D")))
         return s;
+      if (c->proj_mode >= TDDFT_PROJ_TF32 && (s = upload_typed<float>(c, &c->g_tab, ht.g_tab, "g_tab"))) return s;
     }
   }
   return c->cuda(cudaDeviceSynchronize(), "create sync");

@@ -51,6 +51,12 @@ template <typename R> struct ProjTables {
   const int* s_atom = nullptr;              // atom of each scatter entry
   const R* s_tab = nullptr;                 // [entries][3 + nlm]
   const R* Dmat = nullptr;                  // [natoms][2 nlm][2 nlm] complex (re, im)
+  // Compact rows for the CUDA-core gather and the scatter: beta is evaluated from d as
+  // N_l(w_a) g S_lm(d) with g = exp(-|d|^2 / (2 w_a^2)) and S_lm the real solid harmonics.
+  const R* g_row = nullptr;                 // [entries][4]: d, g (gather order)
+  const R* s_row = nullptr;                 // [entries][4] (scatter order)
+  const R* nrm = nullptr;                   // [natoms][4]: N_0, N_1, N_2 of the atom's width, 0
+  R yc[4] = {};                             // solid-harmonic constants: l = 0, l = 1, l = 2 (xy, ...), l = 2 (3z^2 - r^2)
 };
 
 // ---------------------------------------------------------------- launchers

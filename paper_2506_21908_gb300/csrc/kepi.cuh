@@ -44,6 +44,24 @@ __device__ __forceinline__ void load_row(const R* __restrict__ t, R* v) {
   }
 }
 
+// Projector values beta_p(d) = N_l g S_lm(d), p = l^2 + l + mu, from a compact row (d, g): the
+// real solid harmonics r^l Y_lm for l <= 2 in the order of the tables (1; y, z, x; xy, yz,
+// 3z^2 - r^2, xz, x^2 - y^2), nl = N_0, N_1, N_2 of the atom, yc the harmonic constants.
+template <typename R, int NLM>
+__device__ __forceinline__ void beta_values(R x, R y, R z, R g, const R* nl, const R* yc, R* b) {
+  b[0] = nl[0] * g * yc[0];
+  if constexpr (NLM > 1) {
+    const R s1 = nl[1] * g * yc[1];
+    b[1] = s1 * y; b[2] = s1 * z; b[3] = s1 * x;
+  }
+  if constexpr (NLM > 4) {
+    const R s2 = nl[2] * g * yc[2], s0 = nl[2] * g * yc[3];
+    b[4] = s2 * (x * y); b[5] = s2 * (y * z);
+    b[6] = s0 * ((R)2 * z * z - x * x - y * y);
+    b[7] = s2 * (x * z); b[8] = (R)0.5 * s2 * (x * x - y * y);
+  }
+}
+
 // phase exp(-i arg): FP32 reduces the argument to [-pi, pi] and uses the fast intrinsic
 __device__ __forceinline__ void phase_sincos(float x, float* sn, float* cs) {
   const float r = x - 6.28318530717958647692f * rintf(x * 0.15915494309189533577f);
@@ -58,20 +76,21 @@ __device__ __forceinline__ void h_point(typename CT<R>::type& hu, typename CT<R>
                                         typename CT<R>::type pd, R V0, R V1, R hx, R hy, size_t r,
                                         const ProjTables<R>& pt, const typename CT<R>::type* dcb, R sx, R sy, R sz) {
   using C = typename CT<R>::type;
-  constexpr int TAB = 3 + NLM;
   hu = cmake<C>(hu.x + V0 * pu.x + hx * pd.x - hy * pd.y, hu.y + V0 * pu.y + hx * pd.y + hy * pd.x);
   hd = cmake<C>(hd.x + V1 * pd.x + hx * pu.x + hy * pu.y, hd.y + V1 * pd.y + hx * pu.y - hy * pu.x);
-  if (NLM > 0) {
+  if constexpr (NLM > 0) {
     const int e0 = pt.s_ptr[r], e1 = pt.s_ptr[r + 1];
     for (int e = e0; e < e1; ++e) {
       const int a = pt.s_atom[e];
-      R t[TAB];
-      load_row<R, TAB>(pt.s_tab + (size_t)e * TAB, t);
+      R t[4], nl[4], bt[NLM];
+      load_row<R, 4>(pt.s_row + (size_t)e * 4, t);
+      load_row<R, 4>(pt.nrm + (size_t)a * 4, nl);
+      beta_values<R, NLM>(t[0], t[1], t[2], t[3], nl, pt.yc, bt);
       const C* dca = dcb + (size_t)a * 2 * NLM;  // this spinor's D c of atom a, (up, dn) per p
       R vux = 0, vuy = 0, vdx = 0, vdy = 0;
 #pragma unroll
       for (int p = 0; p < NLM; ++p) {
-        const R bp = t[3 + p];
+        const R bp = bt[p];
         const Pair<C> cc = ld2(dca + 2 * p);
         vux += bp * cc.a.x; vuy += bp * cc.a.y;
         vdx += bp * cc.b.x; vdy += bp * cc.b.y;

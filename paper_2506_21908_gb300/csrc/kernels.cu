@@ -439,7 +439,6 @@ k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTable
               typename CT<R>::type* __restrict__ c_out, typename CT<R>::type* __restrict__ dc_out) {
   using C = typename CT<R>::type;
   constexpr int NV = 4 * NLM;  // reals: (re, im) x (up, dn) x NLM
-  constexpr int TAB = 3 + NLM;
   const int a = blockIdx.x;
   const int kb = blockIdx.y;
   const int k = kb / ep.nstates;
@@ -450,10 +449,13 @@ k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTable
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = (R)0;
   const int e0 = pt.g_ptr[a], e1 = pt.g_ptr[a + 1];
+  R nl[4];
+  load_row<R, 4>(pt.nrm + (size_t)a * 4, nl);
   for (int e = e0 + threadIdx.x; e < e1; e += 256) {
     const int r = pt.g_idx[e];
-    R t[TAB];
-    load_row<R, TAB>(pt.g_tab + (size_t)e * TAB, t);
+    R t[4], bt[NLM];
+    load_row<R, 4>(pt.g_row + (size_t)e * 4, t);
+    beta_values<R, NLM>(t[0], t[1], t[2], t[3], nl, pt.yc, bt);
     R sn, cs;
     sincos_r<R>(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);
     const C u = up[r], d = dn[r];
@@ -465,7 +467,7 @@ k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTable
     }
 #pragma unroll
     for (int p = 0; p < NLM; ++p) {
-      const R bp = t[3 + p];
+      const R bp = bt[p];
       acc[4 * p + 0] += bp * pux;
       acc[4 * p + 1] += bp * puy;
       acc[4 * p + 2] += bp * pdx;
