@@ -198,6 +198,7 @@ struct tddft_ctx {
   size_t n_entries = 0;
   double2* Tsoc = nullptr;   // [natoms][3][2 nlm][2 nlm] 2 i [D_a, S_i] (spin-orbit torque)
   double* tq = nullptr;       // torque partial sums: [nkb][3] spin-orbit, then 6 field sums
+  double* red_part = nullptr;  // partials of the two-pass reductions (band dots, field sums)
   int* owner = nullptr;      // nearest atom of each grid point (per-atom moments)
   double* atom_sums = nullptr;
   float* tc_part = nullptr;  // tensor-core gather partial products
@@ -1254,13 +1255,25 @@ void set_orders(tddft_ctx* c) {
   }
 }
 
+// Device address of page-locked host memory (cudaHostAlloc, cudaHostRegister), through which a
+// kernel reads or writes it directly (NVLink-C2C on Grace systems); null for pageable memory,
+// which is staged through device buffers.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (at.type == cudaMemoryTypeHost && at.devicePointer) ? at.devicePointer : nullptr;
+}
+
 template <typename R> tddft_status do_set_states(tddft_ctx* c, const void* psi, int on_device, double t0) {
   const size_t n = c->psi_elems();
   tddft_status s;
   if (c->prec == TDDFT_FP64) {
     if ((s = c->cuda(cudaMemcpyAsync(c->psi, psi, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st), "set_states copy"))) return s;
-  } else if (on_device) {
-    if ((s = c->launch(KC_OTHER, "convert in", [&] { return launch_convert_in<R>(c->st, n, (const double2*)psi, c->psi); }))) return s;
+  } else if (const void* src = on_device ? psi : mapped_host(psi)) {
+    if ((s = c->launch(KC_OTHER, "convert in", [&] { return launch_convert_in<R>(c->st, n, (const double2*)src, c->psi); }))) return s;
   } else {
     for (size_t off = 0; off < n; off += c->stage_elems) {
       const size_t m = std::min(c->stage_elems, n - off);
@@ -1320,8 +1333,8 @@ template <typename R> tddft_status do_get_states(tddft_ctx* c, void* out, int on
   tddft_status s;
   if (c->prec == TDDFT_FP64) {
     if ((s = c->cuda(cudaMemcpyAsync(out, c->psi, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st), "get_states copy"))) return s;
-  } else if (on_device) {
-    if ((s = c->launch(KC_OTHER, "convert out", [&] { return launch_convert_out<R>(c->st, n, c->psi, (double2*)out); }))) return s;
+  } else if (void* dst = on_device ? out : const_cast<void*>(mapped_host(out))) {
+    if ((s = c->launch(KC_OTHER, "convert out", [&] { return launch_convert_out<R>(c->st, n, c->psi, (double2*)dst); }))) return s;
   } else {
     for (size_t off = 0; off < n; off += c->stage_elems) {
       const size_t m = std::min(c->stage_elems, n - off);
@@ -1341,15 +1354,15 @@ template <typename R> tddft_status do_observables(tddft_ctx* c, double* n, doubl
   double* dots = c->red + 16;  // [nkb][2] then [nkb][2] then [nkb]
   double* kdots = dots + 2 * nkb;
   double* nle = kdots + 2 * nkb;
-  if ((s = c->launch(KC_OTHER, "norms", [&] { return launch_band_dot<R>(c->st, 2 * c->N3, nkb, c->psi, c->psi, dots); }))) return s;
+  if ((s = c->launch(KC_OTHER, "norms", [&] { return launch_band_dot<R>(c->st, 2 * c->N3, nkb, c->psi, c->psi, dots, c->red_part); }))) return s;
   if ((s = kinetic<R>(c, c->psi, c->tmp, A))) return s;
-  if ((s = c->launch(KC_OTHER, "kinetic dot", [&] { return launch_band_dot<R>(c->st, 2 * c->N3, nkb, c->psi, c->tmp, kdots); }))) return s;
+  if ((s = c->launch(KC_OTHER, "kinetic dot", [&] { return launch_band_dot<R>(c->st, 2 * c->N3, nkb, c->psi, c->tmp, kdots, c->red_part); }))) return s;
   if (c->natoms > 0) {
     if ((s = gather<R>(c, c->psi, A))) return s;
     if ((s = c->launch(KC_OTHER, "nl energy", [&] { return launch_nl_energy<R>(c->st, nkb, c->natoms * 2 * c->nlm, c->cbuf, c->dcbuf, nle); }))) return s;
   }
   if ((s = c->launch(KC_OTHER, "field sums", [&] {
-         return launch_field_sums(c->st, c->N3, c->rho, c->vloc, c->vH, c->exc, c->vxc4, c->V, B, c->red);
+         return launch_field_sums(c->st, c->N3, c->rho, c->vloc, c->vH, c->exc, c->vxc4, c->V, B, c->red, c->red_part);
        })))
     return s;
   std::vector<double> h(16 + 5 * nkb, 0.0);
@@ -1585,6 +1598,9 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   if ((s = upload(c, &pos_d, c->pos.empty() ? std::vector<double>(3, 0.0) : c->pos, "pos")) || (s = upload(c, &zr_d, Zr, "Zr")))
     return s;
   if ((s = c->alloc(&c->tq, (3 * (size_t)c->nkb + 8) * sizeof(double), "torque sums"))) return s;
+  if ((s = c->alloc(&c->red_part, std::max(band_dot_part_doubles(c->nkb), field_sums_part_doubles()) * sizeof(double),
+                    "reduction partials")))
+    return s;
   if (c->natoms > 0) {
     if ((s = c->alloc(&c->owner, N3 * sizeof(int), "voronoi owner")) ||
         (s = c->alloc(&c->atom_sums, 4 * (size_t)c->natoms * 8, "atom sums")))

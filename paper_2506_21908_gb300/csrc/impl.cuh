@@ -103,12 +103,14 @@ template <typename R>
 cudaError_t launch_convert_out(cudaStream_t st, size_t n, const void* in, double2* out);
 template <typename R>
 cudaError_t launch_band_dot(cudaStream_t st, size_t npts, int nbands, const void* a, const void* b,
-                            double* out2);
+                            double* out2, double* part);  // part: band_dot_part_doubles(nbands)
+size_t band_dot_part_doubles(int nbands);
 template <typename R>
 cudaError_t launch_nl_energy(cudaStream_t st, int nkb, int ncoef, const void* c, const void* dc, double* out);
 cudaError_t launch_field_sums(cudaStream_t st, size_t N3, const double* rho, const double* vloc,
                               const double* vH, const double* exc, const double* vxc4, const double* V,
-                              const double* B, double* out);
+                              const double* B, double* out, double* part);  // part: field_sums_part_doubles()
+size_t field_sums_part_doubles();
 cudaError_t launch_max_abs_diff(cudaStream_t st, size_t n, const double* a, const double* b, double* out);
 cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, double lo, double hi,
                                 double kin_max, double nl_bound, int* flag);

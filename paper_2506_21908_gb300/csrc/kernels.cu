@@ -109,14 +109,15 @@ k_fft_z(typename CT<R>::type* __restrict__ data, const typename CT<R>::type* __r
 
 // ---------------------------------------------------------------- two-factor passes (N = R1 R2)
 //
-// Row pitch of the xy plane: congruent to 8 modulo 16 elements, so that the in-row exchange
-// (8 lanes per row, rotated columns) and the column accesses are both free of bank conflicts.
+// Each thread carries two neighbouring work items (adjacent n0, K0 or x), so that every global
+// and shared-memory access moves two complex values at once (16 bytes in FP32).  Row pitch of
+// the xy plane: congruent to 8 modulo 16 elements.  The in-row exchange stores E[K0][n0] at
+// column K0 R1 + (n0 + 2 floor(K0 / 2)) mod R1: the even rotation keeps the pairs (n0, n0 + 1)
+// adjacent, and with this pitch the A-side writes, the B-side reads and writes and the column
+// accesses of the y and z transforms are all free of bank conflicts at n = 64.
 template <int N> struct TFPitch { static constexpr int value = (N % 16 == 8) ? N : (N % 16 == 0 ? N + 8 : N + 1); };
+template <int R1> __device__ __forceinline__ int tf_col(int k0, int n0) { return k0 * R1 + (n0 + 2 * (k0 >> 1)) % R1; }
 
-// xy transform of one z-plane with one shared-memory exchange per axis: the x transform's A side
-// reads global memory directly, the y transform's B side writes it directly (forward); the
-// inverse runs the steps in the opposite order.  Column of the in-row exchange: K0 R1 + (n0 +
-// K0) mod R1 (a rotation, so that the 8 lanes of a row hit distinct banks on both sides).
 template <typename R, int N, bool INV>
 __global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::value)
 k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const typename CT<R>::type* __restrict__ twg) {
@@ -124,9 +125,11 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
   using T = TF<C, N, INV>;
   constexpr int NT = FFTThreads<N>::value;
   constexpr int R1 = TwoFactor<N>::R1, R2 = TwoFactor<N>::R2;
+  static_assert(R1 % 2 == 0 && R2 % 2 == 0 && N % 2 == 0, "paired two-factor pass needs even factors");
   constexpr int RS = TFPitch<N>::value;
-  constexpr int IA = N * R1, IB = N * R2;                 // A / B items of one axis
-  constexpr int PA = (IA + NT - 1) / NT, PB = (IB + NT - 1) / NT;
+  constexpr int AX = N * R1 / 2, BX = N * R2 / 2;  // item pairs of the x transform (rows y)
+  constexpr int AY = N / 2 * R1, BY = N / 2 * R2;  // item pairs of the y transform (columns x)
+  constexpr int PAX = (AX + NT - 1) / NT, PBX = (BX + NT - 1) / NT, PAY = (AY + NT - 1) / NT, PBY = (BY + NT - 1) / NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s = tw + N;
@@ -135,157 +138,177 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
   C* o = dst + base;
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
   __syncthreads();
-  C v[PA][R2];
-  C u[PB][R1];
   if (!INV) {
-    // x, A side: item (y, n0), n0 fastest
+    // x, A side from global: pair (y, n0, n0 + 1)
 #pragma unroll
-    for (int p = 0; p < PA; ++p) {
+    for (int p = 0; p < PAX; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (IA % NT == 0 || i < IA) {
-        const int y = i / R1, n0 = i - y * R1;
+      if (AX % NT == 0 || i < AX) {
+        const int y = i / (R1 / 2), n0 = 2 * (i - y * (R1 / 2));
+        C v0[R2], v1[R2];
 #pragma unroll
-        for (int q = 0; q < R2; ++q) v[p][q] = g[y * N + n0 + R1 * q];
-        T::a_side(v[p], n0, tw);
+        for (int q = 0; q < R2; ++q) { const Pair<C> w = ld2(g + y * N + n0 + R1 * q); v0[q] = w.a; v1[q] = w.b; }
+        T::a_side(v0, n0, tw);
+        T::a_side(v1, n0 + 1, tw);
 #pragma unroll
-        for (int k0 = 0; k0 < R2; ++k0) s[y * RS + k0 * R1 + (n0 + k0) % R1] = v[p][k0];
+        for (int k0 = 0; k0 < R2; ++k0) st2(s + y * RS + tf_col<R1>(k0, n0), v0[k0], v1[k0]);
       }
     }
     __syncthreads();
-    // x, B side: item (y, K0)
+    // x, B side: pair (y, K0, K0 + 1), K0 even
+    C u0[PBX][R1], u1[PBX][R1];
 #pragma unroll
-    for (int p = 0; p < PB; ++p) {
+    for (int p = 0; p < PBX; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (IB % NT == 0 || i < IB) {
-        const int y = i / R2, k0 = i - y * R2;
+      if (BX % NT == 0 || i < BX) {
+        const int y = i / (R2 / 2), k0 = 2 * (i - y * (R2 / 2));
 #pragma unroll
-        for (int n0 = 0; n0 < R1; ++n0) u[p][n0] = s[y * RS + k0 * R1 + (n0 + k0) % R1];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PB; ++p) {
-      const int i = threadIdx.x + p * NT;
-      if (IB % NT == 0 || i < IB) {
-        const int y = i / R2, k0 = i - y * R2;
-        T::b_side(u[p], k0, tw);
-#pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) s[y * RS + k0 + R2 * k1] = u[p][k1];
-      }
-    }
-    __syncthreads();
-    // y, A side: item (x, n0), x fastest
-#pragma unroll
-    for (int p = 0; p < PA; ++p) {
-      const int i = threadIdx.x + p * NT;
-      if (IA % NT == 0 || i < IA) {
-        const int n0 = i / N, x = i - n0 * N;
-#pragma unroll
-        for (int q = 0; q < R2; ++q) v[p][q] = s[(n0 + R1 * q) * RS + x];
-        T::a_side(v[p], n0, tw);
+        for (int n0 = 0; n0 < R1; n0 += 2) {
+          const Pair<C> a = ld2(s + y * RS + tf_col<R1>(k0, n0)), b = ld2(s + y * RS + tf_col<R1>(k0 + 1, n0));
+          u0[p][n0] = a.a; u0[p][n0 + 1] = a.b; u1[p][n0] = b.a; u1[p][n0 + 1] = b.b;
+        }
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int p = 0; p < PA; ++p) {
+    for (int p = 0; p < PBX; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (IA % NT == 0 || i < IA) {
-        const int n0 = i / N, x = i - n0 * N;
+      if (BX % NT == 0 || i < BX) {
+        const int y = i / (R2 / 2), k0 = 2 * (i - y * (R2 / 2));
+        T::b_side(u0[p], k0, tw);
+        T::b_side(u1[p], k0 + 1, tw);
 #pragma unroll
-        for (int k0 = 0; k0 < R2; ++k0) s[(k0 * R1 + n0) * RS + x] = v[p][k0];
+        for (int k1 = 0; k1 < R1; ++k1) st2(s + y * RS + k0 + R2 * k1, u0[p][k1], u1[p][k1]);
       }
     }
     __syncthreads();
-    // y, B side: item (x, K0) -> global
+    // y, A side: pair (x, x + 1; n0)
+    C w0[PAY][R2], w1[PAY][R2];
 #pragma unroll
-    for (int p = 0; p < PB; ++p) {
+    for (int p = 0; p < PAY; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (IB % NT == 0 || i < IB) {
-        const int k0 = i / N, x = i - k0 * N;
+      if (AY % NT == 0 || i < AY) {
+        const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
 #pragma unroll
-        for (int n0 = 0; n0 < R1; ++n0) u[p][n0] = s[(k0 * R1 + n0) * RS + x];
-        T::b_side(u[p], k0, tw);
+        for (int q = 0; q < R2; ++q) { const Pair<C> w = ld2(s + (n0 + R1 * q) * RS + x); w0[p][q] = w.a; w1[p][q] = w.b; }
+        T::a_side(w0[p], n0, tw);
+        T::a_side(w1[p], n0, tw);
+      }
+    }
+    __syncthreads();
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) o[(k0 + R2 * k1) * N + x] = u[p][k1];
+    for (int p = 0; p < PAY; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (AY % NT == 0 || i < AY) {
+        const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
+#pragma unroll
+        for (int k0 = 0; k0 < R2; ++k0) st2(s + (k0 * R1 + n0) * RS + x, w0[p][k0], w1[p][k0]);
+      }
+    }
+    __syncthreads();
+    // y, B side to global: pair (x, x + 1; K0)
+#pragma unroll
+    for (int p = 0; p < PBY; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (BY % NT == 0 || i < BY) {
+        const int k0 = i / (N / 2), x = 2 * (i - k0 * (N / 2));
+        C a0[R1], a1[R1];
+#pragma unroll
+        for (int n0 = 0; n0 < R1; ++n0) { const Pair<C> w = ld2(s + (k0 * R1 + n0) * RS + x); a0[n0] = w.a; a1[n0] = w.b; }
+        T::b_side(a0, k0, tw);
+        T::b_side(a1, k0, tw);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) st2(o + (k0 + R2 * k1) * N + x, a0[k1], a1[k1]);
       }
     }
   } else {
-    // y, B side from global: item (x, K0)
+    // y, B side from global: pair (x, x + 1; K0)
 #pragma unroll
-    for (int p = 0; p < PB; ++p) {
+    for (int p = 0; p < PBY; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (IB % NT == 0 || i < IB) {
-        const int k0 = i / N, x = i - k0 * N;
+      if (BY % NT == 0 || i < BY) {
+        const int k0 = i / (N / 2), x = 2 * (i - k0 * (N / 2));
+        C a0[R1], a1[R1];
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) u[p][k1] = g[(k0 + R2 * k1) * N + x];
-        T::b_side(u[p], k0, tw);
+        for (int k1 = 0; k1 < R1; ++k1) { const Pair<C> w = ld2(g + (k0 + R2 * k1) * N + x); a0[k1] = w.a; a1[k1] = w.b; }
+        T::b_side(a0, k0, tw);
+        T::b_side(a1, k0, tw);
 #pragma unroll
-        for (int n0 = 0; n0 < R1; ++n0) s[(k0 * R1 + n0) * RS + x] = u[p][n0];
+        for (int n0 = 0; n0 < R1; ++n0) st2(s + (k0 * R1 + n0) * RS + x, a0[n0], a1[n0]);
       }
     }
     __syncthreads();
-    // y, A side: item (x, n0)
+    // y, A side: pair (x, x + 1; n0)
+    C w0[PAY][R2], w1[PAY][R2];
 #pragma unroll
-    for (int p = 0; p < PA; ++p) {
+    for (int p = 0; p < PAY; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (IA % NT == 0 || i < IA) {
-        const int n0 = i / N, x = i - n0 * N;
+      if (AY % NT == 0 || i < AY) {
+        const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
 #pragma unroll
-        for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[(k0 * R1 + n0) * RS + x];
-        T::a_side(v[p], n0, tw);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PA; ++p) {
-      const int i = threadIdx.x + p * NT;
-      if (IA % NT == 0 || i < IA) {
-        const int n0 = i / N, x = i - n0 * N;
-#pragma unroll
-        for (int n1 = 0; n1 < R2; ++n1) s[(n0 + R1 * n1) * RS + x] = v[p][n1];
-      }
-    }
-    __syncthreads();
-    // x, B side: item (y, K0)
-#pragma unroll
-    for (int p = 0; p < PB; ++p) {
-      const int i = threadIdx.x + p * NT;
-      if (IB % NT == 0 || i < IB) {
-        const int y = i / R2, k0 = i - y * R2;
-#pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) u[p][k1] = s[y * RS + k0 + R2 * k1];
+        for (int k0 = 0; k0 < R2; ++k0) { const Pair<C> w = ld2(s + (k0 * R1 + n0) * RS + x); w0[p][k0] = w.a; w1[p][k0] = w.b; }
+        T::a_side(w0[p], n0, tw);
+        T::a_side(w1[p], n0, tw);
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int p = 0; p < PB; ++p) {
+    for (int p = 0; p < PAY; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (IB % NT == 0 || i < IB) {
-        const int y = i / R2, k0 = i - y * R2;
-        T::b_side(u[p], k0, tw);
+      if (AY % NT == 0 || i < AY) {
+        const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
 #pragma unroll
-        for (int n0 = 0; n0 < R1; ++n0) s[y * RS + k0 * R1 + (n0 + k0) % R1] = u[p][n0];
+        for (int n1 = 0; n1 < R2; ++n1) st2(s + (n0 + R1 * n1) * RS + x, w0[p][n1], w1[p][n1]);
       }
     }
     __syncthreads();
-    // x, A side -> global: item (y, n0)
+    // x, B side: pair (y, K0, K0 + 1)
+    C u0[PBX][R1], u1[PBX][R1];
 #pragma unroll
-    for (int p = 0; p < PA; ++p) {
+    for (int p = 0; p < PBX; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (IA % NT == 0 || i < IA) {
-        const int y = i / R1, n0 = i - y * R1;
+      if (BX % NT == 0 || i < BX) {
+        const int y = i / (R2 / 2), k0 = 2 * (i - y * (R2 / 2));
 #pragma unroll
-        for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[y * RS + k0 * R1 + (n0 + k0) % R1];
-        T::a_side(v[p], n0, tw);
+        for (int k1 = 0; k1 < R1; ++k1) { const Pair<C> w = ld2(s + y * RS + k0 + R2 * k1); u0[p][k1] = w.a; u1[p][k1] = w.b; }
+      }
+    }
+    __syncthreads();
 #pragma unroll
-        for (int n1 = 0; n1 < R2; ++n1) o[y * N + n0 + R1 * n1] = v[p][n1];
+    for (int p = 0; p < PBX; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (BX % NT == 0 || i < BX) {
+        const int y = i / (R2 / 2), k0 = 2 * (i - y * (R2 / 2));
+        T::b_side(u0[p], k0, tw);
+        T::b_side(u1[p], k0 + 1, tw);
+#pragma unroll
+        for (int n0 = 0; n0 < R1; n0 += 2) {
+          st2(s + y * RS + tf_col<R1>(k0, n0), u0[p][n0], u0[p][n0 + 1]);
+          st2(s + y * RS + tf_col<R1>(k0 + 1, n0), u1[p][n0], u1[p][n0 + 1]);
+        }
+      }
+    }
+    __syncthreads();
+    // x, A side to global: pair (y, n0, n0 + 1)
+#pragma unroll
+    for (int p = 0; p < PAX; ++p) {
+      const int i = threadIdx.x + p * NT;
+      if (AX % NT == 0 || i < AX) {
+        const int y = i / (R1 / 2), n0 = 2 * (i - y * (R1 / 2));
+        C v0[R2], v1[R2];
+#pragma unroll
+        for (int k0 = 0; k0 < R2; ++k0) { const Pair<C> w = ld2(s + y * RS + tf_col<R1>(k0, n0)); v0[k0] = w.a; v1[k0] = w.b; }
+        T::a_side(v0, n0, tw);
+        T::a_side(v1, n0 + 1, tw);
+#pragma unroll
+        for (int n1 = 0; n1 < R2; ++n1) st2(o + y * N + n0 + R1 * n1, v0[n1], v1[n1]);
       }
     }
   }
 }
 
 // z transform + kinetic multiply + inverse z transform of one y-slab, one exchange each way:
-// A side (x, n0) reads global memory along z, B side (x, K0) transforms, multiplies by
+// A side (x pair, n0) reads global memory along z, B side (x pair, K0) transforms, multiplies by
 // tx[x] + ty + tz[kz] and transforms back in registers, A side writes global memory.
 template <typename R, int N>
 __global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::value)
@@ -295,7 +318,7 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   using TIN = TF<C, N, true>;
   constexpr int NT = FFTThreads<N>::value;
   constexpr int R1 = TwoFactor<N>::R1, R2 = TwoFactor<N>::R2;
-  constexpr int IA = N * R1, IB = N * R2;
+  constexpr int IA = N / 2 * R1, IB = N / 2 * R2;
   constexpr int PA = (IA + NT - 1) / NT, PB = (IB + NT - 1) / NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -309,14 +332,14 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   constexpr size_t ZS = (size_t)N * N;
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
   z_tables<R, N, Z_KIN>(tx, tz, ty, zp, y, b / zp.comps_per_k);
-  C v[PA][R2];
+  C v0[PA][R2], v1[PA][R2];
 #pragma unroll
   for (int p = 0; p < PA; ++p) {
     const int i = threadIdx.x + p * NT;
     if (IA % NT == 0 || i < IA) {
-      const int n0 = i / N, x = i - n0 * N;
+      const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
 #pragma unroll
-      for (int q = 0; q < R2; ++q) v[p][q] = g[(size_t)(n0 + R1 * q) * ZS + x];
+      for (int q = 0; q < R2; ++q) { const Pair<C> w = ld2(g + (size_t)(n0 + R1 * q) * ZS + x); v0[p][q] = w.a; v1[p][q] = w.b; }
     }
   }
   __syncthreads();  // tables
@@ -324,10 +347,11 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   for (int p = 0; p < PA; ++p) {
     const int i = threadIdx.x + p * NT;
     if (IA % NT == 0 || i < IA) {
-      const int n0 = i / N, x = i - n0 * N;
-      TFW::a_side(v[p], n0, tw);
+      const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
+      TFW::a_side(v0[p], n0, tw);
+      TFW::a_side(v1[p], n0, tw);
 #pragma unroll
-      for (int k0 = 0; k0 < R2; ++k0) s[(k0 * R1 + n0) * N + x] = v[p][k0];
+      for (int k0 = 0; k0 < R2; ++k0) st2(s + (k0 * R1 + n0) * N + x, v0[p][k0], v1[p][k0]);
     }
   }
   __syncthreads();
@@ -336,17 +360,23 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   for (int p = 0; p < PB; ++p) {
     const int i = threadIdx.x + p * NT;
     if (IB % NT == 0 || i < IB) {
-      const int k0 = i / N, x = i - k0 * N;
-      C u[R1];
+      const int k0 = i / (N / 2), x = 2 * (i - k0 * (N / 2));
+      C a0[R1], a1[R1];
 #pragma unroll
-      for (int n0 = 0; n0 < R1; ++n0) u[n0] = s[(k0 * R1 + n0) * N + x];
-      TFW::b_side(u, k0, tw);
-      const R txy = tx[x] + tyv;
+      for (int n0 = 0; n0 < R1; ++n0) { const Pair<C> w = ld2(s + (k0 * R1 + n0) * N + x); a0[n0] = w.a; a1[n0] = w.b; }
+      TFW::b_side(a0, k0, tw);
+      TFW::b_side(a1, k0, tw);
+      const R t0 = tx[x] + tyv, t1 = tx[x + 1] + tyv;
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) u[k1] = cscale(u[k1], txy + tz[k0 + R2 * k1]);
-      TIN::b_side(u, k0, tw);
+      for (int k1 = 0; k1 < R1; ++k1) {
+        const R tzk = tz[k0 + R2 * k1];
+        a0[k1] = cscale(a0[k1], t0 + tzk);
+        a1[k1] = cscale(a1[k1], t1 + tzk);
+      }
+      TIN::b_side(a0, k0, tw);
+      TIN::b_side(a1, k0, tw);
 #pragma unroll
-      for (int n0 = 0; n0 < R1; ++n0) s[(k0 * R1 + n0) * N + x] = u[n0];
+      for (int n0 = 0; n0 < R1; ++n0) st2(s + (k0 * R1 + n0) * N + x, a0[n0], a1[n0]);
     }
   }
   __syncthreads();
@@ -354,12 +384,13 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   for (int p = 0; p < PA; ++p) {
     const int i = threadIdx.x + p * NT;
     if (IA % NT == 0 || i < IA) {
-      const int n0 = i / N, x = i - n0 * N;
+      const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
 #pragma unroll
-      for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[(k0 * R1 + n0) * N + x];
-      TIN::a_side(v[p], n0, tw);
+      for (int k0 = 0; k0 < R2; ++k0) { const Pair<C> w = ld2(s + (k0 * R1 + n0) * N + x); v0[p][k0] = w.a; v1[p][k0] = w.b; }
+      TIN::a_side(v0[p], n0, tw);
+      TIN::a_side(v1[p], n0, tw);
 #pragma unroll
-      for (int n1 = 0; n1 < R2; ++n1) g[(size_t)(n0 + R1 * n1) * ZS + x] = v[p][n1];
+      for (int n1 = 0; n1 < R2; ++n1) st2(g + (size_t)(n0 + R1 * n1) * ZS + x, v0[p][n1], v1[p][n1]);
     }
   }
 }
@@ -569,7 +600,7 @@ k_density(const typename CT<R>::type* __restrict__ psi, size_t N3, int nkb, int 
   for (int kc = kb0; kc < kb1; kc += CH) {
     R p[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     const int kend = min(kb1, kc + CH);
-#pragma unroll 4
+#pragma unroll 1
     for (int kb = kc; kb < kend; ++kb) {
       const Pair<typename CT<R>::type> u = ld2(psi + (size_t)(2 * kb) * N3 + r);
       const Pair<typename CT<R>::type> d = ld2(psi + (size_t)(2 * kb + 1) * N3 + r);
@@ -805,14 +836,19 @@ __device__ double block_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
-// out2[band] = sum over npts of conj(a) b (complex, double accumulation), one CTA per band.
+// out2[band] = sum over npts of conj(a) b (complex, double accumulation) in two passes: CTA
+// (chunk, band) sums a fixed range of points, then one thread per band adds the chunks in
+// order (deterministic, and every SM busy).
+constexpr int kDotChunks = 64;
 template <typename R>
-__global__ void __launch_bounds__(256) k_band_dot(size_t npts, const typename CT<R>::type* __restrict__ a,
-                                                  const typename CT<R>::type* __restrict__ b, double* out2) {
+__global__ void __launch_bounds__(256) k_band_dot_part(size_t npts, const typename CT<R>::type* __restrict__ a,
+                                                       const typename CT<R>::type* __restrict__ b, double* part) {
   __shared__ double sh[8];
-  const size_t off = (size_t)blockIdx.x * npts;
+  const size_t off = (size_t)blockIdx.y * npts;
+  const size_t len = (npts + kDotChunks - 1) / kDotChunks;
+  const size_t lo = (size_t)blockIdx.x * len, hi = lo + len < npts ? lo + len : npts;
   double re = 0.0, im = 0.0;
-  for (size_t i = threadIdx.x; i < npts; i += 256) {
+  for (size_t i = lo + threadIdx.x; i < hi; i += 256) {
     const auto x = a[off + i], y = b[off + i];
     re += (double)x.x * y.x + (double)x.y * y.y;
     im += (double)x.x * y.y - (double)x.y * y.x;
@@ -820,16 +856,31 @@ __global__ void __launch_bounds__(256) k_band_dot(size_t npts, const typename CT
   const double tr = block_sum<256>(re, sh);
   const double ti = block_sum<256>(im, sh);
   if (threadIdx.x == 0) {
-    out2[2 * blockIdx.x] = tr;
-    out2[2 * blockIdx.x + 1] = ti;
+    const size_t o = ((size_t)blockIdx.y * kDotChunks + blockIdx.x) * 2;
+    part[o] = tr;
+    part[o + 1] = ti;
   }
 }
+__global__ void k_band_dot_sum(int nbands, const double* __restrict__ part, double* out2) {
+  const int band = blockIdx.x * blockDim.x + threadIdx.x;
+  if (band >= nbands) return;
+  double re = 0.0, im = 0.0;
+  for (int ch = 0; ch < kDotChunks; ++ch) {
+    re += part[((size_t)band * kDotChunks + ch) * 2];
+    im += part[((size_t)band * kDotChunks + ch) * 2 + 1];
+  }
+  out2[2 * band] = re;
+  out2[2 * band + 1] = im;
+}
 template <typename R>
-cudaError_t launch_band_dot(cudaStream_t st, size_t npts, int nbands, const void* a, const void* b, double* out2) {
+cudaError_t launch_band_dot(cudaStream_t st, size_t npts, int nbands, const void* a, const void* b, double* out2,
+                            double* part) {
   using C = typename CT<R>::type;
-  k_band_dot<R><<<nbands, 256, 0, st>>>(npts, (const C*)a, (const C*)b, out2);
+  k_band_dot_part<R><<<dim3(kDotChunks, nbands), 256, 0, st>>>(npts, (const C*)a, (const C*)b, part);
+  k_band_dot_sum<<<(nbands + 127) / 128, 128, 0, st>>>(nbands, part, out2);
   return cudaGetLastError();
 }
+size_t band_dot_part_doubles(int nbands) { return (size_t)nbands * kDotChunks * 2; }
 
 // out[kb] = Re sum conj(c) dc over atoms, projectors and spins.
 template <typename R>
@@ -911,15 +962,19 @@ cudaError_t launch_xc_torque(cudaStream_t st, size_t N3, const double* rho, cons
 }
 
 // Field integrals (without dV): [0] v_loc n, [1] v_H n, [2] e_xc, [3..5] m, [6] n, [7] B.m,
-// [8] <rho_v, V_v^xc>, [9] count of non-finite rho values.
-__global__ void __launch_bounds__(1024)
-k_field_sums(size_t N3, const double* __restrict__ rho, const double* __restrict__ vloc, const double* __restrict__ vH,
-             const double* __restrict__ exc, const double* __restrict__ vxc4, double Bx, double By, double Bz,
-             double* out) {
-  __shared__ double sh[32];
+// [8] <rho_v, V_v^xc>, [9] count of non-finite rho values.  Two passes: each of kFieldBlocks
+// CTAs sums a fixed range of points, then one CTA adds the block partials in order.
+constexpr int kFieldBlocks = 304;
+__global__ void __launch_bounds__(256)
+k_field_sums_part(size_t N3, const double* __restrict__ rho, const double* __restrict__ vloc, const double* __restrict__ vH,
+                  const double* __restrict__ exc, const double* __restrict__ vxc4, double Bx, double By, double Bz,
+                  double* part) {
+  __shared__ double sh[8];
   double acc[10];
   for (int i = 0; i < 10; ++i) acc[i] = 0.0;
-  for (size_t r = threadIdx.x; r < N3; r += 1024) {
+  const size_t len = (N3 + kFieldBlocks - 1) / kFieldBlocks;
+  const size_t lo = (size_t)blockIdx.x * len, hi = lo + len < N3 ? lo + len : N3;
+  for (size_t r = lo + threadIdx.x; r < hi; r += 256) {
     const double r0 = rho[r], r1 = rho[N3 + r], r2 = rho[2 * N3 + r], r3 = rho[3 * N3 + r];
     const double n = r0 + r1, mx = 2.0 * r2, my = -2.0 * r3, mz = r0 - r1;
     acc[0] += vloc[r] * n;
@@ -932,15 +987,25 @@ k_field_sums(size_t N3, const double* __restrict__ rho, const double* __restrict
     acc[9] += (isfinite(r0) && isfinite(r1) && isfinite(r2) && isfinite(r3)) ? 0.0 : 1.0;
   }
   for (int i = 0; i < 10; ++i) {
-    const double t = block_sum<1024>(acc[i], sh);
-    if (threadIdx.x == 0) out[i] = t;
+    const double t = block_sum<256>(acc[i], sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * 10 + i] = t;
   }
 }
+__global__ void k_field_sums_total(const double* __restrict__ part, double* out) {
+  const int i = threadIdx.x;
+  if (i >= 10) return;
+  double s = 0.0;
+  for (int b = 0; b < kFieldBlocks; ++b) s += part[(size_t)b * 10 + i];
+  out[i] = s;
+}
 cudaError_t launch_field_sums(cudaStream_t st, size_t N3, const double* rho, const double* vloc, const double* vH,
-                              const double* exc, const double* vxc4, const double* /*V*/, const double* B, double* out) {
-  k_field_sums<<<1, 1024, 0, st>>>(N3, rho, vloc, vH, exc, vxc4, B[0], B[1], B[2], out);
+                              const double* exc, const double* vxc4, const double* /*V*/, const double* B, double* out,
+                              double* part) {
+  k_field_sums_part<<<kFieldBlocks, 256, 0, st>>>(N3, rho, vloc, vH, exc, vxc4, B[0], B[1], B[2], part);
+  k_field_sums_total<<<1, 32, 0, st>>>(part, out);
   return cudaGetLastError();
 }
+size_t field_sums_part_doubles() { return (size_t)kFieldBlocks * 10; }
 
 __global__ void __launch_bounds__(1024) k_max_abs_diff(size_t n, const double* a, const double* b, double* out) {
   __shared__ double sh[32];
@@ -1048,7 +1113,7 @@ cudaError_t launch_atom_sums(cudaStream_t st, size_t N3, int natoms, const doubl
                                          double*);                                                                \
   template cudaError_t launch_convert_in<R>(cudaStream_t, size_t, const double2*, void*);                        \
   template cudaError_t launch_convert_out<R>(cudaStream_t, size_t, const void*, double2*);                       \
-  template cudaError_t launch_band_dot<R>(cudaStream_t, size_t, int, const void*, const void*, double*);         \
+  template cudaError_t launch_band_dot<R>(cudaStream_t, size_t, int, const void*, const void*, double*, double*); \
   template cudaError_t launch_nl_energy<R>(cudaStream_t, int, int, const void*, const void*, double*);          \
   template cudaError_t launch_soc_torque<R>(cudaStream_t, int, int, int, const void*, const double2*, double*);  \
   template cudaError_t launch_proj_gather_mom<R>(cudaStream_t, int, const void*, int, const ProjTables<R>&,      \

@@ -391,3 +391,25 @@ def test_crank_nicolson_step_matches_oracle(lib, precision, tol):
         assert r["E"] <= (1e-8 * max(1, s_) if precision == 0 else 1e-4)
         assert r["norms"] <= (1e-12 if precision == 0 else 1e-5)
     assert rel(psi_g, o.psi) <= (1e-10 if precision == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pinned_host_buffers_match_pageable(lib, precision):
+    """set_states / get_states from page-locked host memory (read and written by the conversion
+    kernels through the mapped address) give the same bits as pageable numpy arrays."""
+    import torch
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=3, nk=2, natoms=2)
+    psi0 = S.small_parity_states(wl)
+    outs = []
+    for pinned in (False, True):
+        h = _lib.TDDFT.from_workload(wl, precision=precision, e_min=-20, e_max=100)
+        h.set_fields(wl.times, wl.A, wl.B)
+        src = torch.from_numpy(psi0.copy()).pin_memory() if pinned else psi0.copy()
+        h.set_states(src.numpy() if pinned else src, 0.0)
+        h.step(1)
+        dst = torch.empty(psi0.shape, dtype=torch.complex128).pin_memory() if pinned else None
+        got = h.get_states(dst.numpy() if pinned else None)
+        outs.append(np.array(got))
+        h.close()
+    assert np.array_equal(outs[0], outs[1])
