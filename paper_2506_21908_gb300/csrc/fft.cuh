@@ -284,7 +284,7 @@ template <typename C, bool INV> struct SmallDFT<C, 6, INV> {
 
 template <int N> struct TwoFactor { static constexpr bool ok = false; };
 template <> struct TwoFactor<16> { static constexpr bool ok = true; static constexpr int R1 = 4, R2 = 4; };
-template <> struct TwoFactor<24> { static constexpr bool ok = true; static constexpr int R1 = 6, R2 = 4; };
+template <> struct TwoFactor<24> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 3; };
 template <> struct TwoFactor<32> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 4; };
 template <> struct TwoFactor<48> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 6; };
 template <> struct TwoFactor<64> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 8; };

@@ -109,15 +109,14 @@ k_fft_z(typename CT<R>::type* __restrict__ data, const typename CT<R>::type* __r
 
 // ---------------------------------------------------------------- two-factor passes (N = R1 R2)
 //
-// Each thread carries two neighbouring work items (adjacent n0, K0 or x), so that every global
-// and shared-memory access moves two complex values at once (16 bytes in FP32).  Row pitch of
-// the xy plane: congruent to 8 modulo 16 elements.  The in-row exchange stores E[K0][n0] at
-// column K0 R1 + (n0 + 2 floor(K0 / 2)) mod R1: the even rotation keeps the pairs (n0, n0 + 1)
-// adjacent, and with this pitch the A-side writes, the B-side reads and writes and the column
-// accesses of the y and z transforms are all free of bank conflicts at n = 64.
+// Row pitch of the xy plane: congruent to 8 modulo 16 elements, so that the in-row exchange
+// (8 lanes per row, rotated columns) and the column accesses are both free of bank conflicts.
 template <int N> struct TFPitch { static constexpr int value = (N % 16 == 8) ? N : (N % 16 == 0 ? N + 8 : N + 1); };
-template <int R1> __device__ __forceinline__ int tf_col(int k0, int n0) { return k0 * R1 + (n0 + 2 * (k0 >> 1)) % R1; }
 
+// xy transform of one z-plane with one shared-memory exchange per axis: the x transform's A side
+// reads global memory directly, the y transform's B side writes it directly (forward); the
+// inverse runs the steps in the opposite order.  Column of the in-row exchange: K0 R1 + (n0 +
+// K0) mod R1 (a rotation, so that the 8 lanes of a row hit distinct banks on both sides).
 template <typename R, int N, bool INV>
 __global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::value)
 k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const typename CT<R>::type* __restrict__ twg) {
@@ -125,11 +124,9 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
   using T = TF<C, N, INV>;
   constexpr int NT = FFTThreads<N>::value;
   constexpr int R1 = TwoFactor<N>::R1, R2 = TwoFactor<N>::R2;
-  static_assert(R1 % 2 == 0 && R2 % 2 == 0 && N % 2 == 0, "paired two-factor pass needs even factors");
   constexpr int RS = TFPitch<N>::value;
-  constexpr int AX = N * R1 / 2, BX = N * R2 / 2;  // item pairs of the x transform (rows y)
-  constexpr int AY = N / 2 * R1, BY = N / 2 * R2;  // item pairs of the y transform (columns x)
-  constexpr int PAX = (AX + NT - 1) / NT, PBX = (BX + NT - 1) / NT, PAY = (AY + NT - 1) / NT, PBY = (BY + NT - 1) / NT;
+  constexpr int IA = N * R1, IB = N * R2;                 // A / B items of one axis
+  constexpr int PA = (IA + NT - 1) / NT, PB = (IB + NT - 1) / NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s = tw + N;
@@ -138,177 +135,157 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
   C* o = dst + base;
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
   __syncthreads();
+  C v[PA][R2];
+  C u[PB][R1];
   if (!INV) {
-    // x, A side from global: pair (y, n0, n0 + 1)
+    // x, A side: item (y, n0), n0 fastest
 #pragma unroll
-    for (int p = 0; p < PAX; ++p) {
+    for (int p = 0; p < PA; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (AX % NT == 0 || i < AX) {
-        const int y = i / (R1 / 2), n0 = 2 * (i - y * (R1 / 2));
-        C v0[R2], v1[R2];
+      if (IA % NT == 0 || i < IA) {
+        const int y = i / R1, n0 = i - y * R1;
 #pragma unroll
-        for (int q = 0; q < R2; ++q) { const Pair<C> w = ld2(g + y * N + n0 + R1 * q); v0[q] = w.a; v1[q] = w.b; }
-        T::a_side(v0, n0, tw);
-        T::a_side(v1, n0 + 1, tw);
+        for (int q = 0; q < R2; ++q) v[p][q] = g[y * N + n0 + R1 * q];
+        T::a_side(v[p], n0, tw);
 #pragma unroll
-        for (int k0 = 0; k0 < R2; ++k0) st2(s + y * RS + tf_col<R1>(k0, n0), v0[k0], v1[k0]);
+        for (int k0 = 0; k0 < R2; ++k0) s[y * RS + k0 * R1 + (n0 + k0) % R1] = v[p][k0];
       }
     }
     __syncthreads();
-    // x, B side: pair (y, K0, K0 + 1), K0 even
-    C u0[PBX][R1], u1[PBX][R1];
+    // x, B side: item (y, K0)
 #pragma unroll
-    for (int p = 0; p < PBX; ++p) {
+    for (int p = 0; p < PB; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (BX % NT == 0 || i < BX) {
-        const int y = i / (R2 / 2), k0 = 2 * (i - y * (R2 / 2));
+      if (IB % NT == 0 || i < IB) {
+        const int y = i / R2, k0 = i - y * R2;
 #pragma unroll
-        for (int n0 = 0; n0 < R1; n0 += 2) {
-          const Pair<C> a = ld2(s + y * RS + tf_col<R1>(k0, n0)), b = ld2(s + y * RS + tf_col<R1>(k0 + 1, n0));
-          u0[p][n0] = a.a; u0[p][n0 + 1] = a.b; u1[p][n0] = b.a; u1[p][n0 + 1] = b.b;
-        }
+        for (int n0 = 0; n0 < R1; ++n0) u[p][n0] = s[y * RS + k0 * R1 + (n0 + k0) % R1];
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int p = 0; p < PBX; ++p) {
+    for (int p = 0; p < PB; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (BX % NT == 0 || i < BX) {
-        const int y = i / (R2 / 2), k0 = 2 * (i - y * (R2 / 2));
-        T::b_side(u0[p], k0, tw);
-        T::b_side(u1[p], k0 + 1, tw);
+      if (IB % NT == 0 || i < IB) {
+        const int y = i / R2, k0 = i - y * R2;
+        T::b_side(u[p], k0, tw);
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) st2(s + y * RS + k0 + R2 * k1, u0[p][k1], u1[p][k1]);
+        for (int k1 = 0; k1 < R1; ++k1) s[y * RS + k0 + R2 * k1] = u[p][k1];
       }
     }
     __syncthreads();
-    // y, A side: pair (x, x + 1; n0)
-    C w0[PAY][R2], w1[PAY][R2];
+    // y, A side: item (x, n0), x fastest
 #pragma unroll
-    for (int p = 0; p < PAY; ++p) {
+    for (int p = 0; p < PA; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (AY % NT == 0 || i < AY) {
-        const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
+      if (IA % NT == 0 || i < IA) {
+        const int n0 = i / N, x = i - n0 * N;
 #pragma unroll
-        for (int q = 0; q < R2; ++q) { const Pair<C> w = ld2(s + (n0 + R1 * q) * RS + x); w0[p][q] = w.a; w1[p][q] = w.b; }
-        T::a_side(w0[p], n0, tw);
-        T::a_side(w1[p], n0, tw);
+        for (int q = 0; q < R2; ++q) v[p][q] = s[(n0 + R1 * q) * RS + x];
+        T::a_side(v[p], n0, tw);
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int p = 0; p < PAY; ++p) {
+    for (int p = 0; p < PA; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (AY % NT == 0 || i < AY) {
-        const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
+      if (IA % NT == 0 || i < IA) {
+        const int n0 = i / N, x = i - n0 * N;
 #pragma unroll
-        for (int k0 = 0; k0 < R2; ++k0) st2(s + (k0 * R1 + n0) * RS + x, w0[p][k0], w1[p][k0]);
+        for (int k0 = 0; k0 < R2; ++k0) s[(k0 * R1 + n0) * RS + x] = v[p][k0];
       }
     }
     __syncthreads();
-    // y, B side to global: pair (x, x + 1; K0)
+    // y, B side: item (x, K0) -> global
 #pragma unroll
-    for (int p = 0; p < PBY; ++p) {
+    for (int p = 0; p < PB; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (BY % NT == 0 || i < BY) {
-        const int k0 = i / (N / 2), x = 2 * (i - k0 * (N / 2));
-        C a0[R1], a1[R1];
+      if (IB % NT == 0 || i < IB) {
+        const int k0 = i / N, x = i - k0 * N;
 #pragma unroll
-        for (int n0 = 0; n0 < R1; ++n0) { const Pair<C> w = ld2(s + (k0 * R1 + n0) * RS + x); a0[n0] = w.a; a1[n0] = w.b; }
-        T::b_side(a0, k0, tw);
-        T::b_side(a1, k0, tw);
+        for (int n0 = 0; n0 < R1; ++n0) u[p][n0] = s[(k0 * R1 + n0) * RS + x];
+        T::b_side(u[p], k0, tw);
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) st2(o + (k0 + R2 * k1) * N + x, a0[k1], a1[k1]);
+        for (int k1 = 0; k1 < R1; ++k1) o[(k0 + R2 * k1) * N + x] = u[p][k1];
       }
     }
   } else {
-    // y, B side from global: pair (x, x + 1; K0)
+    // y, B side from global: item (x, K0)
 #pragma unroll
-    for (int p = 0; p < PBY; ++p) {
+    for (int p = 0; p < PB; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (BY % NT == 0 || i < BY) {
-        const int k0 = i / (N / 2), x = 2 * (i - k0 * (N / 2));
-        C a0[R1], a1[R1];
+      if (IB % NT == 0 || i < IB) {
+        const int k0 = i / N, x = i - k0 * N;
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) { const Pair<C> w = ld2(g + (k0 + R2 * k1) * N + x); a0[k1] = w.a; a1[k1] = w.b; }
-        T::b_side(a0, k0, tw);
-        T::b_side(a1, k0, tw);
+        for (int k1 = 0; k1 < R1; ++k1) u[p][k1] = g[(k0 + R2 * k1) * N + x];
+        T::b_side(u[p], k0, tw);
 #pragma unroll
-        for (int n0 = 0; n0 < R1; ++n0) st2(s + (k0 * R1 + n0) * RS + x, a0[n0], a1[n0]);
+        for (int n0 = 0; n0 < R1; ++n0) s[(k0 * R1 + n0) * RS + x] = u[p][n0];
       }
     }
     __syncthreads();
-    // y, A side: pair (x, x + 1; n0)
-    C w0[PAY][R2], w1[PAY][R2];
+    // y, A side: item (x, n0)
 #pragma unroll
-    for (int p = 0; p < PAY; ++p) {
+    for (int p = 0; p < PA; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (AY % NT == 0 || i < AY) {
-        const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
+      if (IA % NT == 0 || i < IA) {
+        const int n0 = i / N, x = i - n0 * N;
 #pragma unroll
-        for (int k0 = 0; k0 < R2; ++k0) { const Pair<C> w = ld2(s + (k0 * R1 + n0) * RS + x); w0[p][k0] = w.a; w1[p][k0] = w.b; }
-        T::a_side(w0[p], n0, tw);
-        T::a_side(w1[p], n0, tw);
+        for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[(k0 * R1 + n0) * RS + x];
+        T::a_side(v[p], n0, tw);
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int p = 0; p < PAY; ++p) {
+    for (int p = 0; p < PA; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (AY % NT == 0 || i < AY) {
-        const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
+      if (IA % NT == 0 || i < IA) {
+        const int n0 = i / N, x = i - n0 * N;
 #pragma unroll
-        for (int n1 = 0; n1 < R2; ++n1) st2(s + (n0 + R1 * n1) * RS + x, w0[p][n1], w1[p][n1]);
+        for (int n1 = 0; n1 < R2; ++n1) s[(n0 + R1 * n1) * RS + x] = v[p][n1];
       }
     }
     __syncthreads();
-    // x, B side: pair (y, K0, K0 + 1)
-    C u0[PBX][R1], u1[PBX][R1];
+    // x, B side: item (y, K0)
 #pragma unroll
-    for (int p = 0; p < PBX; ++p) {
+    for (int p = 0; p < PB; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (BX % NT == 0 || i < BX) {
-        const int y = i / (R2 / 2), k0 = 2 * (i - y * (R2 / 2));
+      if (IB % NT == 0 || i < IB) {
+        const int y = i / R2, k0 = i - y * R2;
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) { const Pair<C> w = ld2(s + y * RS + k0 + R2 * k1); u0[p][k1] = w.a; u1[p][k1] = w.b; }
+        for (int k1 = 0; k1 < R1; ++k1) u[p][k1] = s[y * RS + k0 + R2 * k1];
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int p = 0; p < PBX; ++p) {
+    for (int p = 0; p < PB; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (BX % NT == 0 || i < BX) {
-        const int y = i / (R2 / 2), k0 = 2 * (i - y * (R2 / 2));
-        T::b_side(u0[p], k0, tw);
-        T::b_side(u1[p], k0 + 1, tw);
+      if (IB % NT == 0 || i < IB) {
+        const int y = i / R2, k0 = i - y * R2;
+        T::b_side(u[p], k0, tw);
 #pragma unroll
-        for (int n0 = 0; n0 < R1; n0 += 2) {
-          st2(s + y * RS + tf_col<R1>(k0, n0), u0[p][n0], u0[p][n0 + 1]);
-          st2(s + y * RS + tf_col<R1>(k0 + 1, n0), u1[p][n0], u1[p][n0 + 1]);
-        }
+        for (int n0 = 0; n0 < R1; ++n0) s[y * RS + k0 * R1 + (n0 + k0) % R1] = u[p][n0];
       }
     }
     __syncthreads();
-    // x, A side to global: pair (y, n0, n0 + 1)
+    // x, A side -> global: item (y, n0)
 #pragma unroll
-    for (int p = 0; p < PAX; ++p) {
+    for (int p = 0; p < PA; ++p) {
       const int i = threadIdx.x + p * NT;
-      if (AX % NT == 0 || i < AX) {
-        const int y = i / (R1 / 2), n0 = 2 * (i - y * (R1 / 2));
-        C v0[R2], v1[R2];
+      if (IA % NT == 0 || i < IA) {
+        const int y = i / R1, n0 = i - y * R1;
 #pragma unroll
-        for (int k0 = 0; k0 < R2; ++k0) { const Pair<C> w = ld2(s + y * RS + tf_col<R1>(k0, n0)); v0[k0] = w.a; v1[k0] = w.b; }
-        T::a_side(v0, n0, tw);
-        T::a_side(v1, n0 + 1, tw);
+        for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[y * RS + k0 * R1 + (n0 + k0) % R1];
+        T::a_side(v[p], n0, tw);
 #pragma unroll
-        for (int n1 = 0; n1 < R2; ++n1) st2(o + y * N + n0 + R1 * n1, v0[n1], v1[n1]);
+        for (int n1 = 0; n1 < R2; ++n1) o[y * N + n0 + R1 * n1] = v[p][n1];
       }
     }
   }
 }
 
 // z transform + kinetic multiply + inverse z transform of one y-slab, one exchange each way:
-// A side (x pair, n0) reads global memory along z, B side (x pair, K0) transforms, multiplies by
+// A side (x, n0) reads global memory along z, B side (x, K0) transforms, multiplies by
 // tx[x] + ty + tz[kz] and transforms back in registers, A side writes global memory.
 template <typename R, int N>
 __global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::value)
@@ -318,7 +295,7 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   using TIN = TF<C, N, true>;
   constexpr int NT = FFTThreads<N>::value;
   constexpr int R1 = TwoFactor<N>::R1, R2 = TwoFactor<N>::R2;
-  constexpr int IA = N / 2 * R1, IB = N / 2 * R2;
+  constexpr int IA = N * R1, IB = N * R2;
   constexpr int PA = (IA + NT - 1) / NT, PB = (IB + NT - 1) / NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -332,14 +309,14 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   constexpr size_t ZS = (size_t)N * N;
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
   z_tables<R, N, Z_KIN>(tx, tz, ty, zp, y, b / zp.comps_per_k);
-  C v0[PA][R2], v1[PA][R2];
+  C v[PA][R2];
 #pragma unroll
   for (int p = 0; p < PA; ++p) {
     const int i = threadIdx.x + p * NT;
     if (IA % NT == 0 || i < IA) {
-      const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
+      const int n0 = i / N, x = i - n0 * N;
 #pragma unroll
-      for (int q = 0; q < R2; ++q) { const Pair<C> w = ld2(g + (size_t)(n0 + R1 * q) * ZS + x); v0[p][q] = w.a; v1[p][q] = w.b; }
+      for (int q = 0; q < R2; ++q) v[p][q] = g[(size_t)(n0 + R1 * q) * ZS + x];
     }
   }
   __syncthreads();  // tables
@@ -347,11 +324,10 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   for (int p = 0; p < PA; ++p) {
     const int i = threadIdx.x + p * NT;
     if (IA % NT == 0 || i < IA) {
-      const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
-      TFW::a_side(v0[p], n0, tw);
-      TFW::a_side(v1[p], n0, tw);
+      const int n0 = i / N, x = i - n0 * N;
+      TFW::a_side(v[p], n0, tw);
 #pragma unroll
-      for (int k0 = 0; k0 < R2; ++k0) st2(s + (k0 * R1 + n0) * N + x, v0[p][k0], v1[p][k0]);
+      for (int k0 = 0; k0 < R2; ++k0) s[(k0 * R1 + n0) * N + x] = v[p][k0];
     }
   }
   __syncthreads();
@@ -360,23 +336,17 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   for (int p = 0; p < PB; ++p) {
     const int i = threadIdx.x + p * NT;
     if (IB % NT == 0 || i < IB) {
-      const int k0 = i / (N / 2), x = 2 * (i - k0 * (N / 2));
-      C a0[R1], a1[R1];
+      const int k0 = i / N, x = i - k0 * N;
+      C u[R1];
 #pragma unroll
-      for (int n0 = 0; n0 < R1; ++n0) { const Pair<C> w = ld2(s + (k0 * R1 + n0) * N + x); a0[n0] = w.a; a1[n0] = w.b; }
-      TFW::b_side(a0, k0, tw);
-      TFW::b_side(a1, k0, tw);
-      const R t0 = tx[x] + tyv, t1 = tx[x + 1] + tyv;
+      for (int n0 = 0; n0 < R1; ++n0) u[n0] = s[(k0 * R1 + n0) * N + x];
+      TFW::b_side(u, k0, tw);
+      const R txy = tx[x] + tyv;
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) {
-        const R tzk = tz[k0 + R2 * k1];
-        a0[k1] = cscale(a0[k1], t0 + tzk);
-        a1[k1] = cscale(a1[k1], t1 + tzk);
-      }
-      TIN::b_side(a0, k0, tw);
-      TIN::b_side(a1, k0, tw);
+      for (int k1 = 0; k1 < R1; ++k1) u[k1] = cscale(u[k1], txy + tz[k0 + R2 * k1]);
+      TIN::b_side(u, k0, tw);
 #pragma unroll
-      for (int n0 = 0; n0 < R1; ++n0) st2(s + (k0 * R1 + n0) * N + x, a0[n0], a1[n0]);
+      for (int n0 = 0; n0 < R1; ++n0) s[(k0 * R1 + n0) * N + x] = u[n0];
     }
   }
   __syncthreads();
@@ -384,13 +354,12 @@ k_fft_z2_kin(typename CT<R>::type* __restrict__ data, const typename CT<R>::type
   for (int p = 0; p < PA; ++p) {
     const int i = threadIdx.x + p * NT;
     if (IA % NT == 0 || i < IA) {
-      const int n0 = i / (N / 2), x = 2 * (i - n0 * (N / 2));
+      const int n0 = i / N, x = i - n0 * N;
 #pragma unroll
-      for (int k0 = 0; k0 < R2; ++k0) { const Pair<C> w = ld2(s + (k0 * R1 + n0) * N + x); v0[p][k0] = w.a; v1[p][k0] = w.b; }
-      TIN::a_side(v0[p], n0, tw);
-      TIN::a_side(v1[p], n0, tw);
+      for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[(k0 * R1 + n0) * N + x];
+      TIN::a_side(v[p], n0, tw);
 #pragma unroll
-      for (int n1 = 0; n1 < R2; ++n1) st2(g + (size_t)(n0 + R1 * n1) * ZS + x, v0[p][n1], v1[p][n1]);
+      for (int n1 = 0; n1 < R2; ++n1) g[(size_t)(n0 + R1 * n1) * ZS + x] = v[p][n1];
     }
   }
 }
