@@ -433,8 +433,11 @@ cudaError_t launch_fft_z(cudaStream_t st, int N, void* data, int nbatch, const v
 // One CTA per (atom, spinor): c[p][sigma] = sum_e beta_p exp(+i s.d) psi_sigma(r_e) dV, then D c.
 // MOM < 0: projections c and D c.  MOM = a in {0, 1, 2}: moment projections
 // sum_e d_a beta_p exp(+i s.d) psi(r_e) dV only (written to c_out).
+template <typename R> struct GatherMinBlocks { static constexpr int value = 1; };
+template <> struct GatherMinBlocks<float> { static constexpr int value = 3; };
+
 template <typename R, int NLM, int MOM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, GatherMinBlocks<R>::value)
 k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTables<R> pt, R dV, EpiParams ep,
               typename CT<R>::type* __restrict__ c_out, typename CT<R>::type* __restrict__ dc_out) {
   using C = typename CT<R>::type;
@@ -451,14 +454,39 @@ k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTable
   const int e0 = pt.g_ptr[a], e1 = pt.g_ptr[a + 1];
   R nl[4];
   load_row<R, 4>(pt.nrm + (size_t)a * 4, nl);
-  for (int e = e0 + threadIdx.x; e < e1; e += 256) {
-    const int r = pt.g_idx[e];
-    R t[4], bt[NLM];
-    load_row<R, 4>(pt.g_row + (size_t)e * 4, t);
+  // Software pipeline over this thread's entries e, e + 256, ...: the grid index of the entry
+  // after next, and the table row and psi values of the next entry, are requested before the
+  // current entry is processed, so two dependent load chains are in flight at a time.
+  const C zc = cmake<C>((R)0, (R)0);
+  int e = e0 + threadIdx.x;
+  int r1 = (e + 256 < e1) ? pt.g_idx[e + 256] : 0;  // index of the next entry
+  R tc[4] = {(R)0, (R)0, (R)0, (R)0};
+  C uc = zc, dc = zc;
+  if (e < e1) {
+    const int r0 = pt.g_idx[e];
+    load_row<R, 4>(pt.g_row + (size_t)e * 4, tc);
+    uc = up[r0];
+    dc = dn[r0];
+  }
+  for (; e < e1; e += 256) {
+    R tn[4] = {(R)0, (R)0, (R)0, (R)0};
+    C un = zc, dn_ = zc;
+    int r2 = 0;
+    if (e + 256 < e1) {
+      load_row<R, 4>(pt.g_row + (size_t)(e + 256) * 4, tn);
+      un = up[r1];
+      dn_ = dn[r1];
+      if (e + 512 < e1) r2 = pt.g_idx[e + 512];
+    }
+    R t[4] = {tc[0], tc[1], tc[2], tc[3]}, bt[NLM];
     beta_values<R, NLM>(t[0], t[1], t[2], t[3], nl, pt.yc, bt);
     R sn, cs;
     sincos_r<R>(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);
-    const C u = up[r], d = dn[r];
+    const C u = uc, d = dc;
+    for (int i = 0; i < 4; ++i) tc[i] = tn[i];
+    uc = un;
+    dc = dn_;
+    r1 = r2;
     R pux = u.x * cs - u.y * sn, puy = u.x * sn + u.y * cs;  // u exp(+i arg)
     R pdx = d.x * cs - d.y * sn, pdy = d.x * sn + d.y * cs;
     if (MOM >= 0) {

@@ -11,7 +11,7 @@ from tests._systems import parity_system, uniform_gas
 
 
 def test_hamiltonian_hermitian_with_soc_kpoints_and_fields():
-    """<phi|H psi> = <H phi|psi> on random spinors (the benchmark spec form <phi|H psi> = <psi|H phi>*)."""
+    """<phi|H psi> = <H phi|psi> on random spinors (equivalently <phi|H psi> = <psi|H phi>*)."""
     wl, s, psi = parity_system(n=12, nstates=3, nk=2)
     rho = s.rho_v(psi)
     A, B = np.array([0.05, -0.1, 0.2]), np.array([0.3, 0.1, -0.2])

@@ -79,7 +79,7 @@ def test_noncollinear_xc_zero_torque_and_collinear_limit():
 
 
 def test_rho_v_and_magnetisation_identities():
-    """m = Tr(sigma rho_s), n = Tr rho_s (Eqs. rho1-rho3) and the L553 initialisation formula
+    """m = Tr(sigma rho_s), n = Tr rho_s (Eqs. rho1-rho3) and the initial-density formula of Algorithm 1
     rho_v = n {(1+m_z)/2, (1-m_z)/2, m_x/2, -m_y/2} with m = M/n round-trips to (n, M)."""
     rng = np.random.default_rng(1)
     psi = rng.normal(size=(1, 3, 2, 4, 4, 4)) + 1j * rng.normal(size=(1, 3, 2, 4, 4, 4))
