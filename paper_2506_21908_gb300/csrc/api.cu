@@ -183,6 +183,11 @@ struct tddft_ctx {
   bool use_cluster = false;  // one-kernel kinetic term on 16-CTA clusters (FP32, n = 32, 48, 64)
   // device memory
   cudaStream_t st = nullptr;
+  // second stream for the projector gather, which runs beside the FFT passes of the same term
+  // (it only reads T_k; fork and join events order it after the previous epilogue and before
+  // the next one)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<void*> allocs;
   void *psi = nullptr, *phi = nullptr, *pred = nullptr, *Ta = nullptr, *Tb = nullptr, *tmp = nullptr;
   void *cbuf = nullptr, *dcbuf = nullptr, *tw = nullptr;
@@ -262,6 +267,9 @@ struct tddft_ctx {
   }
   // Launch wrapper: counts launches and records CUDA events around them when profiling.
   template <class F> tddft_status launch(int cls, const char* what, F&& f, double bytes = 0.0) {
+    return launch_on(st, cls, what, f, bytes);
+  }
+  template <class F> tddft_status launch_on(cudaStream_t s, int cls, const char* what, F&& f, double bytes = 0.0) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (prof) {
       if (ev_used == ev_pool.size()) {
@@ -273,11 +281,11 @@ struct tddft_ctx {
       a = ev_pool[ev_used].first;
       b = ev_pool[ev_used].second;
       ++ev_used;
-      cudaEventRecord(a, st);
+      cudaEventRecord(a, s);
     }
     cudaError_t e = f();
     if (prof) {
-      cudaEventRecord(b, st);
+      cudaEventRecord(b, s);
       ev[cls].push_back({a, b});
       alg_bytes[cls] += bytes;
     }
@@ -557,8 +565,9 @@ template <typename R> tddft_status kinetic(tddft_ctx* c, const void* in, void* o
   return c->launch(KC_FFT_XY, "ifft xy", [&] { return launch_fft_xy<R>(c->st, c->N, out, out, nbatch, c->tw, true); }, by);
 }
 
-template <typename R> tddft_status gather(tddft_ctx* c, const void* in, const double A[3]) {
+template <typename R> tddft_status gather(tddft_ctx* c, const void* in, const double A[3], cudaStream_t sg = nullptr) {
   if (c->natoms == 0) return TDDFT_OK;
+  if (!sg) sg = c->st;
   EpiParams ep{};
   ep.nstates = c->nb;
   fill_shifts(c, A, ep.shift);
@@ -566,15 +575,32 @@ template <typename R> tddft_status gather(tddft_ctx* c, const void* in, const do
   const double by = (double)c->n_entries * c->nkb * 2 * 2 * sizeof(R);  // psi at the sphere points
   if (c->prec != TDDFT_FP64 && c->proj_mode >= TDDFT_PROJ_TF32) {
     ProjTables<float> pf = c->tables<float>();
-    return c->launch(KC_PROJ, "projector gather (tensor cores)", [&] {
-      return launch_proj_gather_tc(c->st, c->N, in, c->nk, c->nb, pf, c->dV, ep,
+    return c->launch_on(sg, KC_PROJ, "projector gather (tensor cores)", [&] {
+      return launch_proj_gather_tc(sg, c->N, in, c->nk, c->nb, pf, c->dV, ep,
                                    c->proj_mode == TDDFT_PROJ_TF32X3 ? 1 : 0, c->tc_part, c->cbuf, c->dcbuf,
                                    c->tc_err);
     }, by);
   }
-  return c->launch(KC_PROJ, "projector gather", [&] {
-    return launch_proj_gather<R>(c->st, c->N, in, c->nkb, pt, c->dV, ep, c->cbuf, c->dcbuf);
+  return c->launch_on(sg, KC_PROJ, "projector gather", [&] {
+    return launch_proj_gather<R>(sg, c->N, in, c->nkb, pt, c->dV, ep, c->cbuf, c->dcbuf);
   }, by);
+}
+
+// The kinetic passes and the projector gather of one term: with a second stream the gather runs
+// beside the FFT passes (fork after the previous epilogue, join before the next one).
+template <typename R> tddft_status kinetic_and_gather(tddft_ctx* c, const void* cur, const double A[3]) {
+  tddft_status s;
+  if (!c->side || c->natoms == 0) {
+    if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
+    return gather<R>(c, cur, A);
+  }
+  if ((s = c->cuda(cudaEventRecord(c->ev_fork, c->st), "fork")) ||
+      (s = c->cuda(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork wait")))
+    return s;
+  if ((s = gather<R>(c, cur, A, c->side))) return s;
+  if ((s = c->cuda(cudaEventRecord(c->ev_join, c->side), "join"))) return s;
+  if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
+  return c->cuda(cudaStreamWaitEvent(c->st, c->ev_join, 0), "join wait");
 }
 
 // Fused form of one Chebyshev series: per term a projector gather of T_k, the z pass with the
@@ -679,8 +705,7 @@ tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double
     return cheb_series_fused<R>(c, in, Vr, A, acc1, cf1, K1, acc2, cf2, K2, ep, slots);
   int done1 = 0, done2 = 0;
   for (int k = 0; k < K; ++k) {
-    if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
-    if ((s = gather<R>(c, cur, A))) return s;
+    if ((s = kinetic_and_gather<R>(c, cur, A))) return s;
     void* out;
     if (slots) out = slots[k + 1];
     else if (k == 0) out = c->Ta;
@@ -719,8 +744,7 @@ tddft_status taylor_series(tddft_ctx* c, const void* in, bool vcur, const double
   const R* Vr = vsel<R>(c, vcur);
   const void* cur = in;
   for (int k = 1; k <= K; ++k) {
-    if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
-    if ((s = gather<R>(c, cur, A))) return s;
+    if ((s = kinetic_and_gather<R>(c, cur, A))) return s;
     void* out = (cur == c->Ta) ? c->Tb : c->Ta;
     ep.a1[0] = 0.0;
     ep.a1[1] = -tau / k;
@@ -1505,6 +1529,17 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   if ((c->emin_user != 0.0 || c->emax_user != 0.0) && !(c->emax_user > c->emin_user))
     return c->fail(TDDFT_ERR_ARG, "e_max must exceed e_min");
   c->xc = pr->xc ? 1 : 0;
+  {
+    // TDDFT_NO_OVERLAP=1 keeps the gather on the main stream (same work, serial order)
+    const char* e = std::getenv("TDDFT_NO_OVERLAP");
+    if (!(e && e[0] == '1') &&
+        (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      c->side = nullptr;
+    }
+  }
   c->spin_mode = pr->spin_mode;
   if (c->spin_mode < TDDFT_SPIN_NONCOLLINEAR || c->spin_mode > TDDFT_SPIN_UNPOLARISED)
     return c->fail(TDDFT_ERR_ARG, "spin_mode must be 0 (non-collinear), 1 (collinear) or 2 (unpolarised)");
@@ -1886,6 +1921,12 @@ const char* tddft_last_error(tddft_handle h) {
 void tddft_destroy(tddft_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   free_all(h);
   delete h;
 }

@@ -844,11 +844,23 @@ __global__ void __launch_bounds__(256) k_band_dot_part(size_t npts, const typena
   const size_t off = (size_t)blockIdx.y * npts;
   const size_t len = (npts + kDotChunks - 1) / kDotChunks;
   const size_t lo = (size_t)blockIdx.x * len, hi = lo + len < npts ? lo + len : npts;
+  // groups of kDotGroup products are summed in R before entering the FP64 sum (FP64 arithmetic
+  // is scarce on this part; in FP64 mode R is double and nothing changes)
+  constexpr int kDotGroup = 8;
   double re = 0.0, im = 0.0;
-  for (size_t i = lo + threadIdx.x; i < hi; i += 256) {
-    const auto x = a[off + i], y = b[off + i];
-    re += (double)x.x * y.x + (double)x.y * y.y;
-    im += (double)x.x * y.y - (double)x.y * y.x;
+  for (size_t i0 = lo + threadIdx.x; i0 < hi; i0 += (size_t)256 * kDotGroup) {
+    R gr = (R)0, gi = (R)0;
+#pragma unroll
+    for (int j = 0; j < kDotGroup; ++j) {
+      const size_t i = i0 + (size_t)j * 256;
+      if (i < hi) {
+        const auto x = a[off + i], y = b[off + i];
+        gr += x.x * y.x + x.y * y.y;
+        gi += x.x * y.y - x.y * y.x;
+      }
+    }
+    re += (double)gr;
+    im += (double)gi;
   }
   const double tr = block_sum<256>(re, sh);
   const double ti = block_sum<256>(im, sh);
