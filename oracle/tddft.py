@@ -444,14 +444,23 @@ class System:
 
     # --------------------------------------------------------- spectral bound
     def nl_norm_bound(self):
-        """sum over atoms of max|eig D_a| times a Gershgorin bound of the projector Gram matrix."""
-        tot = 0.0
+        """Upper bound on ||V_NL|| = ||P D P^dagger|| <= max_a ||D_a|| ||P^dagger P||, with ||P^dagger P||
+        bounded by the largest Gershgorin row sum of the Gram matrix of all projectors: within an
+        atom the exact overlaps (the phases cancel), between atoms sum_r |beta_ap| |beta_bq| dV."""
+        g = self.grid
+        S = np.zeros(g.N)
+        for at in self.atoms:
+            np.add.at(S, at.idx, np.abs(at.beta).sum(axis=0))
+        gmax = 0.0
+        dmax = 0.0
         for a, at in enumerate(self.atoms):
-            gram = (at.beta @ at.beta.T) * self.grid.dV
-            gmax = np.abs(gram).sum(axis=1).max() if gram.size else 0.0
-            dmax = max(np.abs(np.linalg.eigvalsh(b)).max() for b in self.blocks[a])
-            tot += dmax * gmax
-        return tot
+            own = np.abs(at.beta).sum(axis=0)
+            gram = (at.beta @ at.beta.T) * g.dV
+            inter = (np.abs(at.beta) * (S[at.idx] - own)[None, :]).sum(axis=1) * g.dV
+            if gram.size:
+                gmax = max(gmax, (np.abs(gram).sum(axis=1) + inter).max())
+            dmax = max(dmax, max(np.abs(np.linalg.eigvalsh(b)).max() for b in self.blocks[a]))
+        return dmax * gmax
 
     def spectral_bounds(self, V, A_list, margin=0.05):
         """Reading P2: window [E_min, E_max] for the Chebyshev expansion."""

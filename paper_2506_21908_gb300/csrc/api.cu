@@ -441,7 +441,16 @@ tddft_status build_tables(tddft_ctx* c, const tddft_projectors* pj, const int* s
   std::vector<std::vector<std::vector<cd>>> Lm[3];
   for (int al = 0; al < 3; ++al)
     for (int l = 0; l <= c->lmax; ++l) Lm[al].push_back(angular_momentum(l, al));
-  double bound = 0.0;
+  // ||V_NL|| = ||P D P^dagger|| <= max_a ||D_a|| ||P^dagger P||; ||P^dagger P|| is bounded by the
+  // largest Gershgorin row sum of the Gram matrix of all projectors: exact overlaps within an
+  // atom (the phases cancel), sum_r |beta_ap| |beta_bq| dV between atoms.
+  std::vector<double> Sabs(c->N3, 0.0);  // sum over all entries at r of |beta|
+  for (int a = 0; a < c->natoms; ++a)
+    for (int e = ht.g_ptr[a]; e < ht.g_ptr[a + 1]; ++e) {
+      const double* t = &ht.g_tab[(size_t)e * tab + 3];
+      for (int p = 0; p < nlm; ++p) Sabs[ht.g_idx[e]] += std::fabs(t[p]);
+    }
+  double dmax_all = 0.0, gmax_all = 0.0;
   for (int a = 0; a < c->natoms; ++a) {
     const int s = species[a];
     double* Da = &ht.Dmat[(size_t)a * M * M * 2];
@@ -462,21 +471,26 @@ tddft_status build_tables(tddft_ctx* c, const tddft_projectors* pj, const int* s
               Da[(row * M + col) * 2 + 1] = v.imag();
             }
     }
-    // Gershgorin bound of the projector Gram matrix of this atom
-    std::vector<double> G((size_t)nlm * nlm, 0.0);
+    // Gershgorin row sums of this atom's rows of the full Gram matrix
+    std::vector<double> G((size_t)nlm * nlm, 0.0), inter(nlm, 0.0);
     for (int e = ht.g_ptr[a]; e < ht.g_ptr[a + 1]; ++e) {
       const double* t = &ht.g_tab[(size_t)e * tab + 3];
-      for (int p = 0; p < nlm; ++p)
+      double own = 0.0;
+      for (int q = 0; q < nlm; ++q) own += std::fabs(t[q]);
+      const double other = Sabs[ht.g_idx[e]] - own;
+      for (int p = 0; p < nlm; ++p) {
         for (int q = 0; q < nlm; ++q) G[p * nlm + q] += t[p] * t[q] * c->dV;
+        inter[p] += std::fabs(t[p]) * other * c->dV;
+      }
     }
-    double gmax = 0.0;
     for (int p = 0; p < nlm; ++p) {
-      double rs = 0.0;
+      double rs = inter[p];
       for (int q = 0; q < nlm; ++q) rs += std::fabs(G[p * nlm + q]);
-      gmax = std::max(gmax, rs);
+      gmax_all = std::max(gmax_all, rs);
     }
-    bound += dmax * gmax;
+    dmax_all = std::max(dmax_all, dmax);
   }
+  const double bound = dmax_all * gmax_all;
   ht.nl_bound = bound;
   (void)pi;
   return TDDFT_OK;

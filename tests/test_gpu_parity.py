@@ -413,3 +413,22 @@ def test_pinned_host_buffers_match_pageable(lib, precision):
         outs.append(np.array(got))
         h.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gather_overlap_gives_identical_bits(lib, precision, monkeypatch):
+    """The projector gather on its second stream (beside the FFT passes) against the serial
+    order (TDDFT_NO_OVERLAP=1): same kernels on the same data, so the states agree bit for bit."""
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=5, nk=2, natoms=3)
+    psi0 = S.small_parity_states(wl)
+    outs = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("TDDFT_NO_OVERLAP", flag)
+        h = _lib.TDDFT.from_workload(wl, precision=precision, e_min=-20, e_max=100)
+        h.set_fields(wl.times, wl.A, wl.B)
+        h.set_states(psi0, 0.0)
+        h.step(3)
+        outs.append(h.get_states())
+        h.close()
+    assert np.array_equal(outs[0], outs[1])

@@ -105,3 +105,33 @@ def test_zeeman_splitting_uniform_gas():
         nrm = np.vdot(p, p).real * s.grid.dV
         E.append((np.vdot(p, s.apply_h(p, V, np.zeros(3))) * s.grid.dV / nrm).real)
     assert E[1] - E[0] == pytest.approx(2 * MU_B * np.linalg.norm(B), rel=1e-12)
+
+
+def test_spectral_window_contains_the_exact_spectrum():
+    """The non-local bound dominates ||V_NL|| and the window of reading P2 contains every
+    eigenvalue of H (dense, tiny system with overlapping SOC projectors of two atoms)."""
+    from tests._systems import parity_system
+    wl, s, psi = parity_system(n=8, nstates=1, nk=1, lam=0.3, natoms=2)
+    s.pos[1] = s.pos[0] + np.array([1.5, 0.7, -0.9])  # strongly overlapping projector spheres
+    s.__init__(wl.L, wl.n, s.pos, wl.species, wl.Z, wl.rc_loc, wl.width, wl.lmax, wl.D, wl.lam,
+               wl.r_cut, wl.kpts, wl.kw, wl.occ)
+    A = np.array([0.1, -0.2, 0.05])
+    V, _ = s.potential(s.rho_v(psi), [0.05, 0.0, 0.1])
+    shape = psi.shape
+    nvec = int(np.prod(shape))
+    H = np.empty((nvec, nvec), np.complex128)
+    NL = np.empty((nvec, nvec), np.complex128)
+    e = np.zeros(nvec, np.complex128)
+    for j in range(nvec):
+        e[j] = 1.0
+        x = e.reshape(shape)
+        H[:, j] = s.apply_h(x, V, A).reshape(-1)
+        NL[:, j] = s.apply_nonlocal(x[0], wl.kpts[0] + A).reshape(-1)
+        e[j] = 0.0
+    nl_norm = np.abs(np.linalg.eigvalsh(0.5 * (NL + NL.conj().T))).max()
+    bound = s.nl_norm_bound()
+    assert nl_norm <= bound
+    assert bound <= 4.0 * nl_norm  # and is not loose by more than a small factor here
+    ev = np.linalg.eigvalsh(0.5 * (H + H.conj().T))
+    lo, hi = s.spectral_bounds(V, [A], margin=0.0)
+    assert lo <= ev.min() and ev.max() <= hi
