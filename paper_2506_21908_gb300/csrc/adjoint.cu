@@ -14,37 +14,81 @@
 #include "fft.cuh"
 #include "impl.cuh"
 #include "kcommon.cuh"
+#include "kepi.cuh"
 
 namespace tddft {
 
 // ------------------------------------------------------------------ potential gradient
+// Band group g = blockIdx.y sums spinors [kb0, kb1) for two neighbouring points per thread (the
+// density kernel's layout); FP32 spinors sum up to 8 spinors in FP32 before each FP64 addition.
+// With one group the result goes straight into gV (+= f x), else the groups' partials are added
+// in a fixed order by k_grad_v_reduce.
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_grad_v(const typename CT<R>::type* __restrict__ S, const typename CT<R>::type* __restrict__ T, size_t N3, int nkb,
-         double f, double* __restrict__ gV) {
-  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+         int ngroups, double f, double* __restrict__ gV, double* __restrict__ part) {
+  using C = typename CT<R>::type;
+  const size_t r = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
   if (r >= N3) return;
-  double g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-  for (int kb = 0; kb < nkb; ++kb) {
-    const size_t ou = (size_t)(2 * kb) * N3 + r, od = ou + N3;
-    const double sux = S[ou].x, suy = S[ou].y, sdx = S[od].x, sdy = S[od].y;
-    const double tux = T[ou].x, tuy = T[ou].y, tdx = T[od].x, tdy = T[od].y;
-    g0 += sux * tux + suy * tuy;                    // Re(conj(su) tu)
-    g1 += sdx * tdx + sdy * tdy;                    // Re(conj(sd) td)
-    g2 += 0.5 * ((sux * tdx + suy * tdy) + (sdx * tux + sdy * tuy));
-    // 1/2 [Re(i conj(su) td) - Re(i conj(sd) tu)] = 1/2 [-Im(conj(su) td) + Im(conj(sd) tu)]
-    g3 += 0.5 * (-(sux * tdy - suy * tdx) + (sdx * tuy - sdy * tux));
+  const int g = blockIdx.y;
+  const int kb0 = (int)(((long long)nkb * g) / ngroups), kb1 = (int)(((long long)nkb * (g + 1)) / ngroups);
+  double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  constexpr int CH = sizeof(R) == 4 ? 8 : 1;
+  for (int kc = kb0; kc < kb1; kc += CH) {
+    R p[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    const int kend = min(kb1, kc + CH);
+#pragma unroll 1
+    for (int kb = kc; kb < kend; ++kb) {
+      const size_t ou = (size_t)(2 * kb) * N3 + r, od = ou + N3;
+      const Pair<C> su = ld2(S + ou), sd = ld2(S + od), tu = ld2(T + ou), td = ld2(T + od);
+      const C sus[2] = {su.a, su.b}, sds[2] = {sd.a, sd.b}, tus[2] = {tu.a, tu.b}, tds[2] = {td.a, td.b};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const R sux = sus[j].x, suy = sus[j].y, sdx = sds[j].x, sdy = sds[j].y;
+        const R tux = tus[j].x, tuy = tus[j].y, tdx = tds[j].x, tdy = tds[j].y;
+        p[j][0] += sux * tux + suy * tuy;  // Re(conj(su) tu)
+        p[j][1] += sdx * tdx + sdy * tdy;  // Re(conj(sd) td)
+        p[j][2] += (R)0.5 * ((sux * tdx + suy * tdy) + (sdx * tux + sdy * tuy));
+        // 1/2 [Re(i conj(su) td) - Re(i conj(sd) tu)] = 1/2 [-Im(conj(su) td) + Im(conj(sd) tu)]
+        p[j][3] += (R)0.5 * (-(sux * tdy - suy * tdx) + (sdx * tuy - sdy * tux));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[j][c] += (double)p[j][c];
   }
-  gV[r] += f * g0;
-  gV[N3 + r] += f * g1;
-  gV[2 * N3 + r] += f * g2;
-  gV[3 * N3 + r] += f * g3;
+  if (ngroups == 1) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      gV[c * N3 + r] += f * acc[0][c];
+      gV[c * N3 + r + 1] += f * acc[1][c];
+    }
+    return;
+  }
+  double* o = part + (size_t)g * 4 * N3;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) *reinterpret_cast<double2*>(o + c * N3 + r) = make_double2(acc[0][c], acc[1][c]);
+}
+
+__global__ void k_grad_v_reduce(size_t n, int ngroups, const double* __restrict__ part, double f, double* gV) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t = 0.0;
+  for (int g = 0; g < ngroups; ++g) t += part[(size_t)g * n + i];
+  gV[i] += f * t;
 }
 
 template <typename R>
-cudaError_t launch_grad_v(cudaStream_t st, size_t N3, int nkb, const void* S, const void* T, double f, double* gV) {
+cudaError_t launch_grad_v(cudaStream_t st, size_t N3, int nkb, const void* S, const void* T, double f, double* gV,
+                          double* part) {
   using C = typename CT<R>::type;
-  k_grad_v<R><<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>((const C*)S, (const C*)T, N3, nkb, f, gV);
+  const int G = part ? density_groups(N3, nkb) : 1;
+  dim3 grid((unsigned)((N3 / 2 + 255) / 256), G);
+  k_grad_v<R><<<grid, 256, 0, st>>>((const C*)S, (const C*)T, N3, nkb, G, f, gV, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || G == 1) return e;
+  k_grad_v_reduce<<<(unsigned)((4 * N3 + 255) / 256), 256, 0, st>>>(4 * N3, G, part, f, gV);
   return cudaGetLastError();
 }
 
@@ -106,10 +150,148 @@ k_fft_z_current(typename CT<R>::type* __restrict__ U, const typename CT<R>::type
   slab_store<N, NT, RS>(U + base, su, (size_t)N * N);
 }
 
+// Two-factor form of the same pass (n = R1 R2, see k_fft_z2_kin): A side (x, n0) reads both
+// slabs along z, B side (x, K0) holds U^ and W^ at kz = K0 + R2 K1 in registers, adds
+// Re(conj(U^) W^) (G + s)_a over its K1 in the working precision before the FP64 sums, then
+// multiplies U^ by the kinetic factor and transforms it back.
+template <typename R, int N>
+__global__ void __launch_bounds__(256)
+k_fft_z2_current(typename CT<R>::type* __restrict__ U, const typename CT<R>::type* __restrict__ W,
+                 const typename CT<R>::type* __restrict__ twg, ZParams zp, double* __restrict__ part) {
+  using C = typename CT<R>::type;
+  using TFW = TF<C, N, false>;
+  using TIN = TF<C, N, true>;
+  constexpr int NT = 256;
+  constexpr int R1 = TwoFactor<N>::R1, R2 = TwoFactor<N>::R2;
+  constexpr int IA = N * R1, IB = N * R2;
+  constexpr int PA = (IA + NT - 1) / NT, PB = (IB + NT - 1) / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* su = tw + N;            // [K0 R1 + n0][x]
+  C* sw = su + N * N;
+  R* kx = reinterpret_cast<R*>(sw + N * N);  // kinetic factors 1/2 q^2 scale per axis
+  R* kz = kx + N;
+  R* vx = kz + N;                            // velocities q_a = g_a f(i) + s_a
+  R* vz = vx + N;
+  double* red = reinterpret_cast<double*>(vz + N + (N & 1));  // [8][3], 8-byte aligned
+  const int y = blockIdx.x;
+  const int b = blockIdx.y;
+  const int k = b / zp.comps_per_k;
+  const size_t base = (size_t)b * N * N * N + (size_t)y * N;
+  constexpr size_t ZS = (size_t)N * N;
+  for (int i = threadIdx.x; i < N; i += NT) {
+    tw[i] = twg[i];
+    const double qx = zp.gs[0] * freq<N>(i) + zp.shift[k][0];
+    const double qz = zp.gs[2] * freq<N>(i) + zp.shift[k][2];
+    kx[i] = (R)(0.5 * qx * qx * zp.scale);
+    kz[i] = (R)(0.5 * qz * qz * zp.scale);
+    vx[i] = (R)qx;
+    vz[i] = (R)qz;
+  }
+  const double qyd = zp.gs[1] * freq<N>(y) + zp.shift[k][1];
+  const R qy = (R)qyd, ky = (R)(0.5 * qyd * qyd * zp.scale);
+  C vu[PA][R2], vw[PA][R2];
+#pragma unroll
+  for (int p = 0; p < PA; ++p) {
+    const int i = threadIdx.x + p * NT;
+    if (IA % NT == 0 || i < IA) {
+      const int n0 = i / N, x = i - n0 * N;
+#pragma unroll
+      for (int q = 0; q < R2; ++q) {
+        vu[p][q] = U[base + (size_t)(n0 + R1 * q) * ZS + x];
+        vw[p][q] = W[base + (size_t)(n0 + R1 * q) * ZS + x];
+      }
+    }
+  }
+  __syncthreads();  // tables
+#pragma unroll
+  for (int p = 0; p < PA; ++p) {
+    const int i = threadIdx.x + p * NT;
+    if (IA % NT == 0 || i < IA) {
+      const int n0 = i / N, x = i - n0 * N;
+      TFW::a_side(vu[p], n0, tw);
+      TFW::a_side(vw[p], n0, tw);
+#pragma unroll
+      for (int k0 = 0; k0 < R2; ++k0) {
+        su[(k0 * R1 + n0) * N + x] = vu[p][k0];
+        sw[(k0 * R1 + n0) * N + x] = vw[p][k0];
+      }
+    }
+  }
+  __syncthreads();
+  double ax = 0, ay = 0, az = 0;
+#pragma unroll
+  for (int p = 0; p < PB; ++p) {
+    const int i = threadIdx.x + p * NT;
+    if (IB % NT == 0 || i < IB) {
+      const int k0 = i / N, x = i - k0 * N;
+      C a[R1], w[R1];
+#pragma unroll
+      for (int n0 = 0; n0 < R1; ++n0) {
+        a[n0] = su[(k0 * R1 + n0) * N + x];
+        w[n0] = sw[(k0 * R1 + n0) * N + x];
+      }
+      TFW::b_side(a, k0, tw);
+      TFW::b_side(w, k0, tw);
+      R cx = 0, cz = 0, cs = 0;
+      const R kxy = kx[x] + ky;
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) {
+        const int kzi = k0 + R2 * k1;
+        const R re = a[k1].x * w[k1].x + a[k1].y * w[k1].y;  // Re(conj(U^) W^)
+        cs += re;
+        cz += re * vz[kzi];
+        a[k1] = cscale(a[k1], kxy + kz[kzi]);
+      }
+      cx = cs * vx[x];
+      ax += (double)cx;
+      ay += (double)cs * (double)qy;
+      az += (double)cz;
+      TIN::b_side(a, k0, tw);
+#pragma unroll
+      for (int n0 = 0; n0 < R1; ++n0) su[(k0 * R1 + n0) * N + x] = a[n0];
+    }
+  }
+  ax = warp_sum(ax);
+  ay = warp_sum(ay);
+  az = warp_sum(az);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[3 * warp] = ax;
+    red[3 * warp + 1] = ay;
+    red[3 * warp + 2] = az;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w8 = 0; w8 < NT / 32; ++w8) t += red[3 * w8 + threadIdx.x];
+    part[((size_t)b * N + y) * 3 + threadIdx.x] = t;
+  }
+#pragma unroll
+  for (int p = 0; p < PA; ++p) {
+    const int i = threadIdx.x + p * NT;
+    if (IA % NT == 0 || i < IA) {
+      const int n0 = i / N, x = i - n0 * N;
+#pragma unroll
+      for (int k0 = 0; k0 < R2; ++k0) vu[p][k0] = su[(k0 * R1 + n0) * N + x];
+      TIN::a_side(vu[p], n0, tw);
+#pragma unroll
+      for (int n1 = 0; n1 < R2; ++n1) U[base + (size_t)(n0 + R1 * n1) * ZS + x] = vu[p][n1];
+    }
+  }
+}
+
 template <typename R, int N>
 static cudaError_t z_current_n(cudaStream_t st, void* U, const void* W, int nbatch, const void* tw, const ZParams& zp,
                                double* part) {
   using C = typename CT<R>::type;
+  if constexpr (TwoFactor<N>::ok) {
+    const size_t smem2 = (size_t)(N + 2 * N * N) * sizeof(C) + (size_t)(4 * N + 2) * sizeof(R) + 24 * sizeof(double);
+    auto kf2 = k_fft_z2_current<R, N>;
+    cudaFuncSetAttribute(kf2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    kf2<<<dim3(N, nbatch), 256, smem2, st>>>((C*)U, (const C*)W, (const C*)tw, zp, part);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)(N + 2 * N * (N + 1)) * sizeof(C) + 24 * sizeof(double);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   auto kf = k_fft_z_current<R, N>;
@@ -368,19 +550,20 @@ k_density_adjoint(const typename CT<R>::type* __restrict__ psi, const double* __
   if (r >= N3) return;
   const int kb = blockIdx.y;
   const size_t ou = (size_t)(2 * kb) * N3 + r, od = ou + N3;
-  const double w = wf[kb];
-  const double r0 = rbar[r], r1 = rbar[N3 + r], r2 = rbar[2 * N3 + r], r3 = rbar[3 * N3 + r];
+  // in the working precision R (the output's; FP64 arithmetic is scarce on this part)
+  const R w = (R)wf[kb];
+  const R r0 = (R)rbar[r], r1 = (R)rbar[N3 + r], r2 = (R)rbar[2 * N3 + r], r3 = (R)rbar[3 * N3 + r];
   const C u = psi[ou], d = psi[od];
-  double bux = w * (2.0 * r0 * u.x + r2 * d.x - r3 * d.y);
-  double buy = w * (2.0 * r0 * u.y + r2 * d.y + r3 * d.x);
-  double bdx = w * (2.0 * r1 * d.x + r2 * u.x + r3 * u.y);
-  double bdy = w * (2.0 * r1 * d.y + r2 * u.y - r3 * u.x);
+  R bux = w * ((R)2 * r0 * u.x + r2 * d.x - r3 * d.y);
+  R buy = w * ((R)2 * r0 * u.y + r2 * d.y + r3 * d.x);
+  R bdx = w * ((R)2 * r1 * d.x + r2 * u.x + r3 * u.y);
+  R bdy = w * ((R)2 * r1 * d.y + r2 * u.y - r3 * u.x);
   if (add) {
     const C au = add[ou], ad = add[od];
     bux += au.x; buy += au.y; bdx += ad.x; bdy += ad.y;
   }
-  out[ou] = cmake<C>((R)bux, (R)buy);
-  out[od] = cmake<C>((R)bdx, (R)bdy);
+  out[ou] = cmake<C>(bux, buy);
+  out[od] = cmake<C>(bdx, bdy);
 }
 template <typename R>
 cudaError_t launch_density_adjoint(cudaStream_t st, size_t N3, int nkb, const void* psi, const double* rbar,
@@ -399,18 +582,19 @@ __global__ void k_seed(size_t n, const typename CT<R>::type* __restrict__ y1, do
   using C = typename CT<R>::type;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double x = 0.0, y = 0.0;
+  // in the working precision R (the output's; FP64 arithmetic is scarce on this part)
+  R x = 0, y = 0;
   if (y1) {
     const C v = y1[i];
-    x += ar * v.x - ai * v.y;
-    y += ar * v.y + ai * v.x;
+    x += (R)ar * v.x - (R)ai * v.y;
+    y += (R)ar * v.y + (R)ai * v.x;
   }
   if (y2) {
     const C v = y2[i];
-    x += br * v.x - bi * v.y;
-    y += br * v.y + bi * v.x;
+    x += (R)br * v.x - (R)bi * v.y;
+    y += (R)br * v.y + (R)bi * v.x;
   }
-  out[i] = cmake<C>((R)x, (R)y);
+  out[i] = cmake<C>(x, y);
 }
 template <typename R>
 cudaError_t launch_seed(cudaStream_t st, size_t n, const void* y1, const double a[2], const void* y2,
@@ -422,7 +606,8 @@ cudaError_t launch_seed(cudaStream_t st, size_t n, const void* y1, const double 
 }
 
 #define TDDFT_ADJ_INST(R)                                                                                        \
-  template cudaError_t launch_grad_v<R>(cudaStream_t, size_t, int, const void*, const void*, double, double*);     \
+  template cudaError_t launch_grad_v<R>(cudaStream_t, size_t, int, const void*, const void*, double, double*,       \
+                                       double*);                                                                 \
   template cudaError_t launch_fft_z_current<R>(cudaStream_t, int, void*, const void*, int, const void*,            \
                                                const ZParams&, double*);                                         \
   template cudaError_t launch_nl_agrad<R>(cudaStream_t, int, int, const void*, const void*, const void*,           \

@@ -939,7 +939,7 @@ tddft_status cheb_adjoint(tddft_ctx* c, AdjWork& w, const std::vector<const void
   for (int k = K - 1; k >= 0; --k) {
     const void* Tk = T[k];
     const double f = (k >= 1 ? 2.0 : 1.0) * ep.inv_delta;
-    if ((s = c->launch(KC_OTHER, "grad V", [&] { return launch_grad_v<R>(c->st, c->N3, c->nkb, cur, Tk, f, w.gV); })))
+    if ((s = c->launch(KC_OTHER, "grad V", [&] { return launch_grad_v<R>(c->st, c->N3, c->nkb, cur, Tk, f, w.gV, c->rho_part); })))
       return s;
     if ((s = c->launch(KC_FFT_XY, "adj fft xy", [&] { return launch_fft_xy<R>(c->st, c->N, cur, c->tmp, nbatch, c->tw, false); }))) return s;
     if ((s = c->launch(KC_FFT_XY, "adj fft xy T", [&] { return launch_fft_xy<R>(c->st, c->N, Tk, w.tmp2, nbatch, c->tw, false); }))) return s;

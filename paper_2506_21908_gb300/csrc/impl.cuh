@@ -137,7 +137,8 @@ template <typename R>
 cudaError_t launch_proj_gather_mom(cudaStream_t st, int N, const void* psi, int nkb, const ProjTables<R>& pt,
                                    double dV, const EpiParams& ep, int alpha, void* m_out);
 template <typename R>
-cudaError_t launch_grad_v(cudaStream_t st, size_t N3, int nkb, const void* S, const void* T, double f, double* gV);
+cudaError_t launch_grad_v(cudaStream_t st, size_t N3, int nkb, const void* S, const void* T, double f, double* gV,
+                          double* part);  // part: density_groups(N3, nkb) x 4 N3 doubles
 template <typename R>
 cudaError_t launch_fft_z_current(cudaStream_t st, int N, void* U, const void* W, int nbatch, const void* tw,
                                  const ZParams& zp, double* part);
