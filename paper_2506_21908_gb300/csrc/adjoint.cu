@@ -6,7 +6,7 @@
 //   k_grad_v          dRe<S, dV T>/dV_v(r) summed over spinors (4-vector potential gradient)
 //   k_fft_z_current   z pass on the xy transforms of S and T: accumulates the kinetic current
 //                     Re sum_G conj(S^) (G + k + A)_a T^ and applies the kinetic multiply to S
-//   k_nl_agrad        projector-phase part of dRe<S, dV_NL T>/dA from projections and moments
+//   k_nl_agrad_fused  projector-phase part of dRe<S, dV_NL T>/dA in one pass over the entries
 //   k_xc_adjoint      locally collinear LSDA Jacobian-transpose (analytic second derivatives of
 //                     Slater exchange and PW92 correlation), the B-field and Hartree inputs
 //   k_density_adjoint psibar += d rho_v / d psi ^T rhobar  (Eqs. rho1-rho3, density4)
@@ -331,46 +331,110 @@ cudaError_t launch_accum_parts(cudaStream_t st, size_t count, const double* part
 }
 
 // ------------------------------------------------------------------ projector-phase gradient
-// out[kb][a] = (1/dV) sum_{atoms, p, sigma} [ Re(-i conj(mS^a) dcT) + Re(i conj(dcS) mT^a) ]
-// where m^a are the moment projections sum d_a beta~* psi dV and dc = D c.
-template <typename R>
-__global__ void k_nl_agrad(int ncoef, const typename CT<R>::type* __restrict__ mS,
-                           const typename CT<R>::type* __restrict__ dcT, const typename CT<R>::type* __restrict__ dcS,
-                           const typename CT<R>::type* __restrict__ mT, size_t mstride, double inv_dV, double f,
-                           double* out) {
-  __shared__ double sh[8 * 3];
-  const size_t off = (size_t)blockIdx.x * ncoef;
-  double acc[3] = {0, 0, 0};
-  for (int i = threadIdx.x; i < ncoef; i += 256) {
-    const auto dt = dcT[off + i], ds = dcS[off + i];
+// One pass over the sphere entries of atom a for spinor kb: with w_X = sum_p beta_p (D c_X)_p the
+// two moment contractions below reduce to
+//   sum_e d_alpha Im( e^{-i phi} [conj(S) w_T + conj(T) w_S] ),  phi = (k + A).d,
+// summed over both spin components (dV cancels against the 1/dV of the contraction).  Partials
+// per (spinor, atom) are added over atoms in a fixed order by k_nl_agrad_sum.
+template <typename R, int NLM>
+__global__ void __launch_bounds__(256)
+k_nl_agrad_fused(const typename CT<R>::type* __restrict__ S, const typename CT<R>::type* __restrict__ T, size_t N3,
+                 ProjTables<R> pt, EpiParams ep, const typename CT<R>::type* __restrict__ dcS,
+                 const typename CT<R>::type* __restrict__ dcT, double* __restrict__ part) {
+  using C = typename CT<R>::type;
+  const int a = blockIdx.x;
+  const int kb = blockIdx.y;
+  const int k = kb / ep.nstates;
+  const R sx = (R)ep.shift[k][0], sy = (R)ep.shift[k][1], sz = (R)ep.shift[k][2];
+  __shared__ C dS[2 * NLM], dT[2 * NLM];
+  __shared__ double red[8][3];
+  const size_t cof = ((size_t)kb * pt.natoms + a) * 2 * NLM;
+  if (threadIdx.x < 2 * NLM) {
+    dS[threadIdx.x] = dcS[cof + threadIdx.x];
+    dT[threadIdx.x] = dcT[cof + threadIdx.x];
+  }
+  __syncthreads();
+  R nl[4];
+  load_row<R, 4>(pt.nrm + (size_t)a * 4, nl);
+  const C* su_ = S + (size_t)(2 * kb) * N3;
+  const C* sd_ = su_ + N3;
+  const C* tu_ = T + (size_t)(2 * kb) * N3;
+  const C* td_ = tu_ + N3;
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int e0 = pt.g_ptr[a], e1 = pt.g_ptr[a + 1];
+  for (int e = e0 + threadIdx.x; e < e1; e += 256) {
+    const int r = pt.g_idx[e];
+    R t[4], bt[NLM];
+    load_row<R, 4>(pt.g_row + (size_t)e * 4, t);
+    beta_values<R, NLM>(t[0], t[1], t[2], t[3], nl, pt.yc, bt);
+    R sn, cs;
+    sincos_r<R>(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);
+    const C su = su_[r], sd = sd_[r], tu = tu_[r], td = td_[r];
+    R wtu_x = 0, wtu_y = 0, wtd_x = 0, wtd_y = 0, wsu_x = 0, wsu_y = 0, wsd_x = 0, wsd_y = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const auto ms = mS[a * mstride + off + i], mt = mT[a * mstride + off + i];
-      acc[a] += ((double)ms.x * dt.y - (double)ms.y * dt.x) - ((double)ds.x * mt.y - (double)ds.y * mt.x);
+    for (int p = 0; p < NLM; ++p) {
+      const R bp = bt[p];
+      wtu_x += bp * dT[2 * p].x; wtu_y += bp * dT[2 * p].y;
+      wtd_x += bp * dT[2 * p + 1].x; wtd_y += bp * dT[2 * p + 1].y;
+      wsu_x += bp * dS[2 * p].x; wsu_y += bp * dS[2 * p].y;
+      wsd_x += bp * dS[2 * p + 1].x; wsd_y += bp * dS[2 * p + 1].y;
     }
+    // X = conj(su) wTu + conj(sd) wTd + conj(tu) wSu + conj(td) wSd
+    const R xr = su.x * wtu_x + su.y * wtu_y + sd.x * wtd_x + sd.y * wtd_y + tu.x * wsu_x + tu.y * wsu_y +
+                 td.x * wsd_x + td.y * wsd_y;
+    const R xi = su.x * wtu_y - su.y * wtu_x + sd.x * wtd_y - sd.y * wtd_x + tu.x * wsu_y - tu.y * wsu_x +
+                 td.x * wsd_y - td.y * wsd_x;
+    const double im = (double)(cs * xi - sn * xr);  // Im(e^{-i phi} X)
+    acc[0] += (double)t[0] * im;
+    acc[1] += (double)t[1] * im;
+    acc[2] += (double)t[2] * im;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double v = warp_sum(acc[a]);
-    if (lane == 0) sh[3 * warp + a] = v;
+  for (int i = 0; i < 3; ++i) {
+    const double v = warp_sum(acc[i]);
+    if (lane == 0) red[warp][i] = v;
   }
   __syncthreads();
   if (threadIdx.x < 3) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += sh[3 * w + threadIdx.x];
-    out[3 * blockIdx.x + threadIdx.x] += f * inv_dV * t;
+    double tsum = 0.0;
+    for (int w = 0; w < 8; ++w) tsum += red[w][threadIdx.x];
+    part[((size_t)kb * pt.natoms + a) * 3 + threadIdx.x] = tsum;
   }
 }
 
+// out[3 kb + i] += f sum_a part[kb][a][i], atoms in order.
+__global__ void k_nl_agrad_sum(int nkb, int natoms, const double* __restrict__ part, double f, double* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= 3 * nkb) return;
+  const int kb = j / 3, i = j - 3 * kb;
+  double t = 0.0;
+  for (int a = 0; a < natoms; ++a) t += part[((size_t)kb * natoms + a) * 3 + i];
+  out[j] += f * t;
+}
+
 template <typename R>
-cudaError_t launch_nl_agrad(cudaStream_t st, int nkb, int ncoef, const void* mS, const void* dcT, const void* dcS,
-                            const void* mT, size_t mstride, double inv_dV, double f, double* out) {
+cudaError_t launch_nl_agrad_fused(cudaStream_t st, int N, const void* S, const void* T, int nkb,
+                                  const ProjTables<R>& pt, const EpiParams& ep, const void* dcS, const void* dcT,
+                                  double f, double* part, double* out) {
   using C = typename CT<R>::type;
-  k_nl_agrad<R><<<nkb, 256, 0, st>>>(ncoef, (const C*)mS, (const C*)dcT, (const C*)dcS, (const C*)mT, mstride, inv_dV,
-                                      f, out);
+  const size_t N3 = (size_t)N * N * N;
+  dim3 grid(pt.natoms, nkb);
+#define NLA_ARGS (const C*)S, (const C*)T, N3, pt, ep, (const C*)dcS, (const C*)dcT, part
+  switch (pt.nlm) {
+    case 1: k_nl_agrad_fused<R, 1><<<grid, 256, 0, st>>>(NLA_ARGS); break;
+    case 4: k_nl_agrad_fused<R, 4><<<grid, 256, 0, st>>>(NLA_ARGS); break;
+    case 9: k_nl_agrad_fused<R, 9><<<grid, 256, 0, st>>>(NLA_ARGS); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef NLA_ARGS
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_nl_agrad_sum<<<(3 * nkb + 127) / 128, 128, 0, st>>>(nkb, pt.natoms, part, f, out);
   return cudaGetLastError();
 }
+
+
 
 // ------------------------------------------------------------------ XC adjoint
 // PW92 G(rs) with first and second derivatives.
@@ -610,12 +674,13 @@ cudaError_t launch_seed(cudaStream_t st, size_t n, const void* y1, const double 
                                        double*);                                                                 \
   template cudaError_t launch_fft_z_current<R>(cudaStream_t, int, void*, const void*, int, const void*,            \
                                                const ZParams&, double*);                                         \
-  template cudaError_t launch_nl_agrad<R>(cudaStream_t, int, int, const void*, const void*, const void*,           \
-                                          const void*, size_t, double, double, double*);                          \
   template cudaError_t launch_density_adjoint<R>(cudaStream_t, size_t, int, const void*, const double*,           \
                                                  const double*, const void*, void*);                             \
   template cudaError_t launch_seed<R>(cudaStream_t, size_t, const void*, const double*, const void*,              \
-                                      const double*, void*);
+                                      const double*, void*);                                                     \
+  template cudaError_t launch_nl_agrad_fused<R>(cudaStream_t, int, const void*, const void*, int,                 \
+                                                const ProjTables<R>&, const EpiParams&, const void*, const void*,  \
+                                                double, double*, double*);
 
 TDDFT_ADJ_INST(float)
 TDDFT_ADJ_INST(double)

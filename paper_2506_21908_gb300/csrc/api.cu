@@ -857,7 +857,8 @@ struct AdjWork {
   std::vector<double*> rhos, Vs;
   std::vector<float*> Vfs;
   double *gV = nullptr, *rbar = nullptr, *gvf = nullptr, *gbf = nullptr, *part = nullptr, *agrad = nullptr;
-  void *cS = nullptr, *dcS = nullptr, *mS = nullptr, *cT = nullptr, *dcT = nullptr, *mT = nullptr;
+  void *cS = nullptr, *dcS = nullptr, *cT = nullptr, *dcT = nullptr;
+  double* apart = nullptr;                 // projector-phase gradient partials [nkb][natoms][3]
   size_t ncoef = 0;
 };
 
@@ -877,22 +878,6 @@ tddft_status gather_into(tddft_ctx* c, const void* in, const double A[3], void* 
   });
 }
 
-template <typename R>
-tddft_status gather_moments(tddft_ctx* c, const void* in, const double A[3], void* mb, size_t ncoef) {
-  if (c->natoms == 0) return TDDFT_OK;
-  EpiParams ep{};
-  ep.nstates = c->nb;
-  fill_shifts(c, A, ep.shift);
-  ProjTables<R> pt = c->tables<R>();
-  for (int a = 0; a < 3; ++a) {
-    void* dst = (char*)mb + (size_t)a * ncoef * 2 * sizeof(R);
-    tddft_status s = c->launch(KC_PROJ, "adjoint moments", [&] {
-      return launch_proj_gather_mom<R>(c->st, c->N, in, c->nkb, pt, c->dV, ep, a, dst);
-    });
-    if (s) return s;
-  }
-  return TDDFT_OK;
-}
 
 // Reverse of one Chebyshev series with terms T[0..K-1]; seeds (y1, a1 up to K1), (y2, a2 up to K2).
 // Accumulates the potential gradient into w.gV, the A-gradient into gA[3]; returns S_0 in *xbar.
@@ -953,12 +938,9 @@ tddft_status cheb_adjoint(tddft_ctx* c, AdjWork& w, const std::vector<const void
       return s;
     if ((s = c->launch(KC_FFT_XY, "adj ifft xy", [&] { return launch_fft_xy<R>(c->st, c->N, c->tmp, c->tmp, nbatch, c->tw, true); }))) return s;
     if (c->natoms > 0) {
-      if ((s = gather_into<R>(c, cur, A, w.cS, w.dcS)) || (s = gather_moments<R>(c, cur, A, w.mS, w.ncoef)) ||
-          (s = gather_into<R>(c, Tk, A, w.cT, w.dcT)) || (s = gather_moments<R>(c, Tk, A, w.mT, w.ncoef)))
-        return s;
-      const int per = c->natoms * 2 * c->nlm;
-      if ((s = c->launch(KC_OTHER, "adj nl agrad", [&] {
-             return launch_nl_agrad<R>(c->st, c->nkb, per, w.mS, w.dcT, w.dcS, w.mT, w.ncoef, 1.0 / c->dV, f, w.agrad);
+      if ((s = gather_into<R>(c, cur, A, w.cS, w.dcS)) || (s = gather_into<R>(c, Tk, A, w.cT, w.dcT))) return s;
+      if ((s = c->launch(KC_PROJ, "adj nl agrad", [&] {
+             return launch_nl_agrad_fused<R>(c->st, c->N, cur, Tk, c->nkb, pt, ep, w.dcS, w.dcT, f, w.apart, w.agrad);
            })))
         return s;
     }
@@ -1162,8 +1144,8 @@ tddft_status do_backward(tddft_ctx* c, int nsteps, int ckpt, const double* dL_dr
   w.ncoef = (size_t)c->nkb * std::max(1, c->natoms) * 2 * c->nlm;
   const size_t cb = w.ncoef * 2 * sizeof(R);
   if ((s = tmp_alloc(c, db, &w.cS, cb, "cS")) || (s = tmp_alloc(c, db, &w.dcS, cb, "dcS")) ||
-      (s = tmp_alloc(c, db, &w.mS, 3 * cb, "mS")) || (s = tmp_alloc(c, db, &w.cT, cb, "cT")) ||
-      (s = tmp_alloc(c, db, &w.dcT, cb, "dcT")) || (s = tmp_alloc(c, db, &w.mT, 3 * cb, "mT")))
+      (s = tmp_alloc(c, db, &w.apart, (size_t)c->nkb * std::max(c->natoms, 1) * 3 * 8, "agrad parts")) ||
+      (s = tmp_alloc(c, db, &w.cT, cb, "cT")) || (s = tmp_alloc(c, db, &w.dcT, cb, "dcT")))
     return s;
   const int nck = (nsteps + ckpt - 1) / ckpt;
   std::vector<void*> ck(std::max(nck, 1), nullptr), seg(ckpt, nullptr);

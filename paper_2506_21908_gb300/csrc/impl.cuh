@@ -134,17 +134,18 @@ cudaError_t launch_atom_sums(cudaStream_t st, size_t N3, int natoms, const doubl
 
 // ---------------------------------------------------------------- adjoint launchers
 template <typename R>
-cudaError_t launch_proj_gather_mom(cudaStream_t st, int N, const void* psi, int nkb, const ProjTables<R>& pt,
-                                   double dV, const EpiParams& ep, int alpha, void* m_out);
-template <typename R>
 cudaError_t launch_grad_v(cudaStream_t st, size_t N3, int nkb, const void* S, const void* T, double f, double* gV,
                           double* part);  // part: density_groups(N3, nkb) x 4 N3 doubles
 template <typename R>
 cudaError_t launch_fft_z_current(cudaStream_t st, int N, void* U, const void* W, int nbatch, const void* tw,
                                  const ZParams& zp, double* part);
+// Projector-phase A-gradient in one pass over the entries (replaces the moment gathers and
+// launch_nl_agrad): out[kb][a] += f sum_atoms sum_e d_a Im(e^{-i phi}[conj(S) w_T + conj(T) w_S]).
+// part: natoms x nkb x 3 doubles of scratch.
 template <typename R>
-cudaError_t launch_nl_agrad(cudaStream_t st, int nkb, int ncoef, const void* mS, const void* dcT, const void* dcS,
-                            const void* mT, size_t mstride, double inv_dV, double f, double* out);
+cudaError_t launch_nl_agrad_fused(cudaStream_t st, int N, const void* S, const void* T, int nkb,
+                                  const ProjTables<R>& pt, const EpiParams& ep, const void* dcS, const void* dcT,
+                                  double f, double* part, double* out);
 cudaError_t launch_xc_adjoint(cudaStream_t st, size_t N3, const double* rho, const double* gV, int xc, double* rbar,
                               double* gvf, double* gbf);
 cudaError_t launch_add_hartree_adjoint(cudaStream_t st, size_t N3, const double2* h, double* rbar);

@@ -431,12 +431,10 @@ cudaError_t launch_fft_z(cudaStream_t st, int N, void* data, int nbatch, const v
 // ============================================================================ projectors
 
 // One CTA per (atom, spinor): c[p][sigma] = sum_e beta_p exp(+i s.d) psi_sigma(r_e) dV, then D c.
-// MOM < 0: projections c and D c.  MOM = a in {0, 1, 2}: moment projections
-// sum_e d_a beta_p exp(+i s.d) psi(r_e) dV only (written to c_out).
 template <typename R> struct GatherMinBlocks { static constexpr int value = 1; };
 template <> struct GatherMinBlocks<float> { static constexpr int value = 3; };
 
-template <typename R, int NLM, int MOM>
+template <typename R, int NLM>
 __global__ void __launch_bounds__(256, GatherMinBlocks<R>::value)
 k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTables<R> pt, R dV, EpiParams ep,
               typename CT<R>::type* __restrict__ c_out, typename CT<R>::type* __restrict__ dc_out) {
@@ -487,12 +485,8 @@ k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTable
     uc = un;
     dc = dn_;
     r1 = r2;
-    R pux = u.x * cs - u.y * sn, puy = u.x * sn + u.y * cs;  // u exp(+i arg)
-    R pdx = d.x * cs - d.y * sn, pdy = d.x * sn + d.y * cs;
-    if (MOM >= 0) {
-      const R wgt = t[MOM];
-      pux *= wgt; puy *= wgt; pdx *= wgt; pdy *= wgt;
-    }
+    const R pux = u.x * cs - u.y * sn, puy = u.x * sn + u.y * cs;  // u exp(+i arg)
+    const R pdx = d.x * cs - d.y * sn, pdy = d.x * sn + d.y * cs;
 #pragma unroll
     for (int p = 0; p < NLM; ++p) {
       const R bp = bt[p];
@@ -521,7 +515,6 @@ k_proj_gather(const typename CT<R>::type* __restrict__ psi, size_t N3, ProjTable
     cv[threadIdx.x] = c;
     c_out[((size_t)kb * pt.natoms + a) * 2 * NLM + threadIdx.x] = c;
   }
-  if (MOM >= 0) return;
   __syncthreads();
   if (threadIdx.x < 2 * NLM) {
     const R* D = pt.Dmat + ((size_t)a * 2 * NLM + threadIdx.x) * 2 * NLM * 2;
@@ -543,39 +536,14 @@ cudaError_t launch_proj_gather(cudaStream_t st, int N, const void* psi, int nkb,
   dim3 grid(pt.natoms, nkb);
   const size_t N3 = (size_t)N * N * N;
   switch (pt.nlm) {
-    case 1: k_proj_gather<R, 1, -1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
-    case 4: k_proj_gather<R, 4, -1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
-    case 9: k_proj_gather<R, 9, -1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
+    case 1: k_proj_gather<R, 1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
+    case 4: k_proj_gather<R, 4><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
+    case 9: k_proj_gather<R, 9><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)c_out, (C*)dc_out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-template <typename R, int NLM>
-static cudaError_t gather_mom_nlm(cudaStream_t st, dim3 grid, const void* psi, size_t N3, const ProjTables<R>& pt,
-                                  double dV, const EpiParams& ep, int alpha, void* m_out) {
-  using C = typename CT<R>::type;
-  switch (alpha) {
-    case 0: k_proj_gather<R, NLM, 0><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)m_out, nullptr); break;
-    case 1: k_proj_gather<R, NLM, 1><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)m_out, nullptr); break;
-    default: k_proj_gather<R, NLM, 2><<<grid, 256, 0, st>>>((const C*)psi, N3, pt, (R)dV, ep, (C*)m_out, nullptr); break;
-  }
-  return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_proj_gather_mom(cudaStream_t st, int N, const void* psi, int nkb, const ProjTables<R>& pt,
-                                   double dV, const EpiParams& ep, int alpha, void* m_out) {
-  if (pt.natoms == 0) return cudaSuccess;
-  dim3 grid(pt.natoms, nkb);
-  const size_t N3 = (size_t)N * N * N;
-  switch (pt.nlm) {
-    case 1: return gather_mom_nlm<R, 1>(st, grid, psi, N3, pt, dV, ep, alpha, m_out);
-    case 4: return gather_mom_nlm<R, 4>(st, grid, psi, N3, pt, dV, ep, alpha, m_out);
-    case 9: return gather_mom_nlm<R, 9>(st, grid, psi, N3, pt, dV, ep, alpha, m_out);
-    default: return cudaErrorInvalidValue;
-  }
-}
 
 // ============================================================================ density
 
@@ -1124,9 +1092,7 @@ cudaError_t launch_atom_sums(cudaStream_t st, size_t N3, int natoms, const doubl
   template cudaError_t launch_convert_out<R>(cudaStream_t, size_t, const void*, double2*);                       \
   template cudaError_t launch_band_dot<R>(cudaStream_t, size_t, int, const void*, const void*, double*, double*); \
   template cudaError_t launch_nl_energy<R>(cudaStream_t, int, int, const void*, const void*, double*);          \
-  template cudaError_t launch_soc_torque<R>(cudaStream_t, int, int, int, const void*, const double2*, double*);  \
-  template cudaError_t launch_proj_gather_mom<R>(cudaStream_t, int, const void*, int, const ProjTables<R>&,      \
-                                                 double, const EpiParams&, int, void*);
+  template cudaError_t launch_soc_torque<R>(cudaStream_t, int, int, int, const void*, const double2*, double*);
 
 TDDFT_INST(float)
 TDDFT_INST(double)
