@@ -331,11 +331,13 @@ cudaError_t launch_accum_parts(cudaStream_t st, size_t count, const double* part
 }
 
 // ------------------------------------------------------------------ projector-phase gradient
-// One pass over the sphere entries of atom a for spinor kb: with w_X = sum_p beta_p (D c_X)_p the
-// two moment contractions below reduce to
-//   sum_e d_alpha Im( e^{-i phi} [conj(S) w_T + conj(T) w_S] ),  phi = (k + A).d,
-// summed over both spin components (dV cancels against the 1/dV of the contraction).  Partials
-// per (spinor, atom) are added over atoms in a fixed order by k_nl_agrad_sum.
+// d Re<S, V_NL T> / dA_alpha through the projector phases exp(-i (k + A).d): with the moment
+// projections m^alpha_p[X] = sum_e d_alpha beta_p e^{i phi} X(e) dV (phi = (k + A).d) it is
+//   sum_{p, sigma} [ Im(conj(m^alpha_p[S]) (D c_T)_p) + Im(conj(m^alpha_p[T]) (D c_S)_p) ],
+// and since beta is real this equals, per atom and spinor, one pass over the sphere entries:
+//   sum_e d_alpha Im( e^{-i phi} [conj(S) w_T + conj(T) w_S] ) dV,  w_X = sum_p beta_p (D c_X)_p,
+// summed over both spin components.  The caller's 1/dV cancels the dV.  Partials per (spinor,
+// atom) are added over atoms in a fixed order by k_nl_agrad_sum.
 template <typename R, int NLM>
 __global__ void __launch_bounds__(256)
 k_nl_agrad_fused(const typename CT<R>::type* __restrict__ S, const typename CT<R>::type* __restrict__ T, size_t N3,
