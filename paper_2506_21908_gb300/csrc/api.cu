@@ -21,6 +21,7 @@
 #include <map>
 #include <array>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "impl.cuh"
@@ -181,6 +182,8 @@ struct tddft_ctx {
   std::vector<cd> cf_full, cf_half;
   bool use_fused = false;  // fused term kernel (where two planes fit in shared memory)
   bool use_cluster = false;  // one-kernel kinetic term on 16-CTA clusters (FP32, n = 32, 48, 64)
+  bool use_tma = false;      // FP32 xy passes fed by bulk asynchronous copies
+  bool epi_pairs = false;    // epilogue threads take one point of two spinors
   // device memory
   cudaStream_t st = nullptr;
   // second stream for the projector gather, which runs beside the FFT passes of the same term
@@ -207,7 +210,7 @@ struct tddft_ctx {
   int* owner = nullptr;      // nearest atom of each grid point (per-atom moments)
   double* atom_sums = nullptr;
   float* tc_part = nullptr;  // tensor-core gather partial products
-  int* tc_err = nullptr;     // set when a tensor-core wait gave up
+  int* tc_err = nullptr;     // wait errors: bit 1 tensor-core projector, bit 2 bulk-copy FFT pass
   void *g_tab = nullptr, *s_tab = nullptr, *Dmat = nullptr;
   void *g_row = nullptr, *s_row = nullptr, *nrm = nullptr;
   // bookkeeping
@@ -559,6 +562,23 @@ void fill_shifts(tddft_ctx* c, const double A[3], double (*shift)[3]) {
     for (int a = 0; a < 3; ++a) shift[k][a] = c->kpts[3 * k + a] + A[a];
 }
 
+// One xy pass over nbatch spinor components (FP32: the bulk-copy form where it applies).
+template <typename R> cudaError_t xy_pass(tddft_ctx* c, const void* in, void* out, int nbatch, bool inv) {
+  if constexpr (std::is_same<R, float>::value)
+    if (c->use_tma && fft_xy_tma_supported(c->N))
+      return launch_fft_xy_tma(c->st, c->N, in, out, nbatch, c->tw, inv, c->tc_err);
+  return launch_fft_xy<R>(c->st, c->N, in, out, nbatch, c->tw, inv);
+}
+
+// The pointwise epilogue (one point of two spinors per thread unless switched off).
+template <typename R>
+cudaError_t epilogue(tddft_ctx* c, const void* kin, const void* Tk, const void* Tkm1, void* Tout, void* acc1,
+                     void* acc2, const R* V, const ProjTables<R>& pt, const void* dc, int nkb, const EpiParams& ep) {
+  EpiParams e = ep;
+  e.spinor_pairs = c->epi_pairs ? 1 : 0;
+  return launch_epilogue<R>(c->st, c->N, kin, Tk, Tkm1, Tout, acc1, acc2, V, pt, dc, nkb, e);
+}
+
 // Kinetic part of H on all spinors: out = T in (three FFT passes).
 template <typename R> tddft_status kinetic(tddft_ctx* c, const void* in, void* out, const double A[3]) {
   ZParams zp{};
@@ -574,9 +594,9 @@ template <typename R> tddft_status kinetic(tddft_ctx* c, const void* in, void* o
     return c->launch(KC_FFT_Z, "kinetic cluster", [&] {
       return launch_kinetic_cluster(c->st, c->N, in, out, nbatch, c->tw, zp);
     }, by);
-  if ((s = c->launch(KC_FFT_XY, "fft xy", [&] { return launch_fft_xy<R>(c->st, c->N, in, out, nbatch, c->tw, false); }, by))) return s;
+  if ((s = c->launch(KC_FFT_XY, "fft xy", [&] { return xy_pass<R>(c, in, out, nbatch, false); }, by))) return s;
   if ((s = c->launch(KC_FFT_Z, "fft z", [&] { return launch_fft_z<R>(c->st, c->N, out, nbatch, c->tw, Z_KIN, zp); }, by))) return s;
-  return c->launch(KC_FFT_XY, "ifft xy", [&] { return launch_fft_xy<R>(c->st, c->N, out, out, nbatch, c->tw, true); }, by);
+  return c->launch(KC_FFT_XY, "ifft xy", [&] { return xy_pass<R>(c, out, out, nbatch, true); }, by);
 }
 
 template <typename R> tddft_status gather(tddft_ctx* c, const void* in, const double A[3], cudaStream_t sg = nullptr) {
@@ -734,7 +754,7 @@ tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double
                            (ep.use_acc2 ? (ep.init2 ? 1.0 : 2.0) : 0.0);
     const double by = streams * c->psi_elems() * 2 * sizeof(R) + 4.0 * c->N3 * sizeof(R);
     if ((s = c->launch(KC_EPI, "chebyshev epilogue", [&] {
-           return launch_epilogue<R>(c->st, c->N, c->tmp, cur, tkm1, out, acc1, acc2, Vr, pt, c->dcbuf, c->nkb, ep);
+           return epilogue<R>(c, c->tmp, cur, tkm1, out, acc1, acc2, Vr, pt, c->dcbuf, c->nkb, ep);
          }, by)))
       return s;
     prev = cur;
@@ -763,7 +783,7 @@ tddft_status taylor_series(tddft_ctx* c, const void* in, bool vcur, const double
     ep.a1[0] = 0.0;
     ep.a1[1] = -tau / k;
     if ((s = c->launch(KC_EPI, "taylor epilogue", [&] {
-           return launch_epilogue<R>(c->st, c->N, c->tmp, cur, nullptr, out, acc, nullptr, Vr, pt, c->dcbuf, c->nkb, ep);
+           return epilogue<R>(c, c->tmp, cur, nullptr, out, acc, nullptr, Vr, pt, c->dcbuf, c->nkb, ep);
          })))
       return s;
     cur = out;
@@ -926,8 +946,8 @@ tddft_status cheb_adjoint(tddft_ctx* c, AdjWork& w, const std::vector<const void
     const double f = (k >= 1 ? 2.0 : 1.0) * ep.inv_delta;
     if ((s = c->launch(KC_OTHER, "grad V", [&] { return launch_grad_v<R>(c->st, c->N3, c->nkb, cur, Tk, f, w.gV, c->rho_part); })))
       return s;
-    if ((s = c->launch(KC_FFT_XY, "adj fft xy", [&] { return launch_fft_xy<R>(c->st, c->N, cur, c->tmp, nbatch, c->tw, false); }))) return s;
-    if ((s = c->launch(KC_FFT_XY, "adj fft xy T", [&] { return launch_fft_xy<R>(c->st, c->N, Tk, w.tmp2, nbatch, c->tw, false); }))) return s;
+    if ((s = c->launch(KC_FFT_XY, "adj fft xy", [&] { return xy_pass<R>(c, cur, c->tmp, nbatch, false); }))) return s;
+    if ((s = c->launch(KC_FFT_XY, "adj fft xy T", [&] { return xy_pass<R>(c, Tk, w.tmp2, nbatch, false); }))) return s;
     if ((s = c->launch(KC_FFT_Z, "adj fft z current", [&] {
            return launch_fft_z_current<R>(c->st, c->N, c->tmp, w.tmp2, nbatch, c->tw, zp, w.part);
          })))
@@ -936,7 +956,7 @@ tddft_status cheb_adjoint(tddft_ctx* c, AdjWork& w, const std::vector<const void
            return launch_accum_parts(c->st, (size_t)nbatch * c->N, w.part, f / (double)c->N3, agk);
          })))
       return s;
-    if ((s = c->launch(KC_FFT_XY, "adj ifft xy", [&] { return launch_fft_xy<R>(c->st, c->N, c->tmp, c->tmp, nbatch, c->tw, true); }))) return s;
+    if ((s = c->launch(KC_FFT_XY, "adj ifft xy", [&] { return xy_pass<R>(c, c->tmp, c->tmp, nbatch, true); }))) return s;
     if (c->natoms > 0) {
       if ((s = gather_into<R>(c, cur, A, w.cS, w.dcS)) || (s = gather_into<R>(c, Tk, A, w.cT, w.dcT))) return s;
       if ((s = c->launch(KC_PROJ, "adj nl agrad", [&] {
@@ -955,7 +975,7 @@ tddft_status cheb_adjoint(tddft_ctx* c, AdjWork& w, const std::vector<const void
     ep.b1[0] = cb[0]; ep.b1[1] = cb[1];
     const void* s2 = prev2;
     if ((s = c->launch(KC_EPI, "adjoint epilogue", [&] {
-           return launch_epilogue<R>(c->st, c->N, c->tmp, cur, s2, out, const_cast<void*>(y1), const_cast<void*>(y2), Vr,
+           return epilogue<R>(c, c->tmp, cur, s2, out, const_cast<void*>(y1), const_cast<void*>(y2), Vr,
                                      pt, w.dcS, c->nkb, ep);
          })))
       return s;
@@ -1429,7 +1449,8 @@ template <typename R> tddft_status do_observables(tddft_ctx* c, double* n, doubl
       m[N3 + r] = -2.0 * rho_h[3 * N3 + r];
       m[2 * N3 + r] = rho_h[r] - rho_h[N3 + r];
     }
-  if (tcflag) return c->fail(TDDFT_ERR_CUDA, "a tensor-core projector wait exceeded its iteration limit");
+  if (tcflag & 1) return c->fail(TDDFT_ERR_CUDA, "a tensor-core projector wait exceeded its iteration limit");
+  if (tcflag & 2) return c->fail(TDDFT_ERR_CUDA, "a bulk-copy wait of an FFT pass exceeded its iteration limit");
   if (bad) return c->fail(TDDFT_ERR_DIVERGED, "non-finite density or norm");
   if (flag) return c->fail(TDDFT_ERR_BOUND, "potential left the Chebyshev spectral window");
   return TDDFT_OK;
@@ -1461,7 +1482,7 @@ template <typename R> tddft_status do_apply_h(tddft_ctx* c, const void* in, void
   ProjTables<R> pt = c->tables<R>();
   const R* Vr = vsel<R>(c, true);
   if ((s = c->launch(KC_EPI, "apply H", [&] {
-         return launch_epilogue<R>(c->st, c->N, c->tmp, c->Ta, nullptr, c->Tb, nullptr, nullptr, Vr, pt, c->dcbuf, c->nkb, ep);
+         return epilogue<R>(c, c->tmp, c->Ta, nullptr, c->Tb, nullptr, nullptr, Vr, pt, c->dcbuf, c->nkb, ep);
        })))
     return s;
   if (c->prec == TDDFT_FP64) {
@@ -1552,6 +1573,15 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
     // this part than the three passes, which overlap HBM traffic and shared-memory FFTs better).
     const char* f = std::getenv("TDDFT_CLUSTER");
     c->use_cluster = f && f[0] == '1';
+    // FP32 xy passes take their planes through bulk asynchronous copies; TDDFT_NO_TMA=1 keeps
+    // the register-fed passes (same results).
+    const char* g = std::getenv("TDDFT_NO_TMA");
+    c->use_tma = !(g && g[0] == '1');
+    // The epilogue gives each thread one grid point of two spinors (with an even number of
+    // states), so the projector scatter walks each point's entries once per spinor pair;
+    // TDDFT_NO_EPI_PAIRS=1 keeps two points of one spinor per thread (same results).
+    const char* h = std::getenv("TDDFT_NO_EPI_PAIRS");
+    c->epi_pairs = !(h && h[0] == '1');
   }
   if (atoms->natoms < 0 || (atoms->natoms > 0 && (!atoms->pos || !atoms->species))) return c->fail(TDDFT_ERR_ARG, "bad atoms");
   c->natoms = atoms->natoms;

@@ -16,8 +16,10 @@ namespace tddft {
 
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-// Two neighbouring grid points of one spinor per thread (16-byte accesses); the spinor's D c
-// for every atom is staged in shared memory when it is small.
+// Each thread takes two items: two neighbouring grid points of one spinor (SP = 0, 16-byte
+// accesses) or one grid point of two spinors of one k-point (SP = 1, 8-byte accesses), whose
+// projector scatter then walks the point's entries once for both.  The D c of the CTA's
+// spinor(s) for every atom is staged in shared memory when it is small.
 // AK selects the accumulator code compiled in: 0 = Chebyshev term without accumulator update,
 // 1 = Chebyshev term updating accumulator 1 only, 2 = every mode with run-time flags.  The
 // Chebyshev recurrence touches its accumulators on every third term only, so most launches take
@@ -26,7 +28,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 template <typename R, int AK> struct EpiMinBlocks { static constexpr int value = 1; };
 template <int AK> struct EpiMinBlocks<float, AK> { static constexpr int value = 4; };
 
-template <typename R, int NLM, int AK>
+template <typename R, int NLM, int AK, int SP>
 __global__ void __launch_bounds__(256, EpiMinBlocks<R, AK>::value)
 k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::type* Tk,
            const typename CT<R>::type* Tkm1, typename CT<R>::type* Tout, typename CT<R>::type* acc1,
@@ -35,20 +37,34 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
   using C = typename CT<R>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* dcs = reinterpret_cast<C*>(smem_raw);
-  const int kb = blockIdx.y;
+  const int kb = SP ? 2 * blockIdx.y : blockIdx.y;  // the (first) spinor
   const int k = kb / ep.nstates;
   const int ncoef = pt.natoms * 2 * NLM;
   const C* dcg = dc + (size_t)kb * ncoef;
   if (NLM > 0 && ep.dc_staged) {
-    for (int i = threadIdx.x; i < ncoef; i += blockDim.x) dcs[i] = dcg[i];
+    for (int i = threadIdx.x; i < (SP + 1) * ncoef; i += blockDim.x) dcs[i] = dcg[i];
     __syncthreads();
   }
   const C* dcb = (NLM > 0 && ep.dc_staged) ? dcs : dcg;
-  const size_t r = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const size_t r = (SP ? 1 : 2) * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
   if (r >= N3) return;
   const size_t ou = (size_t)(2 * kb) * N3 + r, od = ou + N3;
-  const Pair<C> pu2 = ld2(Tk + ou), pd2 = ld2(Tk + od);
-  const Pair<C> ku2 = ld2(kin + ou), kd2 = ld2(kin + od);
+  // the thread's two items of an array at offset o (up) or o + N3 (down)
+  const size_t step = 2 * N3;
+  auto ld = [&](const C* b, size_t o) -> Pair<C> {
+    if constexpr (SP) return Pair<C>{b[o], b[o + step]};
+    else return ld2(b + o);
+  };
+  auto st = [&](C* b, size_t o, C x, C y) {
+    if constexpr (SP) { b[o] = x; b[o + step] = y; }
+    else st2(b + o, x, y);
+  };
+  auto pf = [&](const C* b, size_t o) {
+    prefetch_l2(b + o);
+    if constexpr (SP) prefetch_l2(b + o + step);
+  };
+  const Pair<C> pu2 = ld(Tk, ou), pd2 = ld(Tk, od);
+  const Pair<C> ku2 = ld(kin, ou), kd2 = ld(kin, od);
   // Chebyshev terms: every input is requested before any arithmetic (more loads in flight)
   const bool cheb = AK < 2 || ep.mode == EPI_RECUR || ep.mode == EPI_FIRST;
   const bool rec = ep.mode == EPI_RECUR;
@@ -59,36 +75,41 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
   // lines are requested from HBM into L2 now and read into registers after the scatter, so they
   // hold no registers across its loop.
   const bool ld_acc1 = cheb && use1 && !ep.init1, ld_acc2 = cheb && use2 && !ep.init2;
-  if (rec) { prefetch_l2(Tkm1 + ou); prefetch_l2(Tkm1 + od); }
-  if (ld_acc1) { prefetch_l2(acc1 + ou); prefetch_l2(acc1 + od); }
-  if (ld_acc2) { prefetch_l2(acc2 + ou); prefetch_l2(acc2 + od); }
+  if (rec) { pf(Tkm1, ou); pf(Tkm1, od); }
+  if (ld_acc1) { pf(acc1, ou); pf(acc1, od); }
+  if (ld_acc2) { pf(acc2, ou); pf(acc2, od); }
   const C pu[2] = {pu2.a, pu2.b}, pd[2] = {pd2.a, pd2.b};
   C hu[2] = {ku2.a, ku2.b}, hd[2] = {kd2.a, kd2.b};
   {
-    const C v0 = *reinterpret_cast<const C*>(V + r), v1 = *reinterpret_cast<const C*>(V + N3 + r);
-    const C v2 = *reinterpret_cast<const C*>(V + 2 * N3 + r), v3 = *reinterpret_cast<const C*>(V + 3 * N3 + r);
     const R sx = (R)ep.shift[k][0], sy = (R)ep.shift[k][1], sz = (R)ep.shift[k][2];
-    h_point<R, NLM>(hu[0], hd[0], pu[0], pd[0], v0.x, v1.x, (R)0.5 * v2.x, (R)0.5 * v3.x, r, pt, dcb, sx, sy, sz);
-    h_point<R, NLM>(hu[1], hd[1], pu[1], pd[1], v0.y, v1.y, (R)0.5 * v2.y, (R)0.5 * v3.y, r + 1, pt, dcb, sx, sy, sz);
+    if constexpr (SP) {
+      const R v0 = V[r], v1 = V[N3 + r], v2 = V[2 * N3 + r], v3 = V[3 * N3 + r];
+      h_point_2sp<R, NLM>(hu, hd, pu, pd, v0, v1, (R)0.5 * v2, (R)0.5 * v3, r, pt, dcb, dcb + ncoef, sx, sy, sz);
+    } else {
+      const C v0 = *reinterpret_cast<const C*>(V + r), v1 = *reinterpret_cast<const C*>(V + N3 + r);
+      const C v2 = *reinterpret_cast<const C*>(V + 2 * N3 + r), v3 = *reinterpret_cast<const C*>(V + 3 * N3 + r);
+      h_point<R, NLM>(hu[0], hd[0], pu[0], pd[0], v0.x, v1.x, (R)0.5 * v2.x, (R)0.5 * v3.x, r, pt, dcb, sx, sy, sz);
+      h_point<R, NLM>(hu[1], hd[1], pu[1], pd[1], v0.y, v1.y, (R)0.5 * v2.y, (R)0.5 * v3.y, r + 1, pt, dcb, sx, sy, sz);
+    }
   }
-  if (rec) { qu0 = ld2(Tkm1 + ou); qd0 = ld2(Tkm1 + od); }
-  if (ld_acc1) { au1 = ld2(acc1 + ou); ad1 = ld2(acc1 + od); }
-  if (ld_acc2) { au2 = ld2(acc2 + ou); ad2 = ld2(acc2 + od); }
+  if (rec) { qu0 = ld(Tkm1, ou); qd0 = ld(Tkm1, od); }
+  if (ld_acc1) { au1 = ld(acc1, ou); ad1 = ld(acc1, od); }
+  if (ld_acc2) { au2 = ld(acc2, ou); ad2 = ld(acc2, od); }
   auto cmulr = [](C a, R cr, R ci) { return cmake<C>(cr * a.x - ci * a.y, cr * a.y + ci * a.x); };
   if (AK == 2 && ep.mode == EPI_APPLY) {
-    st2(Tout + ou, hu[0], hu[1]);
-    st2(Tout + od, hd[0], hd[1]);
+    st(Tout, ou, hu[0], hu[1]);
+    st(Tout, od, hd[0], hd[1]);
     return;
   }
   if (AK == 2 && ep.mode == EPI_TAYLOR) {
     const R cr = (R)ep.a1[0], ci = (R)ep.a1[1];
     C tu[2], td[2];
     for (int j = 0; j < 2; ++j) { tu[j] = cmulr(hu[j], cr, ci); td[j] = cmulr(hd[j], cr, ci); }
-    st2(Tout + ou, tu[0], tu[1]);
-    st2(Tout + od, td[0], td[1]);
-    const Pair<C> au = ld2(acc1 + ou), ad = ld2(acc1 + od);
-    st2(acc1 + ou, cadd(au.a, tu[0]), cadd(au.b, tu[1]));
-    st2(acc1 + od, cadd(ad.a, td[0]), cadd(ad.b, td[1]));
+    st(Tout, ou, tu[0], tu[1]);
+    st(Tout, od, td[0], td[1]);
+    const Pair<C> au = ld(acc1, ou), ad = ld(acc1, od);
+    st(acc1, ou, cadd(au.a, tu[0]), cadd(au.b, tu[1]));
+    st(acc1, od, cadd(ad.a, td[0]), cadd(ad.b, td[1]));
     return;
   }
   const R cc = (R)ep.c, id = (R)ep.inv_delta;
@@ -103,24 +124,24 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
       sd[j] = cmake<C>(fct * (hd[j].x - cc * pd[j].x) * id, fct * (hd[j].y - cc * pd[j].y) * id);
     }
     if (Tkm1) {
-      const Pair<C> qu = ld2(Tkm1 + ou), qd = ld2(Tkm1 + od);
+      const Pair<C> qu = ld(Tkm1, ou), qd = ld(Tkm1, od);
       su[0] = csub(su[0], qu.a); su[1] = csub(su[1], qu.b);
       sd[0] = csub(sd[0], qd.a); sd[1] = csub(sd[1], qd.b);
     }
     if (ep.use_acc1) {
-      const Pair<C> yu = ld2(acc1 + ou), yd = ld2(acc1 + od);
+      const Pair<C> yu = ld(acc1, ou), yd = ld(acc1, od);
       const R ar = (R)ep.a1[0], ai = (R)ep.a1[1];
       su[0] = cadd(su[0], cmulr(yu.a, ar, ai)); su[1] = cadd(su[1], cmulr(yu.b, ar, ai));
       sd[0] = cadd(sd[0], cmulr(yd.a, ar, ai)); sd[1] = cadd(sd[1], cmulr(yd.b, ar, ai));
     }
     if (ep.use_acc2) {
-      const Pair<C> yu = ld2(acc2 + ou), yd = ld2(acc2 + od);
+      const Pair<C> yu = ld(acc2, ou), yd = ld(acc2, od);
       const R br = (R)ep.b1[0], bi = (R)ep.b1[1];
       su[0] = cadd(su[0], cmulr(yu.a, br, bi)); su[1] = cadd(su[1], cmulr(yu.b, br, bi));
       sd[0] = cadd(sd[0], cmulr(yd.a, br, bi)); sd[1] = cadd(sd[1], cmulr(yd.b, br, bi));
     }
-    st2(Tout + ou, su[0], su[1]);
-    st2(Tout + od, sd[0], sd[1]);
+    st(Tout, ou, su[0], su[1]);
+    st(Tout, od, sd[0], sd[1]);
     return;
   }
   const bool first = ep.mode == EPI_FIRST;
@@ -137,8 +158,8 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
       td[j] = cmake<C>((R)2 * (hd[j].x - cc * pd[j].x) * id - qds[j].x, (R)2 * (hd[j].y - cc * pd[j].y) * id - qds[j].y);
     }
   }
-  st2(Tout + ou, tu[0], tu[1]);
-  st2(Tout + od, td[0], td[1]);
+  st(Tout, ou, tu[0], tu[1]);
+  st(Tout, od, td[0], td[1]);
   // Accumulators take up to three terms at once (T_{k-1}, T_k, T_{k+1}, all in registers here),
   // so the host updates each of them on every third term only.
   auto upd = [&](C* acc, int init, const Pair<C>& au, const Pair<C>& ad, const double* cm, const double* c0,
@@ -158,18 +179,23 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
       nu[0] = cadd(nu[0], au.a); nu[1] = cadd(nu[1], au.b);
       nd[0] = cadd(nd[0], ad.a); nd[1] = cadd(nd[1], ad.b);
     }
-    st2(acc + ou, nu[0], nu[1]);
-    st2(acc + od, nd[0], nd[1]);
+    st(acc, ou, nu[0], nu[1]);
+    st(acc, od, nd[0], nd[1]);
   };
   if (use1) upd(acc1, ep.init1, au1, ad1, ep.am, ep.a0, ep.a1);
   if (use2) upd(acc2, ep.init2, au2, ad2, ep.bm, ep.b0, ep.b1);
 }
 
-template <typename R, int NLM, typename... A>
+template <typename R, int NLM, int SP, typename... A>
 static void epi_ak(int ak, dim3 grid, size_t smem, cudaStream_t st, A... args) {
-  if (ak == 0) k_epilogue<R, NLM, 0><<<grid, 256, smem, st>>>(args...);
-  else if (ak == 1) k_epilogue<R, NLM, 1><<<grid, 256, smem, st>>>(args...);
-  else k_epilogue<R, NLM, 2><<<grid, 256, smem, st>>>(args...);
+  if (ak == 0) k_epilogue<R, NLM, 0, SP><<<grid, 256, smem, st>>>(args...);
+  else if (ak == 1) k_epilogue<R, NLM, 1, SP><<<grid, 256, smem, st>>>(args...);
+  else k_epilogue<R, NLM, 2, SP><<<grid, 256, smem, st>>>(args...);
+}
+template <typename R, int NLM, typename... A>
+static void epi_sp(bool sp, int ak, dim3 grid, size_t smem, cudaStream_t st, A... args) {
+  if (sp) epi_ak<R, NLM, 1>(ak, grid, smem, st, args...);
+  else epi_ak<R, NLM, 0>(ak, grid, smem, st, args...);
 }
 
 template <typename R>
@@ -178,20 +204,22 @@ cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void*
                             const EpiParams& ep) {
   using C = typename CT<R>::type;
   const size_t N3 = (size_t)N * N * N;
-  dim3 grid((unsigned)((N3 / 2 + 255) / 256), nkb);
+  // spinor pairs need an even number of states, so that a pair shares its k-point
+  const bool sp = ep.spinor_pairs && ep.nstates % 2 == 0 && nkb % 2 == 0;
+  dim3 grid((unsigned)(sp ? (N3 + 255) / 256 : (N3 / 2 + 255) / 256), sp ? nkb / 2 : nkb);
   const int nlm = pt.natoms > 0 ? pt.nlm : 0;
   EpiParams epx = ep;
-  const size_t dcb = (size_t)pt.natoms * 2 * nlm * sizeof(C);
-  epx.dc_staged = (nlm > 0 && dcb <= 16 * 1024) ? 1 : 0;
+  const size_t dcb = (size_t)pt.natoms * 2 * nlm * sizeof(C) * (sp ? 2 : 1);
+  epx.dc_staged = (nlm > 0 && dcb <= 32 * 1024) ? 1 : 0;
   const size_t smem = epx.dc_staged ? dcb : 0;
   const bool cheb = ep.mode == EPI_FIRST || ep.mode == EPI_RECUR;
   const int ak = !cheb ? 2 : (ep.use_acc2 ? 2 : (ep.use_acc1 ? 1 : 0));
 #define EPI_ARGS (const C*)kin, (const C*)Tk, (const C*)Tkm1, (C*)Tout, (C*)acc1, (C*)acc2, V, N3, pt, (const C*)dc, epx
   switch (nlm) {
-    case 0: epi_ak<R, 0>(ak, grid, smem, st, EPI_ARGS); break;
-    case 1: epi_ak<R, 1>(ak, grid, smem, st, EPI_ARGS); break;
-    case 4: epi_ak<R, 4>(ak, grid, smem, st, EPI_ARGS); break;
-    case 9: epi_ak<R, 9>(ak, grid, smem, st, EPI_ARGS); break;
+    case 0: epi_sp<R, 0>(sp, ak, grid, smem, st, EPI_ARGS); break;
+    case 1: epi_sp<R, 1>(sp, ak, grid, smem, st, EPI_ARGS); break;
+    case 4: epi_sp<R, 4>(sp, ak, grid, smem, st, EPI_ARGS); break;
+    case 9: epi_sp<R, 9>(sp, ak, grid, smem, st, EPI_ARGS); break;
     default: return cudaErrorInvalidValue;
   }
 #undef EPI_ARGS

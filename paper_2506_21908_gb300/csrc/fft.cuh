@@ -289,6 +289,11 @@ template <> struct TwoFactor<32> { static constexpr bool ok = true; static const
 template <> struct TwoFactor<48> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 6; };
 template <> struct TwoFactor<64> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 8; };
 
+// Row pitch of a two-factor xy plane in shared memory: congruent to 8 modulo 16 elements, so that
+// the in-row exchange (8 lanes per row, columns rotated by K0) and the column accesses are both
+// free of bank conflicts.
+template <int N> struct TFPitch { static constexpr int value = (N % 16 == 8) ? N : (N % 16 == 0 ? N + 8 : N + 1); };
+
 // A side, forward: v[n1] = x[n0 + R1 n1] -> v[K0] = E[K0][n0].
 template <typename C, int N, bool INV> struct TF;
 template <typename C, int N> struct TF<C, N, false> {

@@ -39,6 +39,7 @@ struct EpiParams {
   double shift[kMaxK][3];       // k + A(t), for projector phases
   int nstates;
   int dc_staged;                // fused kernel: D c copied to shared memory (set by its launcher)
+  int spinor_pairs;             // epilogue: one point of two spinors per thread (even nstates)
 };
 
 // Device-side projector tables.
@@ -62,6 +63,12 @@ template <typename R> struct ProjTables {
 // ---------------------------------------------------------------- launchers
 template <typename R>
 cudaError_t launch_fft_xy(cudaStream_t st, int N, const void* src, void* dst, int nbatch, const void* tw, bool inv);
+// FP32 xy pass over persistent CTAs whose planes arrive by bulk asynchronous copies into
+// double-buffered shared memory (two-factor sizes; src 16-byte aligned; src == dst allowed).
+// err: bit 2 is set when a copy wait gave up.
+bool fft_xy_tma_supported(int N);
+cudaError_t launch_fft_xy_tma(cudaStream_t st, int N, const void* src, void* dst, int nbatch, const void* tw, bool inv,
+                              int* err);
 template <typename R>
 cudaError_t launch_fft_z(cudaStream_t st, int N, void* data, int nbatch, const void* tw, int mode,
                          const ZParams& zp);

@@ -104,5 +104,48 @@ __device__ __forceinline__ void h_point(typename CT<R>::type& hu, typename CT<R>
 }
 
 
+// The same for one point of two spinors of one k-point (index g = 0, 1): the projector entries
+// of the point, their beta values and phases are evaluated once for both spinors.
+template <typename R, int NLM>
+__device__ __forceinline__ void h_point_2sp(typename CT<R>::type (&hu)[2], typename CT<R>::type (&hd)[2],
+                                            const typename CT<R>::type (&pu)[2], const typename CT<R>::type (&pd)[2],
+                                            R V0, R V1, R hx, R hy, size_t r, const ProjTables<R>& pt,
+                                            const typename CT<R>::type* dcb0, const typename CT<R>::type* dcb1, R sx,
+                                            R sy, R sz) {
+  using C = typename CT<R>::type;
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    hu[g] = cmake<C>(hu[g].x + V0 * pu[g].x + hx * pd[g].x - hy * pd[g].y,
+                     hu[g].y + V0 * pu[g].y + hx * pd[g].y + hy * pd[g].x);
+    hd[g] = cmake<C>(hd[g].x + V1 * pd[g].x + hx * pu[g].x + hy * pu[g].y,
+                     hd[g].y + V1 * pd[g].y + hx * pu[g].y - hy * pu[g].x);
+  }
+  if constexpr (NLM > 0) {
+    const int e0 = pt.s_ptr[r], e1 = pt.s_ptr[r + 1];
+    for (int e = e0; e < e1; ++e) {
+      const int a = pt.s_atom[e];
+      R t[4], nl[4], bt[NLM];
+      load_row<R, 4>(pt.s_row + (size_t)e * 4, t);
+      load_row<R, 4>(pt.nrm + (size_t)a * 4, nl);
+      beta_values<R, NLM>(t[0], t[1], t[2], t[3], nl, pt.yc, bt);
+      R sn, cs;
+      phase_sincos(sx * t[0] + sy * t[1] + sz * t[2], &sn, &cs);
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const C* dca = (g ? dcb1 : dcb0) + (size_t)a * 2 * NLM;
+        R vux = 0, vuy = 0, vdx = 0, vdy = 0;
+#pragma unroll
+        for (int p = 0; p < NLM; ++p) {
+          const R bp = bt[p];
+          const Pair<C> cc = ld2(dca + 2 * p);
+          vux += bp * cc.a.x; vuy += bp * cc.a.y;
+          vdx += bp * cc.b.x; vdy += bp * cc.b.y;
+        }
+        hu[g].x += vux * cs + vuy * sn; hu[g].y += vuy * cs - vux * sn;
+        hd[g].x += vdx * cs + vdy * sn; hd[g].y += vdy * cs - vdx * sn;
+      }
+    }
+  }
+}
 
 }  // namespace tddft

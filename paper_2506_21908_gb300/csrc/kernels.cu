@@ -108,15 +108,14 @@ k_fft_z(typename CT<R>::type* __restrict__ data, const typename CT<R>::type* __r
 }
 
 // ---------------------------------------------------------------- two-factor passes (N = R1 R2)
-//
-// Row pitch of the xy plane: congruent to 8 modulo 16 elements, so that the in-row exchange
-// (8 lanes per row, rotated columns) and the column accesses are both free of bank conflicts.
-template <int N> struct TFPitch { static constexpr int value = (N % 16 == 8) ? N : (N % 16 == 0 ? N + 8 : N + 1); };
 
 // xy transform of one z-plane with one shared-memory exchange per axis: the x transform's A side
 // reads global memory directly, the y transform's B side writes it directly (forward); the
 // inverse runs the steps in the opposite order.  Column of the in-row exchange: K0 R1 + (n0 +
 // K0) mod R1 (a rotation, so that the 8 lanes of a row hit distinct banks on both sides).
+// Barriers: the y A side reads and writes the same rows of its item (n0 + R1 q = K0 R1 + n0)
+// and runs in place without one; the x sides touch one row per item group, whose items sit on
+// neighbouring lanes of a warp when their count divides 32, so a warp barrier orders them.
 template <typename R, int N, bool INV>
 __global__ void __launch_bounds__(FFTThreads<N>::value, FFTMinBlocks<R, N>::value)
 k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const typename CT<R>::type* __restrict__ twg) {
@@ -127,6 +126,9 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
   constexpr int RS = TFPitch<N>::value;
   constexpr int IA = N * R1, IB = N * R2;                 // A / B items of one axis
   constexpr int PA = (IA + NT - 1) / NT, PB = (IB + NT - 1) / NT;
+  constexpr bool ROW1 = (32 % R1 == 0) && (NT % R1 == 0);  // x A-side rows within a warp
+  constexpr bool ROW2 = (32 % R2 == 0) && (NT % R2 == 0);  // x B-side rows within a warp
+  constexpr bool ROW12 = ROW1 && R1 == R2;                 // and on the same lanes for both sides
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s = tw + N;
@@ -151,7 +153,7 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
         for (int k0 = 0; k0 < R2; ++k0) s[y * RS + k0 * R1 + (n0 + k0) % R1] = v[p][k0];
       }
     }
-    __syncthreads();
+    if constexpr (ROW12) __syncwarp(); else __syncthreads();
     // x, B side: item (y, K0)
 #pragma unroll
     for (int p = 0; p < PB; ++p) {
@@ -162,7 +164,7 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
         for (int n0 = 0; n0 < R1; ++n0) u[p][n0] = s[y * RS + k0 * R1 + (n0 + k0) % R1];
       }
     }
-    __syncthreads();
+    if constexpr (ROW2) __syncwarp(); else __syncthreads();
 #pragma unroll
     for (int p = 0; p < PB; ++p) {
       const int i = threadIdx.x + p * NT;
@@ -174,7 +176,7 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
       }
     }
     __syncthreads();
-    // y, A side: item (x, n0), x fastest
+    // y, A side in place: item (x, n0), x fastest; rows n0 + R1 q in, K0 R1 + n0 out (the same)
 #pragma unroll
     for (int p = 0; p < PA; ++p) {
       const int i = threadIdx.x + p * NT;
@@ -183,14 +185,6 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
 #pragma unroll
         for (int q = 0; q < R2; ++q) v[p][q] = s[(n0 + R1 * q) * RS + x];
         T::a_side(v[p], n0, tw);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PA; ++p) {
-      const int i = threadIdx.x + p * NT;
-      if (IA % NT == 0 || i < IA) {
-        const int n0 = i / N, x = i - n0 * N;
 #pragma unroll
         for (int k0 = 0; k0 < R2; ++k0) s[(k0 * R1 + n0) * RS + x] = v[p][k0];
       }
@@ -224,7 +218,7 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
       }
     }
     __syncthreads();
-    // y, A side: item (x, n0)
+    // y, A side in place: item (x, n0)
 #pragma unroll
     for (int p = 0; p < PA; ++p) {
       const int i = threadIdx.x + p * NT;
@@ -233,14 +227,6 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
 #pragma unroll
         for (int k0 = 0; k0 < R2; ++k0) v[p][k0] = s[(k0 * R1 + n0) * RS + x];
         T::a_side(v[p], n0, tw);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PA; ++p) {
-      const int i = threadIdx.x + p * NT;
-      if (IA % NT == 0 || i < IA) {
-        const int n0 = i / N, x = i - n0 * N;
 #pragma unroll
         for (int n1 = 0; n1 < R2; ++n1) s[(n0 + R1 * n1) * RS + x] = v[p][n1];
       }
@@ -256,7 +242,7 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
         for (int k1 = 0; k1 < R1; ++k1) u[p][k1] = s[y * RS + k0 + R2 * k1];
       }
     }
-    __syncthreads();
+    if constexpr (ROW2) __syncwarp(); else __syncthreads();
 #pragma unroll
     for (int p = 0; p < PB; ++p) {
       const int i = threadIdx.x + p * NT;
@@ -267,7 +253,7 @@ k_fft_xy2(const typename CT<R>::type* src, typename CT<R>::type* dst, const type
         for (int n0 = 0; n0 < R1; ++n0) s[y * RS + k0 * R1 + (n0 + k0) % R1] = u[p][n0];
       }
     }
-    __syncthreads();
+    if constexpr (ROW12) __syncwarp(); else __syncthreads();
     // x, A side -> global: item (y, n0)
 #pragma unroll
     for (int p = 0; p < PA; ++p) {

@@ -432,3 +432,44 @@ def test_gather_overlap_gives_identical_bits(lib, precision, monkeypatch):
         outs.append(h.get_states())
         h.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("n", [16, 24, 32, 48, 64])
+def test_bulk_copy_xy_pass_gives_identical_bits(lib, n, monkeypatch):
+    """FP32 xy passes fed by bulk asynchronous copies (double-buffered planes in shared memory)
+    against the register-fed passes (TDDFT_NO_TMA=1): the same DFT arithmetic in the same order,
+    so the states agree bit for bit, and no copy wait reports a timeout."""
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=n, nstates=3, nk=2, natoms=2)
+    psi0 = S.small_parity_states(wl)
+    outs = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("TDDFT_NO_TMA", flag)
+        h = _lib.TDDFT.from_workload(wl, precision=1)
+        h.set_fields(wl.times, wl.A, wl.B)
+        h.set_states(psi0, 0.0)
+        h.step(2)
+        h.observables()
+        outs.append(h.get_states())
+        h.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-6)])
+def test_spinor_pair_epilogue_matches_single_spinor_form(lib, precision, tol, monkeypatch):
+    """Epilogue threads holding one grid point of two spinors (the projector scatter walks the
+    point's entries once for the pair) against two points of one spinor (TDDFT_NO_EPI_PAIRS=1):
+    the same arithmetic per spinor and point, so the states agree to rounding."""
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=4, nk=2, natoms=3)
+    psi0 = S.small_parity_states(wl)
+    outs = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("TDDFT_NO_EPI_PAIRS", flag)
+        h = _lib.TDDFT.from_workload(wl, precision=precision)
+        h.set_fields(wl.times, wl.A, wl.B)
+        h.set_states(psi0, 0.0)
+        h.step(3)
+        outs.append(h.get_states())
+        h.close()
+    assert rel(outs[0], outs[1]) <= tol
