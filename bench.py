@@ -141,7 +141,7 @@ def time_oracle(nbands, steps, warm=0):
 # the parameter structs they take).
 KERNEL_SOURCES = {
     "epilogue": ("epilogue.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
-    "fft_xy": ("kernels.cu", "fft_tma.cu", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+    "fft_xy": ("kernels.cu", "fft_tma.cu", "bulk.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
     "fft_z_kinetic": ("kernels.cu", "kin_cluster.cu", "fft.cuh", "impl.cuh", "kcommon.cuh"),
     "proj_gather": ("kernels.cu", "proj_tc.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
 }

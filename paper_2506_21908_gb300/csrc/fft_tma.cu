@@ -18,6 +18,7 @@
 // buffer holds; every index stays in bounds, and the host reports the flag.
 #include <cstdint>
 
+#include "bulk.cuh"
 #include "fft.cuh"
 #include "impl.cuh"
 #include "kcommon.cuh"
@@ -26,56 +27,15 @@ namespace tddft {
 
 namespace {
 
-constexpr unsigned XY_WAIT_LIMIT = 1u << 26;
-
-__device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool xy_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned it = 0; it < XY_WAIT_LIMIT; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
 // N rows of N complex values (row r at g + r * stride) into a buffer with row pitch P; called by
 // the 32 lanes of warp 0.  Row bytes N * 8, the pitch P * 8 and the row addresses are
 // multiples of 16 for every size used here (N even).
 template <int N, int P>
 __device__ __forceinline__ void issue_rows(const float2* g, size_t stride, float2* buf, uint32_t bar, int lane) {
   constexpr uint32_t ROW = N * sizeof(float2);
-  if (lane == 0) {
-    // shared-memory reads of this buffer by the generic proxy happened before the CTA barrier
-    // that precedes this call; order them before the asynchronous proxy's writes
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(ROW * N) : "memory");
-  }
+  if (lane == 0) bulk_expect(bar, ROW * N);
   __syncwarp();
-  for (int row = lane; row < N; row += 32)
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            sm_addr(buf + row * P)),
-        "l"(g + (size_t)row * stride), "r"(ROW), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void init_bars(uint32_t bar0, uint32_t bar1) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1));
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1));
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void wait_buffer(uint32_t bar, uint32_t parity, int* err) {
-  if (!xy_wait(bar, parity)) {
-    atomicOr(err, 2);
-    xy_wait(bar, parity);
-  }
+  for (int row = lane; row < N; row += 32) bulk_copy(buf + row * P, g + (size_t)row * stride, ROW, bar);
 }
 
 // Threads and resident CTAs: 256 threads; the two 36 KB buffers of a 64^2 plane allow three
@@ -113,7 +73,7 @@ k_fft_xy2_tma(const float2* src, float2* dst, const float2* __restrict__ twg, in
   uint64_t* bars = reinterpret_cast<uint64_t*>(buf1 + N * RS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t bar0 = sm_addr(&bars[0]), bar1 = sm_addr(&bars[1]);
-  if (threadIdx.x == 0) init_bars(bar0, bar1);
+  if (threadIdx.x == 0) bulk_init(bar0, bar1);
   for (int i = threadIdx.x; i < N; i += NT) tw[i] = twg[i];
   __syncthreads();
   int pl = blockIdx.x;
@@ -127,7 +87,7 @@ k_fft_xy2_tma(const float2* src, float2* dst, const float2* __restrict__ twg, in
     C* s = sb ? buf1 : buf0;
     const int nx = pl + gridDim.x;
     if (nx < nplanes && warp == 0) issue_rows<N, RS>(src + (size_t)nx * N * N, N, sb ? buf0 : buf1, sb ? bar0 : bar1, lane);
-    wait_buffer(sb ? bar1 : bar0, (uint32_t)(it >> 1) & 1u, err);
+    bulk_wait(sb ? bar1 : bar0, (uint32_t)(it >> 1) & 1u, err, 2);
     C* o = dst + (size_t)pl * N * N;
     if (!INV) {
       // x, A side in place: item (y, n0); a row's items share a warp
