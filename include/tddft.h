@@ -177,6 +177,13 @@ tddft_status tddft_set_states(tddft_handle h, const void* psi, int on_device, do
 /* Copy the current spinors out as complex128 (layout above). */
 tddft_status tddft_get_states(tddft_handle h, void* psi, int on_device);
 
+/* The same two calls with complex64 spinors (interleaved float pairs, same layout).  An
+ * FP32-mixed handle stores its spinors in this form, so loading moves half the bytes of the
+ * complex128 call and converts nothing; an FP64 handle widens them exactly.  Host buffers may be
+ * pageable or page-locked. */
+tddft_status tddft_set_states_c64(tddft_handle h, const void* psi, int on_device, double t0);
+tddft_status tddft_get_states_c64(tddft_handle h, void* psi, int on_device);
+
 /* Advance nsteps ETRS steps (asynchronous on the handle's stream). */
 tddft_status tddft_step(tddft_handle h, int nsteps);
 

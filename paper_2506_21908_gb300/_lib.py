@@ -24,7 +24,8 @@ KERNEL_CLASSES = ["fft_xy", "fft_z_kinetic", "epilogue", "proj_gather", "density
 EXPORTS = ["tddft_create", "tddft_set_fields", "tddft_set_states", "tddft_get_states", "tddft_step",
            "tddft_observables", "tddft_get_potential", "tddft_apply_hamiltonian", "tddft_set_stream",
            "tddft_info", "tddft_profile", "tddft_profile_read", "tddft_last_error", "tddft_destroy",
-           "tddft_hartree_noalloc", "tddft_backward", "tddft_atom_moments", "tddft_torques"]
+           "tddft_hartree_noalloc", "tddft_backward", "tddft_atom_moments", "tddft_torques",
+           "tddft_set_states_c64", "tddft_get_states_c64"]
 
 
 class TddftError(RuntimeError):
@@ -77,6 +78,8 @@ def load(path=LIB_PATH):
         "tddft_set_fields": [vp, i, vp, vp, vp],
         "tddft_set_states": [vp, vp, i, d],
         "tddft_get_states": [vp, vp, i],
+        "tddft_set_states_c64": [vp, vp, i, d],
+        "tddft_get_states_c64": [vp, vp, i],
         "tddft_step": [vp, i],
         "tddft_observables": [vp, vp, vp, vp, vp, vp],
         "tddft_get_potential": [vp, vp],
@@ -195,23 +198,33 @@ class TDDFT:
         return hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)
 
     def _spinor_arg(self, psi):
+        """(array, on_device, complex64?) for a spinor array: CUDA tensors and complex64 host
+        arrays are passed as they are (complex64 through the *_c64 calls); anything else is made
+        a contiguous complex128 host array."""
         if self._is_dev(psi):
-            assert psi.is_contiguous() and str(psi.dtype) == "torch.complex128", "need contiguous complex128"
+            c64 = str(psi.dtype) == "torch.complex64"
+            assert psi.is_contiguous() and (c64 or str(psi.dtype) == "torch.complex128"), \
+                "need a contiguous complex64 or complex128 tensor"
             assert psi.numel() == int(np.prod(self.psi_shape))
-            return psi, 1
-        arr = np.ascontiguousarray(psi, dtype=np.complex128)
+            return psi, 1, c64
+        c64 = str(getattr(psi, "dtype", "")) in ("complex64", "torch.complex64")
+        arr = np.ascontiguousarray(psi, dtype=np.complex64 if c64 else np.complex128)
         assert arr.size == int(np.prod(self.psi_shape)), "spinor array has the wrong size"
-        return arr, 0
+        return arr, 0, c64
 
     def set_states(self, psi, t0=0.0):
-        arr, dev = self._spinor_arg(psi)
-        self._check(self.lib.tddft_set_states(self.h, _ptr(arr), dev, float(t0)))
+        arr, dev, c64 = self._spinor_arg(psi)
+        fn = self.lib.tddft_set_states_c64 if c64 else self.lib.tddft_set_states
+        self._check(fn(self.h, _ptr(arr), dev, float(t0)))
 
     def get_states(self, out=None):
         if out is None:
             out = np.empty(self.psi_shape, np.complex128)
-        arr, dev = self._spinor_arg(out)
-        self._check(self.lib.tddft_get_states(self.h, _ptr(arr), dev))
+        arr, dev, c64 = self._spinor_arg(out)
+        fn = self.lib.tddft_get_states_c64 if c64 else self.lib.tddft_get_states
+        self._check(fn(self.h, _ptr(arr), dev))
+        if isinstance(out, np.ndarray) and arr is not out:
+            np.copyto(out, arr.reshape(out.shape))
         return out
 
     def step(self, nsteps=1):
@@ -237,11 +250,13 @@ class TDDFT:
         return V
 
     def apply_hamiltonian(self, psi, out=None):
-        arr, dev = self._spinor_arg(psi)
+        arr, dev, c64 = self._spinor_arg(psi)
+        if c64 and not dev:
+            arr = arr.astype(np.complex128)
         if out is None:
             out = np.empty(self.psi_shape, np.complex128)
-        oarr, odev = self._spinor_arg(out)
-        assert odev == dev
+        oarr, odev, oc64 = self._spinor_arg(out)
+        assert odev == dev and not (dev and c64) and not oc64, "H apply takes complex128 arrays on one side"
         self._check(self.lib.tddft_apply_hamiltonian(self.h, _ptr(arr), _ptr(oarr), dev))
         return out
 

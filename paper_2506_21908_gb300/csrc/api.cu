@@ -1307,10 +1307,46 @@ const void* mapped_host(const void* p) {
   return (at.type == cudaMemoryTypeHost && at.devicePointer) ? at.devicePointer : nullptr;
 }
 
-template <typename R> tddft_status do_set_states(tddft_ctx* c, const void* psi, int on_device, double t0) {
+// complex64 spinors in: a plain copy for FP32-mixed handles, an exact widening for FP64 ones
+// (through the mapped address of page-locked memory, or staged in the work array Ta).
+tddft_status load_states_c64(tddft_ctx* c, const void* psi, int on_device) {
+  const size_t n = c->psi_elems();
+  if (c->prec != TDDFT_FP64)
+    return c->cuda(cudaMemcpyAsync(c->psi, psi, n * sizeof(float2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st),
+                   "set_states_c64 copy");
+  const void* src = on_device ? psi : mapped_host(psi);
+  tddft_status s;
+  if (!src) {
+    if ((s = c->cuda(cudaMemcpyAsync(c->Ta, psi, n * sizeof(float2), cudaMemcpyHostToDevice, c->st), "set_states_c64 stage")))
+      return s;
+    src = c->Ta;
+  }
+  return c->launch(KC_OTHER, "widen in", [&] { return launch_convert_out<float>(c->st, n, src, (double2*)c->psi); });
+}
+
+tddft_status store_states_c64(tddft_ctx* c, void* out, int on_device) {
   const size_t n = c->psi_elems();
   tddft_status s;
-  if (c->prec == TDDFT_FP64) {
+  if (c->prec != TDDFT_FP64) {
+    if ((s = c->cuda(cudaMemcpyAsync(out, c->psi, n * sizeof(float2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st),
+                     "get_states_c64 copy")))
+      return s;
+  } else if (void* dst = on_device ? out : const_cast<void*>(mapped_host(out))) {
+    if ((s = c->launch(KC_OTHER, "narrow out", [&] { return launch_convert_in<float>(c->st, n, (const double2*)c->psi, dst); }))) return s;
+  } else {
+    if ((s = c->launch(KC_OTHER, "narrow out", [&] { return launch_convert_in<float>(c->st, n, (const double2*)c->psi, c->Ta); })) ||
+        (s = c->cuda(cudaMemcpyAsync(out, c->Ta, n * sizeof(float2), cudaMemcpyDeviceToHost, c->st), "get_states_c64 stage")))
+      return s;
+  }
+  return c->cuda(cudaStreamSynchronize(c->st), "get_states_c64 sync");
+}
+
+template <typename R> tddft_status do_set_states(tddft_ctx* c, const void* psi, int on_device, double t0, bool c64 = false) {
+  const size_t n = c->psi_elems();
+  tddft_status s;
+  if (c64) {
+    if ((s = load_states_c64(c, psi, on_device))) return s;
+  } else if (c->prec == TDDFT_FP64) {
     if ((s = c->cuda(cudaMemcpyAsync(c->psi, psi, n * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st), "set_states copy"))) return s;
   } else if (const void* src = on_device ? psi : mapped_host(psi)) {
     if ((s = c->launch(KC_OTHER, "convert in", [&] { return launch_convert_in<R>(c->st, n, (const double2*)src, c->psi); }))) return s;
@@ -1341,18 +1377,12 @@ template <typename R> tddft_status do_set_states(tddft_ctx* c, const void* psi, 
   }
   (void)Atab; (void)Btab;
   if (c->emin_user == 0.0 && c->emax_user == 0.0) {
-    std::vector<double> Vh(4 * c->N3);
-    if ((s = c->cuda(cudaMemcpyAsync(Vh.data(), c->V, Vh.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st), "window read"))) return s;
-    if ((s = c->cuda(cudaStreamSynchronize(c->st), "window sync"))) return s;
-    double vmin = 1e300, vmax = -1e300, bmax = 0.0;
-    const size_t N3 = c->N3;
-    for (size_t r = 0; r < N3; ++r) {
-      const double v = 0.5 * (Vh[r] + Vh[N3 + r]);
-      const double bz = 0.5 * (Vh[r] - Vh[N3 + r]), bx = 0.5 * Vh[2 * N3 + r], by = 0.5 * Vh[3 * N3 + r];
-      vmin = std::min(vmin, v);
-      vmax = std::max(vmax, v);
-      bmax = std::max(bmax, std::sqrt(bx * bx + by * by + bz * bz));
-    }
+    double ext[3];
+    if ((s = c->launch(KC_OTHER, "window extrema", [&] { return launch_window_extrema(c->st, c->N3, c->V, c->red_part, c->red); })) ||
+        (s = c->cuda(cudaMemcpyAsync(ext, c->red, sizeof(ext), cudaMemcpyDeviceToHost, c->st), "window read")) ||
+        (s = c->cuda(cudaStreamSynchronize(c->st), "window sync")))
+      return s;
+    const double vmin = ext[0], vmax = ext[1], bmax = ext[2];
     double emin = vmin - bmax - c->nl_bound, emax = vmax + bmax + c->kin_max + c->nl_bound;
     const double w = emax - emin;
     c->emin = emin - 0.025 * w;
@@ -1395,9 +1425,10 @@ template <typename R> tddft_status do_observables(tddft_ctx* c, double* n, doubl
   double* kdots = dots + 2 * nkb;
   double* nle = kdots + 2 * nkb;
   if ((s = c->launch(KC_OTHER, "norms", [&] { return launch_band_dot<R>(c->st, 2 * c->N3, nkb, c->psi, c->psi, dots, c->red_part); }))) return s;
-  if ((s = kinetic<R>(c, c->psi, c->tmp, A))) return s;
-  if ((s = c->launch(KC_OTHER, "kinetic dot", [&] { return launch_band_dot<R>(c->st, 2 * c->N3, nkb, c->psi, c->tmp, kdots, c->red_part); }))) return s;
-  if (c->natoms > 0) {
+  // the kinetic and non-local energies only enter E: without E their passes are skipped
+  if (E && (s = kinetic<R>(c, c->psi, c->tmp, A))) return s;
+  if (E && (s = c->launch(KC_OTHER, "kinetic dot", [&] { return launch_band_dot<R>(c->st, 2 * c->N3, nkb, c->psi, c->tmp, kdots, c->red_part); }))) return s;
+  if (E && c->natoms > 0) {
     if ((s = gather<R>(c, c->psi, A))) return s;
     if ((s = c->launch(KC_OTHER, "nl energy", [&] { return launch_nl_energy<R>(c->st, nkb, c->natoms * 2 * c->nlm, c->cbuf, c->dcbuf, nle); }))) return s;
   }
@@ -1784,6 +1815,20 @@ tddft_status tddft_get_states(tddft_handle h, void* psi, int on_device) {
   if (!psi) return h->fail(TDDFT_ERR_ARG, "null psi");
   if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no states loaded");
   return h->prec == TDDFT_FP64 ? do_get_states<double>(h, psi, on_device) : do_get_states<float>(h, psi, on_device);
+}
+
+tddft_status tddft_set_states_c64(tddft_handle h, const void* psi, int on_device, double t0) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (!psi) return h->fail(TDDFT_ERR_ARG, "null psi");
+  return h->prec == TDDFT_FP64 ? do_set_states<double>(h, psi, on_device, t0, true)
+                               : do_set_states<float>(h, psi, on_device, t0, true);
+}
+
+tddft_status tddft_get_states_c64(tddft_handle h, void* psi, int on_device) {
+  if (!h) return TDDFT_ERR_ARG;
+  if (!psi) return h->fail(TDDFT_ERR_ARG, "null psi");
+  if (!h->have_states) return h->fail(TDDFT_ERR_STATE, "no states loaded");
+  return store_states_c64(h, psi, on_device);
 }
 
 tddft_status tddft_step(tddft_handle h, int nsteps) {

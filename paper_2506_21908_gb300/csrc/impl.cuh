@@ -121,6 +121,8 @@ size_t field_sums_part_doubles();
 cudaError_t launch_max_abs_diff(cudaStream_t st, size_t n, const double* a, const double* b, double* out);
 cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, double lo, double hi,
                                 double kin_max, double nl_bound, int* flag);
+// min v, max v, max |b| of the potential (out3); part: field_sums_part_doubles() scratch.
+cudaError_t launch_window_extrema(cudaStream_t st, size_t N3, const double* V, double* part, double* out3);
 
 // Tensor-core projector contraction (tcgen05 kind::tf32), FP32-mixed path, l <= 2.
 cudaError_t launch_proj_gather_tc(cudaStream_t st, int N, const void* psi, int nk, int nstates,

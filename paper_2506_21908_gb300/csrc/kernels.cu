@@ -751,24 +751,56 @@ cudaError_t launch_vloc_G(cudaStream_t st, int N, const double* L, int natoms, c
 
 // ============================================================================ conversions
 
+// Precision conversion of spinor arrays.  The source or destination may be page-locked host
+// memory read or written through its mapped address (over the CPU-GPU link), where the rate
+// depends on the requests in flight: each warp moves 8 x 32 consecutive elements, eight
+// independent 16-byte loads per thread, every load instruction covering 512 contiguous bytes.
+constexpr int kConvPerThread = 8;
+
 template <typename R>
-__global__ void k_convert_in(size_t n, const double2* __restrict__ in, typename CT<R>::type* __restrict__ out) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = cmake<typename CT<R>::type>((R)in[i].x, (R)in[i].y);
+__global__ void __launch_bounds__(256) k_convert_in(size_t n, const double2* __restrict__ in, typename CT<R>::type* __restrict__ out) {
+  using C = typename CT<R>::type;
+  const size_t base = (((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * kConvPerThread) + (threadIdx.x & 31);
+  double2 v[kConvPerThread];
+#pragma unroll
+  for (int q = 0; q < kConvPerThread; ++q) {
+    const size_t i = base + 32 * q;
+    if (i < n) v[q] = in[i];
+  }
+#pragma unroll
+  for (int q = 0; q < kConvPerThread; ++q) {
+    const size_t i = base + 32 * q;
+    if (i < n) out[i] = cmake<C>((R)v[q].x, (R)v[q].y);
+  }
 }
 template <typename R>
-__global__ void k_convert_out(size_t n, const typename CT<R>::type* __restrict__ in, double2* __restrict__ out) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = make_double2((double)in[i].x, (double)in[i].y);
+__global__ void __launch_bounds__(256) k_convert_out(size_t n, const typename CT<R>::type* __restrict__ in, double2* __restrict__ out) {
+  using C = typename CT<R>::type;
+  const size_t base = (((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 * kConvPerThread) + (threadIdx.x & 31);
+  C v[kConvPerThread];
+#pragma unroll
+  for (int q = 0; q < kConvPerThread; ++q) {
+    const size_t i = base + 32 * q;
+    if (i < n) v[q] = in[i];
+  }
+#pragma unroll
+  for (int q = 0; q < kConvPerThread; ++q) {
+    const size_t i = base + 32 * q;
+    if (i < n) out[i] = make_double2((double)v[q].x, (double)v[q].y);
+  }
 }
 template <typename R>
 cudaError_t launch_convert_in(cudaStream_t st, size_t n, const double2* in, void* out) {
-  k_convert_in<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, in, (typename CT<R>::type*)out);
+  if (n == 0) return cudaSuccess;
+  const size_t per_cta = 256 * kConvPerThread;
+  k_convert_in<R><<<(unsigned)((n + per_cta - 1) / per_cta), 256, 0, st>>>(n, in, (typename CT<R>::type*)out);
   return cudaGetLastError();
 }
 template <typename R>
 cudaError_t launch_convert_out(cudaStream_t st, size_t n, const void* in, double2* out) {
-  k_convert_out<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, (const typename CT<R>::type*)in, out);
+  if (n == 0) return cudaSuccess;
+  const size_t per_cta = 256 * kConvPerThread;
+  k_convert_out<R><<<(unsigned)((n + per_cta - 1) / per_cta), 256, 0, st>>>(n, (const typename CT<R>::type*)in, out);
   return cudaGetLastError();
 }
 
@@ -1003,6 +1035,59 @@ __global__ void k_check_window(size_t N3, const double* __restrict__ V, double l
 cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, double lo, double hi, double kin_max,
                                 double nl_bound, int* flag) {
   k_check_window<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, V, lo, hi, kin_max, nl_bound, flag);
+  return cudaGetLastError();
+}
+
+// Extrema of the local potential for the automatic spectral window: min and max of
+// v = (V_0 + V_1)/2 and max of |b| = |(V_2, V_3, V_0 - V_1)|/2 over the grid.  Products and sums
+// are rounded one by one (no fused multiply-add), as in a plain IEEE evaluation; min and max do
+// not depend on the order, so the result is exact.  Partials per block, then one block.
+__global__ void __launch_bounds__(256) k_window_part(size_t N3, const double* __restrict__ V, double* part) {
+  __shared__ double sh[3][8];
+  double vmin = 1e300, vmax = -1e300, bmax = 0.0;
+  for (size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x; r < N3; r += (size_t)gridDim.x * blockDim.x) {
+    const double v = __dmul_rn(0.5, __dadd_rn(V[r], V[N3 + r]));
+    const double bz = __dmul_rn(0.5, __dsub_rn(V[r], V[N3 + r]));
+    const double bx = __dmul_rn(0.5, V[2 * N3 + r]), by = __dmul_rn(0.5, V[3 * N3 + r]);
+    const double b = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz)));
+    vmin = fmin(vmin, v);
+    vmax = fmax(vmax, v);
+    bmax = fmax(bmax, b);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    vmin = fmin(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+    vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sh[0][warp] = vmin; sh[1][warp] = vmax; sh[2][warp] = bmax; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) {
+      vmin = fmin(vmin, sh[0][w]);
+      vmax = fmax(vmax, sh[1][w]);
+      bmax = fmax(bmax, sh[2][w]);
+    }
+    part[3 * blockIdx.x] = vmin;
+    part[3 * blockIdx.x + 1] = vmax;
+    part[3 * blockIdx.x + 2] = bmax;
+  }
+}
+__global__ void k_window_total(int nparts, const double* __restrict__ part, double* out) {
+  if (threadIdx.x != 0) return;
+  double vmin = 1e300, vmax = -1e300, bmax = 0.0;
+  for (int i = 0; i < nparts; ++i) {
+    vmin = fmin(vmin, part[3 * i]);
+    vmax = fmax(vmax, part[3 * i + 1]);
+    bmax = fmax(bmax, part[3 * i + 2]);
+  }
+  out[0] = vmin;
+  out[1] = vmax;
+  out[2] = bmax;
+}
+cudaError_t launch_window_extrema(cudaStream_t st, size_t N3, const double* V, double* part, double* out3) {
+  k_window_part<<<kFieldBlocks, 256, 0, st>>>(N3, V, part);
+  k_window_total<<<1, 32, 0, st>>>(kFieldBlocks, part, out3);
   return cudaGetLastError();
 }
 

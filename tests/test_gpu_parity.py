@@ -473,3 +473,29 @@ def test_spinor_pair_epilogue_matches_single_spinor_form(lib, precision, tol, mo
         outs.append(h.get_states())
         h.close()
     assert rel(outs[0], outs[1]) <= tol
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_complex64_state_calls(lib, precision):
+    """tddft_set_states_c64 / tddft_get_states_c64: an FP32-mixed handle keeps complex64 spinors
+    as they are, an FP64 handle widens them exactly; loading complex64 states (numpy, page-locked
+    and device tensors) and loading the same values as complex128 give the same states and the
+    same step."""
+    import torch
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=3, nk=2, natoms=2)
+    psi64 = S.small_parity_states(wl).astype(np.complex64)
+    outs = []
+    for src in (psi64, psi64.astype(np.complex128), torch.from_numpy(psi64).pin_memory(),
+                torch.from_numpy(psi64).to("cuda")):
+        h = _lib.TDDFT.from_workload(wl, precision=precision)
+        h.set_fields(wl.times, wl.A, wl.B)
+        h.set_states(src, 0.0)
+        assert np.array_equal(h.get_states(), psi64.astype(np.complex128))
+        assert np.array_equal(h.get_states(np.empty(psi64.shape, np.complex64)), psi64)
+        h.step(2)
+        outs.append((h.get_states(), h.get_states(np.empty(psi64.shape, np.complex64))))
+        h.close()
+    for o128, o64 in outs[1:]:
+        assert np.array_equal(o128, outs[0][0]) and np.array_equal(o64, outs[0][1])
+    assert np.array_equal(outs[0][1], outs[0][0].astype(np.complex64))
