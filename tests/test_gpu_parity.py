@@ -499,3 +499,22 @@ def test_complex64_state_calls(lib, precision):
     for o128, o64 in outs[1:]:
         assert np.array_equal(o128, outs[0][0]) and np.array_equal(o64, outs[0][1])
     assert np.array_equal(outs[0][1], outs[0][0].astype(np.complex64))
+
+
+def test_observables_without_energies_match_full_call(lib):
+    """tddft_observables with E, M and norms NULL skips the energy passes; n and m agree bit for
+    bit with the full call."""
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=3, nk=2, natoms=2)
+    psi0 = S.small_parity_states(wl)
+    h = _lib.TDDFT.from_workload(wl, precision=1)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi0, 0.0)
+    h.step(2)
+    n_full, m_full, E, _ = h.observables()
+    n = np.empty_like(n_full)
+    m = np.empty_like(m_full)
+    assert h.lib.tddft_observables(h.h, _lib._ptr(n), _lib._ptr(m), None, None, None) == 0
+    h.close()
+    assert np.array_equal(n, n_full) and np.array_equal(m, m_full)
+    assert np.isfinite(E["total"])
