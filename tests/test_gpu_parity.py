@@ -518,3 +518,28 @@ def test_observables_without_energies_match_full_call(lib):
     h.close()
     assert np.array_equal(n, n_full) and np.array_equal(m, m_full)
     assert np.isfinite(E["total"])
+
+
+@pytest.mark.parametrize("lmax", [0, 1])
+@pytest.mark.parametrize("nstates", [3, 4])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lower_angular_momentum_projectors(lib, lmax, nstates, precision):
+    """Projectors up to l = 0 and l = 1 (1 and 4 real harmonics per spin): H apply against the
+    oracle, and three steps against the oracle's n and m, with an odd (two points of one spinor
+    per epilogue thread) and an even (one point of two spinors) number of states."""
+    from paper_2506_21908_gb300 import _lib
+    wl = S.small_parity(n=16, nstates=nstates, nk=2, natoms=3, lmax=lmax)
+    psi0 = S.small_parity_states(wl)
+    h = _lib.TDDFT.from_workload(wl, precision=precision, e_min=-20, e_max=100)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi0, 0.1)
+    hpsi = h.apply_hamiltonian(psi0)
+    h.close()
+    s = System.from_workload(wl)
+    o = Oracle(s, FieldTable(wl.times, wl.A, wl.B), wl.dt, psi0, t0=0.1, bounds=(-20, 100))
+    A, _ = o.f.at(0.1)
+    assert rel(hpsi, s.apply_h(psi0, o.V, A)) <= (1e-12 if precision == 0 else 2e-5)
+    rows, psi_g, o = run_pair(lib, wl, psi0, 3, (-20.0, 100.0), precision=precision)
+    tol = 1e-10 if precision == 0 else 2e-5
+    for r in rows:
+        assert r["n"] <= tol and r["m"] <= tol, r
