@@ -1441,10 +1441,15 @@ template <typename R> tddft_status do_observables(tddft_ctx* c, double* n, doubl
   if ((s = c->cuda(cudaMemcpyAsync(h.data(), c->red, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st), "obs read"))) return s;
   if ((s = c->cuda(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "flag read"))) return s;
   if ((s = c->cuda(cudaMemcpyAsync(&tcflag, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st), "tc flag read"))) return s;
-  std::vector<double> rho_h;
   if (n || m) {
-    rho_h.resize(4 * c->N3);
-    if ((s = c->cuda(cudaMemcpyAsync(rho_h.data(), c->rho, rho_h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st), "rho read"))) return s;
+    // n and m are formed on the device in the step scratch rho2 (free between steps) and copied
+    // straight into the caller's arrays
+    const size_t N3 = c->N3;
+    if ((s = c->launch(KC_OTHER, "n, m", [&] { return launch_nm_from_rho(c->st, N3, c->rho, c->rho2); }))) return s;
+    if (n && (s = c->cuda(cudaMemcpyAsync(n, c->rho2, N3 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "n read")))
+      return s;
+    if (m && (s = c->cuda(cudaMemcpyAsync(m, c->rho2 + N3, 3 * N3 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "m read")))
+      return s;
   }
   if ((s = c->cuda(cudaStreamSynchronize(c->st), "obs sync"))) return s;
   double ekin = 0, enl = 0;
@@ -1471,15 +1476,6 @@ template <typename R> tddft_status do_observables(tddft_ctx* c, double* n, doubl
   }
   if (M)
     for (int a = 0; a < 3; ++a) M[a] = h[3 + a] * c->dV;
-  const size_t N3 = c->N3;
-  if (n)
-    for (size_t r = 0; r < N3; ++r) n[r] = rho_h[r] + rho_h[N3 + r];
-  if (m)
-    for (size_t r = 0; r < N3; ++r) {
-      m[r] = 2.0 * rho_h[2 * N3 + r];
-      m[N3 + r] = -2.0 * rho_h[3 * N3 + r];
-      m[2 * N3 + r] = rho_h[r] - rho_h[N3 + r];
-    }
   if (tcflag & 1) return c->fail(TDDFT_ERR_CUDA, "a tensor-core projector wait exceeded its iteration limit");
   if (tcflag & 2) return c->fail(TDDFT_ERR_CUDA, "a bulk-copy wait of an FFT pass exceeded its iteration limit");
   if (bad) return c->fail(TDDFT_ERR_DIVERGED, "non-finite density or norm");

@@ -121,6 +121,8 @@ size_t field_sums_part_doubles();
 cudaError_t launch_max_abs_diff(cudaStream_t st, size_t n, const double* a, const double* b, double* out);
 cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, double lo, double hi,
                                 double kin_max, double nl_bound, int* flag);
+// n and m (4 N3 doubles: n, m_x, m_y, m_z) from rho_v.
+cudaError_t launch_nm_from_rho(cudaStream_t st, size_t N3, const double* rho, double* nm);
 // min v, max v, max |b| of the potential (out3); part: field_sums_part_doubles() scratch.
 cudaError_t launch_window_extrema(cudaStream_t st, size_t N3, const double* V, double* part, double* out3);
 

@@ -1038,6 +1038,22 @@ cudaError_t launch_check_window(cudaStream_t st, size_t N3, const double* V, dou
   return cudaGetLastError();
 }
 
+// n = rho_uu + rho_dd and m = (2 Re rho_ud, -2 Im rho_ud, rho_uu - rho_dd) from rho_v, into
+// nm[0 .. N3) (n) and nm[N3 .. 4 N3) (m_x, m_y, m_z).
+__global__ void k_nm_from_rho(size_t N3, const double* __restrict__ rho, double* __restrict__ nm) {
+  const size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N3) return;
+  const double r0 = rho[r], r1 = rho[N3 + r], r2 = rho[2 * N3 + r], r3 = rho[3 * N3 + r];
+  nm[r] = r0 + r1;
+  nm[N3 + r] = 2.0 * r2;
+  nm[2 * N3 + r] = -2.0 * r3;
+  nm[3 * N3 + r] = r0 - r1;
+}
+cudaError_t launch_nm_from_rho(cudaStream_t st, size_t N3, const double* rho, double* nm) {
+  k_nm_from_rho<<<(unsigned)((N3 + 255) / 256), 256, 0, st>>>(N3, rho, nm);
+  return cudaGetLastError();
+}
+
 // Extrema of the local potential for the automatic spectral window: min and max of
 // v = (V_0 + V_1)/2 and max of |b| = |(V_2, V_3, V_0 - V_1)|/2 over the grid.  Products and sums
 // are rounded one by one (no fused multiply-add), as in a plain IEEE evaluation; min and max do
