@@ -104,3 +104,22 @@ def test_spin_mode_validation_before_device_use(cpu_lib):
         with pytest.raises(_lib.TddftError) as e:
             _lib.TDDFT.from_workload(wl, spin_mode=mode)
         assert e.value.status == -1, mode
+
+
+def test_binding_routes_complex64_to_the_c64_calls():
+    """The binding passes complex64 host arrays through the *_c64 entry points without a copy and
+    turns any other host array into contiguous complex128 (argument handling only, no GPU)."""
+    import numpy as np
+    from paper_2506_21908_gb300 import _lib
+    h = object.__new__(_lib.TDDFT)
+    h.nk, h.nstates, h.n = 1, 2, 4
+    a64 = np.zeros(h.psi_shape, np.complex64)
+    arr, dev, c64 = h._spinor_arg(a64)
+    assert c64 and not dev and arr is a64
+    a128 = np.zeros(h.psi_shape, np.complex128)
+    arr, dev, c64 = h._spinor_arg(a128)
+    assert not c64 and not dev and arr is a128
+    arr, dev, c64 = h._spinor_arg(np.zeros(h.psi_shape))
+    assert not c64 and arr.dtype == np.complex128
+    with pytest.raises(AssertionError):
+        h._spinor_arg(np.zeros(5, np.complex64))
