@@ -135,3 +135,32 @@ def test_spectral_window_contains_the_exact_spectrum():
     ev = np.linalg.eigvalsh(0.5 * (H + H.conj().T))
     lo, hi = s.spectral_bounds(V, [A], margin=0.0)
     assert lo <= ev.min() and ev.max() <= hi
+
+
+def test_zeeman_splitting_matches_the_papers_table():
+    """Lowest eigenvalue of each spin channel of an atom's Hamiltonian (local pseudopotential, no
+    SOC, no XC, static B along z) against the paper's printed Zeeman splittings of the H 1s level
+    (tests/golden/zeeman_splitting_h_1s.txt): b_ext is the Zeeman energy mu_B B of one spin
+    state, so B = b_ext / mu_B and the splitting is 2 b_ext."""
+    import os
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    from tests._systems import parity_system
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "zeeman_splitting_h_1s.txt"))
+    wl, s, psi = parity_system(n=12, nstates=1, nk=1, lam=0.0, natoms=1)
+    s.xc = 0
+    ev = 27.211386245988  # eV per hartree
+    n3 = s.grid.n ** 3
+    for b_ev, split_ev in rows:
+        B = np.array([0.0, 0.0, b_ev / ev / MU_B])
+        V, _ = s.potential(np.zeros((4,) + (s.grid.n,) * 3), B)
+        lows = []
+        for spin in (0, 1):
+            def mv(x, spin=spin):
+                p = np.zeros(psi.shape, np.complex128)
+                p[0, 0, spin] = x.reshape((s.grid.n,) * 3)
+                return s.apply_h(p, V, np.zeros(3))[0, 0, spin].reshape(-1)
+            op = LinearOperator((n3, n3), matvec=mv, dtype=np.complex128)
+            w = eigsh(op, k=1, which="SA", tol=1e-12, v0=np.ones(n3, np.complex128))[0]
+            lows.append(w[0])
+        assert (lows[0] - lows[1]) * ev == pytest.approx(split_ev, abs=5e-5)
+
