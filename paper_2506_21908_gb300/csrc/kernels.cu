@@ -608,37 +608,43 @@ cudaError_t launch_density(cudaStream_t st, size_t N3, const void* psi, int nkb,
 
 // ============================================================================ XC and potential
 
-// PW92 interpolation G(rs) and dG/drs for one parameter row (A, a1, b1, b2, b3, b4), p = 1.
-__device__ __forceinline__ void pw92_g(double rs, double A, double a1, double b1, double b2, double b3, double b4,
-                                       double* g, double* dg) {
-  const double sr = sqrt(rs);
+// PW92 interpolation G(rs) and dG/drs for one parameter row (A, a1, b1, b2, b3, b4), p = 1;
+// sr = sqrt(rs) and isr = 1 / sr are shared by the three rows.
+__device__ __forceinline__ void pw92_g(double rs, double sr, double isr, double A, double a1, double b1, double b2,
+                                       double b3, double b4, double* g, double* dg) {
   const double q0 = -2.0 * A * (1.0 + a1 * rs);
   const double q1 = 2.0 * A * sr * (b1 + sr * (b2 + sr * (b3 + sr * b4)));
-  const double q1p = A * (b1 / sr + 2.0 * b2 + 3.0 * b3 * sr + 4.0 * b4 * rs);
-  const double lg = log1p(1.0 / q1);
+  const double q1p = A * (b1 * isr + 2.0 * b2 + 3.0 * b3 * sr + 4.0 * b4 * rs);
+  const double iq1 = 1.0 / q1;
+  const double lg = log1p(iq1);
   *g = q0 * lg;
-  *dg = -2.0 * A * a1 * lg - q0 * q1p / (q1 * (q1 + 1.0));
+  *dg = -2.0 * A * a1 * lg - q0 * q1p * iq1 / (q1 + 1.0);
 }
 
 // Slater exchange with spin scaling plus PW92 correlation on (nu, nd): energy density, v_up, v_dn.
+// Three cube roots per point: with c = n^(1/3), rs = (3 / 4 pi)^(1/3) / c and
+// (1 +- zeta)^(1/3) = 2^(1/3) n_up,dn^(1/3) / c (nu, nd >= 0, so |zeta| <= 1).
 __device__ void lsda_point(double nu, double nd, double* e, double* vu, double* vd) {
-  const double kPi = 3.14159265358979323846;
-  const double c6 = cbrt(6.0 / kPi);
+  const double c6 = 1.240700981798800033;    // (6 / pi)^(1/3)
+  const double crs = 0.6203504908994000167;  // (3 / (4 pi))^(1/3)
+  const double c2 = 1.259921049894873165;    // 2^(1/3)
+  const double fden = 1.923661050931536320;  // 1 / (2^(4/3) - 2)
   const double cbu = cbrt(nu), cbd = cbrt(nd);
   const double ex = -0.75 * c6 * (nu * cbu + nd * cbd);
   const double vxu = -c6 * cbu, vxd = -c6 * cbd;
   const double n = nu + nd;
-  const double rs = cbrt(3.0 / (4.0 * kPi * n));
+  const double icn = 1.0 / cbrt(n);
+  const double rs = crs * icn;
   double z = (nu - nd) / n;
   z = fmin(1.0, fmax(-1.0, z));
+  const double sr = sqrt(rs), isr = 1.0 / sr;
   double ec0, d0, ec1, d1, mac, dmac;
-  pw92_g(rs, 0.031091, 0.21370, 7.5957, 3.5876, 1.6382, 0.49294, &ec0, &d0);
-  pw92_g(rs, 0.015545, 0.20548, 14.1189, 6.1977, 3.3662, 0.62517, &ec1, &d1);
-  pw92_g(rs, 0.016887, 0.11125, 10.357, 3.6231, 0.88026, 0.49671, &mac, &dmac);
+  pw92_g(rs, sr, isr, 0.031091, 0.21370, 7.5957, 3.5876, 1.6382, 0.49294, &ec0, &d0);
+  pw92_g(rs, sr, isr, 0.015545, 0.20548, 14.1189, 6.1977, 3.3662, 0.62517, &ec1, &d1);
+  pw92_g(rs, sr, isr, 0.016887, 0.11125, 10.357, 3.6231, 0.88026, 0.49671, &mac, &dmac);
   const double ac = -mac, dac = -dmac;
-  const double fden = 1.0 / (cbrt(16.0) - 2.0);  // 1 / (2^(4/3) - 2)
   const double opz = 1.0 + z, omz = 1.0 - z;
-  const double cpz = cbrt(opz), cmz = cbrt(omz);
+  const double cpz = c2 * cbu * icn, cmz = c2 * cbd * icn;
   const double f = (opz * cpz + omz * cmz - 2.0) * fden;
   const double fp = (4.0 / 3.0) * (cpz - cmz) * fden;
   const double fpp0 = 1.709921;
