@@ -93,13 +93,49 @@ def xc_adjoint(n, m, gv, gb):
     return nbar, mbar
 
 
+def collinear_xc_adjoint(nu, nd, gv, gbz):
+    """Cotangents of the channel densities through vbar = (v_u + v_d)/2 and b_z = (v_u - v_d)/2 of
+    the collinear LSDA on (rho_uu, rho_dd) (Eq. SDFT / Eq. HSDFT)."""
+    nubar, ndbar = np.zeros_like(nu), np.zeros_like(nd)
+    ok = nu + nd >= oxc.N_THR
+    if np.any(ok):
+        huu, hud, hdd = lsda_hessian(nu[ok], nd[ok])
+        nubar[ok] = 0.5 * (huu + hud) * gv[ok] + 0.5 * (huu - hud) * gbz[ok]
+        ndbar[ok] = 0.5 * (hud + hdd) * gv[ok] + 0.5 * (hud - hdd) * gbz[ok]
+    return nubar, ndbar
+
+
+def unpolarised_xc_adjoint(n, gv):
+    """Cotangent of n through v(n) = v_u(n/2, n/2) of the spin-unpolarised LDA:
+    dv/dn = (d v_u/d n_u + d v_u/d n_d) / 2."""
+    nbar = np.zeros_like(n)
+    ok = n >= oxc.N_THR
+    if np.any(ok):
+        huu, hud, _ = lsda_hessian(0.5 * n[ok], 0.5 * n[ok])
+        nbar[ok] = 0.5 * (huu + hud) * gv[ok]
+    return nbar
+
+
 def potential_adjoint(system, rho, Vbar):
-    """Cotangent of rho_v and of B from the cotangent of V_v = [v+b_z, v-b_z, 2b_x, -2b_y]."""
+    """Cotangent of rho_v and of B from the cotangent of V_v = [v+b_z, v-b_z, 2b_x, -2b_y].  In the
+    collinear mode only B_z reaches the spinors and the XC field is along z; in the unpolarised
+    mode neither B nor an XC field does."""
     gv = Vbar[0] + Vbar[1]
     gb = np.stack([2.0 * Vbar[2], -2.0 * Vbar[3], Vbar[0] - Vbar[1]])
     Bbar = MU_B * gb.sum(axis=(1, 2, 3))
+    mode = getattr(system, "spin_mode", 0)
     n, m = system.n_m(rho)
     nbar = hartree_potential(system.grid, gv)  # symmetric convolution
+    if mode == 1:
+        Bbar = np.array([0.0, 0.0, Bbar[2]])
+        xu, xd = collinear_xc_adjoint(rho[0], rho[1], gv, gb[2]) if system.xc else (0.0, 0.0)
+        z = np.zeros_like(n)
+        return np.stack([nbar + xu, nbar + xd, z, z]), Bbar
+    if mode == 2:
+        if system.xc:
+            nbar = nbar + unpolarised_xc_adjoint(n, gv)
+        z = np.zeros_like(n)
+        return np.stack([nbar, nbar, z, z]), np.zeros(3)
     if system.xc:
         xn, xm = xc_adjoint(n, m, gv, gb)
         nbar = nbar + xn
