@@ -419,6 +419,11 @@ class System:
         return np.vdot(a, b) * self.grid.dV
 
     def energies(self, psi, rho, V, parts, A, B):
+        """Energy terms of the state (the quantity the exact dynamics conserves when H has no
+        explicit time dependence): E_kin = sum w f <psi|1/2|G+k+A|^2|psi>, E_nl = sum w f <psi|V_NL|psi>,
+        E_loc = int v_loc n, E_H = 1/2 int v_H n, E_xc = int n eps_xc (reading P9: the functional value,
+        with int <rho_v, V_v^xc> of Eq. xc_energy4 reported as xc_pot), E_Z = int mu_B B.m
+        (Eq. zeeman_potential); the ion-ion constant is excluded."""
         g = self.grid
         wf = self.kw[:, None] * self.occ
         ekin = 0.0
