@@ -1,10 +1,13 @@
 """Throughput benchmark of the spinor real-time propagation step.
 
-Default workload: the magnetic-cluster case -- 13 synthetic Z=8 atoms on an icosahedron
-(centre-vertex 4.7 bohr) in a 24 bohr cube, 64^3 grid, 104 occupied spinors, L.S 0.02 Ha,
-Gaussian x-polarised laser in velocity gauge, dt = 0.04, ETRS with Chebyshev exponentials
-and one corrector pass, FP32-mixed precision.  A step is one full ETRS step over all
-spinors; the metric is spinor-grid-point updates per second, N_k N_occ N_g steps / s.
+Default workload (the headline): the large supercell -- 128 synthetic Z=8 atoms on a jittered
+4x4x4 bcc lattice (a = 5.425 bohr, 21.7 bohr cube), 96^3 grid, Gamma point, 1024 occupied
+spinors, L.S 0.02 Ha, Gaussian x-polarised laser in velocity gauge, dt = 0.04, ETRS with
+Chebyshev exponentials and one corrector pass, FP32-mixed precision.  A step is one full ETRS
+step over all spinors; the metric is spinor-grid-point updates per second, N_k N_occ N_g steps / s.
+Extra blocks: the magnetic cluster (64^3, 104 spinors) with its FP64 comparison and propagator
+variants, the bcc supercell (48^3, 8 k-points x 128 spinors), and the differentiation workload
+(48^3 cluster, 500 steps, checkpoints every 50) timed forward + backward.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 (torchrun), every rank runs an independent replica (the path does not shard:
@@ -27,9 +30,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spinor·gridpt updates/s; mixed vs FP64 path at |Δm(T)|≤1e-5; adjoint grad/s"
 UNIT = "spinor*gridpt updates/s"
-WORKLOAD = ("magnetic cluster: 13 synthetic Z=8 atoms, icosahedron 4.7 bohr, 24 bohr cube, 64^3 grid, "
-            "104 occupied spinors (of 112), L.S 0.02 Ha, l<=2 KB projectors, laser E0=0.01 w=0.057 "
-            "FWHM 10 fs x-pol velocity gauge, dt=0.04, ETRS + Chebyshev, n_sc=1")
+LASER = "laser E0=0.01 w=0.057 FWHM 10 fs x-pol velocity gauge, dt=0.04, ETRS + Chebyshev, n_sc=1"
+WORKLOADS = {
+    "large": ("large supercell: 128 synthetic Z=8 atoms, 4x4x4 bcc-like a=5.425 bohr jittered 0.1 bohr, "
+              "21.7 bohr cube, 96^3 grid, Gamma, 1024 occupied spinors (of 1088), L.S 0.02 Ha, l<=2 KB "
+              "projectors, " + LASER),
+    "cluster": ("magnetic cluster: 13 synthetic Z=8 atoms, icosahedron 4.7 bohr, 24 bohr cube, 64^3 grid, "
+                "104 occupied spinors (of 112), L.S 0.02 Ha, l<=2 KB projectors, " + LASER),
+    "bcc": ("bcc supercell: 2x2x2 bcc a=5.42 bohr, 16 synthetic Z=8 atoms, L.S 0.02 Ha, 48^3 grid, "
+            "8 Monkhorst-Pack k-points x 128 occupied spinors (of 144), static B_x=0.001 + " + LASER),
+}
 
 
 def env_rank():
@@ -93,47 +103,103 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- workload
-def cluster_workload(nsteps):
+def make_workload(name, nsteps, states=0, c64=True):
+    """(workload, spinors) of one benchmark configuration; `states` > 0 keeps only the first
+    spinors of each k-point (a small profiling case, not a benchmark line)."""
     from paper_2506_21908_gb300 import synthetic as S
-    wl = S.cluster(n=64, nsteps=nsteps)
-    return wl
-
-
-def make_states(wl):
-    from paper_2506_21908_gb300 import synthetic as S
-    return S.cluster_states(wl)
+    dt = np.complex64 if c64 else np.complex128
+    if name == "large":
+        wl = S.large(nsteps=nsteps)
+        psi = S.large_states(wl, select=np.arange(states) if states else None, dtype=dt)
+    elif name == "cluster":
+        wl = S.cluster(n=64, nsteps=nsteps)
+        psi = S.cluster_states(wl)
+    elif name == "bcc":
+        wl = S.bcc(nsteps=nsteps)
+        psi = S.bcc_states(wl)
+    else:
+        raise ValueError(name)
+    if states and psi.shape[1] > states:
+        psi = psi[:, :states]
+    psi = np.ascontiguousarray(psi, dtype=dt)
+    wl.occ = np.ascontiguousarray(wl.occ[:, :psi.shape[1]])
+    return wl, psi
 
 
 # --------------------------------------------------------------------------- oracle timing
+# One oracle process: builds the oracle for the workload with one spinor, then times a bounded
+# sample of its step -- a Chebyshev series of order 2 (two Hamiltonian applications with the
+# recurrence and accumulation) and one density + potential evaluation -- and scales it to the
+# step's (K_full + 2 K_half) Hamiltonian applications and three density + potential evaluations.
 ORACLE_SNIPPET = r"""
-import json, sys, time, os
+import json, sys, time
 sys.path.insert(0, %(root)r)
 import numpy as np
 from paper_2506_21908_gb300 import synthetic as S
 from oracle import System, Oracle
-from oracle.tddft import FieldTable
-wl = S.cluster(n=64, nsteps=%(nsteps)d)
-nb = %(nbands)d
-psi = S.atomic_orbital_states(wl.L, wl.n, wl.pos, wl.kpts, S.cluster_axes(len(wl.pos)), seed=wl.seed)[:, :nb]
-wl.occ = wl.occ[:, :nb]
+from oracle.tddft import FieldTable, exp_chebyshev
+name, idx, nrep = %(name)r, %(idx)d, %(nrep)d
+if name == "large":
+    wl = S.large(nsteps=16)
+    psi = S.large_states(wl, select=[idx], dtype=np.complex128)
+elif name == "cluster":
+    wl = S.cluster(n=64, nsteps=16)
+    psi = S.cluster_states(wl)[:, idx:idx + 1]
+else:
+    wl = S.bcc(nsteps=16)
+    psi = S.bcc_states(wl)[:1, idx:idx + 1]
+    wl.kpts, wl.kw = wl.kpts[:1], np.ones(1)
+wl.occ = np.ones((1, 1))
 s = System.from_workload(wl)
-o = Oracle(s, FieldTable(wl.times, wl.A, wl.B), wl.dt, psi, n_sc=1)
-times = []
-for i in range(%(warm)d + %(steps)d):
-    t0 = time.perf_counter(); o.step(); times.append(time.perf_counter() - t0)
-json.dump(dict(times=times[%(warm)d:], nbands=nb, ng=wl.ng, K=[o.K_full, o.K_half]), sys.stdout)
+o = Oracle(s, FieldTable(wl.times, wl.A, wl.B), wl.dt, psi, n_sc=1, cheb_tol=1e-9)
+A, B = o.f.at(0.0)
+h = lambda x: s.apply_h(x, o.V, A)
+out = []
+for r in range(nrep):
+    t0 = time.perf_counter()
+    exp_chebyshev(h, o.psi, wl.dt, o.emin, o.emax, 2)
+    t1 = time.perf_counter()
+    s.potential(s.rho_v(o.psi), B)
+    t2 = time.perf_counter()
+    step = 0.5 * (t1 - t0) * (o.K_full + 2 * o.K_half) + 3 * (t2 - t1)
+    out.append(step)
+json.dump(dict(step_s=out, ng=wl.ng, K=[o.K_full, o.K_half]), sys.stdout)
 """
 
 
-def time_oracle(nbands, steps, warm=0):
-    """Run the oracle single-threaded in a separate process on a sample of bands."""
+def time_oracle(name, procs, nrep=1):
+    """Run `procs` single-threaded oracle processes at once (one spinor each, different spinors);
+    returns the per-process results."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET % dict(root=ROOT, nsteps=max(16, warm + steps + 2), nbands=nbands, warm=warm, steps=steps)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d
+    ps = []
+    for i in range(procs):
+        code = ORACLE_SNIPPET % dict(root=ROOT, name=name, idx=(37 * i) % 100, nrep=nrep)
+        ps.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                   text=True, env=env))
+    res = []
+    for p in ps:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle timing failed: " + err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    return res
+
+
+def cpu_baseline(name):
+    """The oracle on one host core and on all host cores (one process per core, each with its own
+    spinor): spinor-grid-point updates per second of a full ETRS step, from the bounded sample."""
+    ncores = os.cpu_count() or 1
+    one = time_oracle(name, 1)[0]
+    allc = time_oracle(name, ncores) if ncores > 1 else [one]
+    v1 = one["ng"] / one["step_s"][0]
+    vall = len(allc) * allc[0]["ng"] / max(r["step_s"][0] for r in allc)
+    sample = ("per process: one spinor of the %s workload, FP64 numpy oracle, single-threaded; timed: a "
+              "Chebyshev series of order 2 (2 Hamiltonian applications) and one density + potential "
+              "evaluation, scaled to the step's K_full + 2 K_half = %d applications and 3 evaluations; "
+              "%d processes at once" % (name, sum(one["K"]) + one["K"][1], ncores))
+    return {"value": vall, "unit": UNIT, "cores": len(allc), "kind": "oracle", "sample": sample,
+            "cores_1": {"value": v1, "cores": 1, "step_s_per_spinor": one["step_s"][0]},
+            "step_s_per_spinor_all_cores": max(r["step_s"][0] for r in allc)}
 
 
 # --------------------------------------------------------------------------- ours
@@ -142,8 +208,8 @@ def time_oracle(nbands, steps, warm=0):
 KERNEL_SOURCES = {
     "epilogue": ("epilogue.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
     "fft_xy": ("kernels.cu", "fft_tma.cu", "bulk.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
-    "fft_z_kinetic": ("kernels.cu", "kin_cluster.cu", "fft.cuh", "impl.cuh", "kcommon.cuh"),
-    "proj_gather": ("kernels.cu", "proj_tc.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+    "fft_z_kinetic": ("kernels.cu", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+    "proj_gather": ("kernels.cu", "proj_tc.cu", "proj_tile.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
 }
 
 
@@ -155,19 +221,21 @@ def kernel_source_hash(kernel_class):
     src = os.path.join(ROOT, "paper_2506_21908_gb300", "csrc")
     files = KERNEL_SOURCES.get(kernel_class) or [f for f in os.listdir(src) if f.endswith((".cu", ".cuh"))]
     for f in sorted(files):
-        h.update(f.encode())
-        h.update(open(os.path.join(src, f), "rb").read())
+        path = os.path.join(src, f)
+        if os.path.exists(path):
+            h.update(f.encode())
+            h.update(open(path, "rb").read())
     return h.hexdigest()
 
 
-def measured_traffic(kernel_class, units_per_launch):
+def measured_traffic(kernel_class, workload, units_per_launch):
     """DRAM bytes (read + write) per launch of `kernel_class` from the committed ncu summary
-    profiles/traffic_<class>_cluster64_fp32mixed.txt (bytes per spinor-gridpoint unit, averaged over
-    the launches of one step), scaled to this launch size; None when there is no summary or the
-    kernels changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "traffic_%s_cluster64_fp32mixed.txt" % kernel_class)
+    profiles/traffic_<class>_<workload>.txt (bytes per spinor-gridpoint unit, averaged over the
+    captured launches), scaled to this launch size; None when there is no summary or the kernels
+    changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic_%s_%s.txt" % (kernel_class, workload))
     if not os.path.exists(path):
-        return None, "no ncu summary for this kernel"
+        return None, "no ncu summary for this kernel and workload"
     kv = {}
     for line in open(path):
         if ":" in line and not line.startswith((" ", "#")):
@@ -176,6 +244,63 @@ def measured_traffic(kernel_class, units_per_launch):
     if kv.get("source_sha256") != kernel_source_hash(kernel_class):
         return None, "kernels changed since the ncu capture (%s)" % os.path.basename(path)
     return float(kv["dram_bytes_per_unit"]) * units_per_launch, os.path.basename(path)
+
+
+def hbm_peak():
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy)"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Ctx:
+    def __init__(self, torch, dist, stream):
+        self.torch, self.dist, self.stream = torch, dist, stream
+
+    def barrier(self):
+        self.torch.cuda.synchronize()
+        if self.dist is not None:
+            self.dist.barrier()
+
+
+def timed_steps(ctx, h, steps):
+    """Time `steps` steps of handle h on the device (CUDA events on the handle's stream, barrier
+    and synchronise on both sides) with the library's per-kernel-class profile."""
+    torch = ctx.torch
+    ctx.barrier()
+    l0 = h.info()["launches"]
+    h.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.barrier()
+    e0.record()
+    h.step(steps)
+    e1.record()
+    ctx.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = h.profile_read()
+    h.profile(False)
+    return ms, prof, h.info()["launches"] - l0
+
+
+def roofline_of(prof, units_per_launch, workload):
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    pk = prof[dom]
+    hbm, src = hbm_peak()
+    avg_ms = pk["ms"] / max(pk["launches"], 1)
+    bytes_per_launch = pk["bytes"] / max(pk["launches"], 1)
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    traffic, tsrc = measured_traffic(dom, workload, units_per_launch)
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_source": src, "traffic": traffic, "traffic_source": tsrc,
+            "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+            "share": pk["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9)}
+
+
+def kernel_table(prof):
+    return {k: {"ms_total": v["ms"], "launches": v["launches"],
+                "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
+            for k, v in prof.items() if v["launches"]}
 
 
 def run_ours(args):
@@ -187,94 +312,51 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2506_21908_gb300 import _lib
+    from paper_2506_21908_gb300.replicas import aggregate
 
-    # CPU oracle baseline first (separate process, before heavy GPU work on this rank)
+    # CPU oracle baseline first (separate processes, before any GPU work on this rank)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        d = time_oracle(nbands=args.oracle_bands, steps=1)
-        t = statistics.mean(d["times"])
-        cpu = {"value": d["nbands"] * d["ng"] / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one ETRS step of the cluster workload restricted to %d of 104 spinors (FP64 numpy, "
-                         "K=%s, %.1f s)" % (d["nbands"], d["K"], t)}
+        cpu = cpu_baseline(args.workload)
 
-    wl = cluster_workload(args.warmup + args.steps + 64)
-    psi0 = make_states(wl)
-    if args.states:
-        psi0 = np.ascontiguousarray(psi0[:, :args.states])
-        wl.occ = wl.occ[:, :args.states]
-    ups = wl.updates_per_step
     stream = torch.cuda.current_stream().cuda_stream
-
-    def barrier():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-
-    from paper_2506_21908_gb300.replicas import aggregate
+    ctx = Ctx(torch, dist, stream)
 
     def max_over_ranks(x):
         return aggregate(0.0, x)[1]
 
-    # ---------------- mixed precision (the headline)
+    # ---------------- headline: FP32-mixed steps of the workload
+    wl, psi0 = make_workload(args.workload, args.warmup + args.steps + 64, args.states)
+    ups = wl.updates_per_step
     h = _lib.TDDFT.from_workload(wl, precision=_lib.FP32_MIXED, proj_mode=args.proj, stream=stream)
     h.set_fields(wl.times, wl.A, wl.B)
     psi_dev = torch.from_numpy(psi0).to("cuda")
     h.set_states(psi_dev, 0.0)
+    del psi_dev
+    torch.cuda.empty_cache()
     info = h.info()
     h.step(args.warmup)
-    barrier()
+    ctx.barrier()
     clk = ClockSampler(local)
     clk.start()
-    l0 = h.info()["launches"]
-    h.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record()
-    h.step(args.steps)
-    e1.record()
-    barrier()
-    ms = e0.elapsed_time(e1)
-    prof = h.profile_read()
-    h.profile(False)
-    launches = h.info()["launches"] - l0
+    ms, prof, launches = timed_steps(ctx, h, args.steps)
     clocks = clk.stop()
     total_units, sec = aggregate(ups * args.steps, ms / 1e3)  # replicas: sum of units, max of time
     ms_step = sec * 1e3 / args.steps
     value = total_units / sec
-    _, _, E_mixed, _ = h.observables(fields=False, check=False)
-    M_mixed = E_mixed["M"]
-
-    # roofline of the dominant kernel class
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    pk = prof[dom]
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        hbm = float(peaks["hbm_gbs"])
-        peak_src = "measured"
-    except Exception:
-        hbm = 6800.0
-        peak_src = "fallback"
-    avg_ms = pk["ms"] / max(pk["launches"], 1)
-    bytes_per_launch = pk["bytes"] / max(pk["launches"], 1)
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    traffic, traffic_src = measured_traffic(dom, wl.nk * psi0.shape[1] * wl.ng)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_source": peak_src, "traffic": traffic, "traffic_source": traffic_src,
-                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
-                "share": pk["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9)}
-    kernels = {k: {"ms_total": v["ms"], "launches": v["launches"],
-                   "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
-               for k, v in prof.items() if v["launches"]}
+    units_per_launch = wl.nk * psi0.shape[1] * wl.ng
+    roofline = roofline_of(prof, units_per_launch, args.workload)
+    kernels = kernel_table(prof)
+    _, _, E_mixed, norms = h.observables(fields=False, check=False)
 
     # ---------------- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
         # the FP32-mixed handle takes its spinors as complex64 (tddft_set_states_c64)
-        pinned = torch.from_numpy(psi0.astype(np.complex64)).pin_memory()
+        pinned = torch.from_numpy(np.ascontiguousarray(psi0, dtype=np.complex64)).pin_memory()
         n_out = np.empty((wl.n,) * 3)
         m_out = np.empty((3,) + (wl.n,) * 3)
-        K2 = max(2, min(args.steps, 5))
+        K2 = 2
 
         def e2e_iteration():
             h.set_states(pinned, 0.0)
@@ -283,102 +365,34 @@ def run_ours(args):
             assert st in (0, -6), st
 
         e2e_iteration()  # untimed warm-up: first transfer from the freshly page-locked buffer
-        barrier()
+        ctx.barrier()
         t0 = time.perf_counter()
         for _ in range(K2):
             e2e_iteration()
-        barrier()
+        ctx.barrier()
         dt_e2e = max_over_ranks(time.perf_counter() - t0) / K2
         e2e = {"value": ups * world / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": int(pinned.numel() * 8),
                "d2h_bytes_per_step": int(4 * wl.ng * 8), "ms_per_step": dt_e2e * 1e3,
                "what": "set_states_c64(pinned host complex64) + 1 step + observables(n, m to host), per iteration"}
+        del pinned
     h.close()
-    del psi_dev
+    del psi0
+    torch.cuda.empty_cache()
 
-    # ---------------- FP64 GPU path (same start, fewer steps) and mixed-vs-FP64 magnetisation
-    fp64 = None
-    if not args.no_fp64:
-        nst = args.warmup + args.steps
-        g = _lib.TDDFT.from_workload(wl, precision=_lib.FP64, stream=stream)
-        g.set_fields(wl.times, wl.A, wl.B)
-        g.set_states(psi0, 0.0)
-        g.step(1)
-        barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record()
-        g.step(2)
-        f1.record()
-        barrier()
-        ms64 = f0.elapsed_time(f1) / 2
-        g.step(nst - 3)
-        _, _, E64, _ = g.observables(fields=False, check=False)
-        g.close()
-        dm = float(np.linalg.norm(M_mixed - E64["M"]) / len(wl.pos))
-        fp64 = {"value": ups / (ms64 / 1e3), "ms_per_step": ms64, "speedup_mixed_vs_fp64": (ups / (ms_step / 1e3)) / (ups / (ms64 / 1e3)),
-                "dm_per_atom_muB": dm, "steps_compared": nst, "K_fp64": None}
+    # ---------------- the magnetic cluster: throughput, FP64 path and propagator variants
+    cluster = None
+    if not args.no_cluster and args.workload != "cluster":
+        cluster = cluster_block(args, ctx, _lib, aggregate)
 
-    # ---------------- propagator comparison: Taylor-4 and Crank-Nicolson against Chebyshev
-    propagators = None
-    if not args.no_propagators:
-        nst = args.warmup + args.steps
-        propagators = {"steps": nst, "reference": "Chebyshev ETRS (the headline path), same start"}
-        for name, kind in (("taylor4", _lib.EXP_TAYLOR), ("crank_nicolson", _lib.EXP_CRANK_NICOLSON)):
-            g = _lib.TDDFT.from_workload(wl, precision=_lib.FP32_MIXED, exp_kind=kind, stream=stream)
-            g.set_fields(wl.times, wl.A, wl.B)
-            g.set_states(psi0, 0.0)
-            gi = g.info()
-            terms = (gi["K_full"] + 2 * gi["K_half"]) if kind == _lib.EXP_CRANK_NICOLSON else 12
-            rec = {"K_full": gi["K_full"], "K_half": gi["K_half"], "h_applies_per_step": terms}
-            try:
-                g.step(1)
-                barrier()
-                p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                p0.record()
-                g.step(2)
-                p1.record()
-                barrier()
-                msp = p0.elapsed_time(p1) / 2
-                rec.update(ms_per_step=msp, value=ups / (msp / 1e3))
-                g.step(nst - 3)
-                _, _, Ep, nrm = g.observables(fields=False, check=False)
-                rec.update(dm_per_atom_muB_vs_chebyshev=float(np.linalg.norm(Ep["M"] - M_mixed) / len(wl.pos)),
-                           max_norm_error=float(np.abs(nrm - 1.0).max()), status=int(Ep["status"]))
-            except _lib.TddftError as err:  # e.g. Taylor-4 leaving the spectral window (unstable)
-                barrier()
-                rec.update(status=err.status, error=str(err)[:160])
-            g.close()
-            propagators[name] = rec
-        propagators["chebyshev"] = {"ms_per_step": ms_step, "K_full": info["K_full"], "K_half": info["K_half"],
-                                    "h_applies_per_step": info["K_full"] + 2 * info["K_half"]}
+    # ---------------- the bcc supercell (k-points with Bloch phases)
+    bcc = None
+    if not args.no_bcc and args.workload != "bcc":
+        bcc = throughput_block(args, ctx, _lib, aggregate, "bcc", steps=3)[0]
 
-    # ---------------- adjoint gradient (differentiation workload, bounded horizon)
+    # ---------------- adjoint gradient (differentiation workload)
     adjoint = None
     if not args.no_adjoint:
-        from paper_2506_21908_gb300 import synthetic as S
-        from paper_2506_21908_gb300.autograd import MagnetizationFromPulse, PulseBasis, mz_seed
-        nst = args.adj_steps
-        dwl = S.cluster(n=48, nsteps=nst, laser=False)
-        dpsi = S.cluster_states(dwl)
-        basis = PulseBasis(dwl.times, 64, mode="laser", omega=0.057)
-        a0 = np.random.default_rng(20250624).uniform(0.0, 0.01, 64)
-        res = {}
-        for prec, name in ((_lib.FP32_MIXED, "fp32_mixed"), (_lib.FP64, "fp64")):
-            hd = _lib.TDDFT.from_workload(dwl, precision=prec, stream=stream)
-            a = torch.tensor(a0, requires_grad=True)
-            barrier()
-            t0 = time.perf_counter()
-            L = MagnetizationFromPulse.apply(a, hd, dpsi, basis, nst, mz_seed(48, dwl.L), args.adj_ckpt)
-            L.backward()
-            barrier()
-            dt_g = max_over_ranks(time.perf_counter() - t0)
-            res[name] = {"seconds": dt_g, "grad_per_s": 1.0 / dt_g, "loss": float(L.detach()),
-                         "grad_norm": float(a.grad.norm())}
-            hd.close()
-        g32 = None
-        adjoint = {"workload": "13-atom cluster, 48^3, 104 spinors, 64-sample laser envelope, L = M_z(T)",
-                   "steps": nst, "ckpt_every": args.adj_ckpt, "per_precision": res,
-                   "grad_per_s_500_steps_est": {k: 1.0 / (v["seconds"] * 500.0 / nst) for k, v in res.items()},
-                   "what": "forward + discrete-adjoint backward of the whole horizon, one 64-parameter gradient"}
+        adjoint = adjoint_block(args, ctx, _lib, max_over_ranks)
 
     if rank != 0:
         return
@@ -386,37 +400,166 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "FP32-mixed (c64 spinors/FFT/potential/projectors; "
-                   "f64 density, XC, Hartree, energies)", "grid": 64, "spinors": 104, "K_full": info["K_full"],
-                   "K_half": info["K_half"], "l2": "inputs larger than L2: 436 MB spinor array per pass",
-                   "projector_contraction": {1: "FP32 CUDA cores", 2: "TF32 tensor cores (tcgen05)",
-                                             3: "3xTF32 tensor cores (tcgen05)"}[args.proj],
+        "config": {"workload": WORKLOADS[args.workload] if not args.states else
+                   WORKLOADS[args.workload] + " [profiling case: %d spinors per k]" % psi0_states(wl),
+                   "precision": "FP32-mixed (c64 spinors/FFT/potential/projectors; f64 density, XC, Hartree, "
+                                "energies)", "grid": wl.n, "spinors_per_k": psi0_states(wl), "kpoints": wl.nk,
+                   "atoms": len(wl.pos), "K_full": info["K_full"], "K_half": info["K_half"],
+                   "l2": "inputs larger than L2: %.0f MB spinor array per pass" % (units_per_launch * 16 / 1e6),
+                   "projector_contraction": PROJ_NAMES[args.proj],
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "fp64": fp64, "propagators": propagators, "adjoint": adjoint,
+        "clocks": clocks, "M_final": E_mixed["M"].tolist(), "max_norm_error": float(np.abs(norms - 1.0).max()),
+        "cluster": cluster, "bcc": bcc, "adjoint": adjoint,
     }
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
 
 
+PROJ_NAMES = {1: "FP32 CUDA cores", 2: "TF32 tensor cores (tcgen05)", 3: "3xTF32 tensor cores (tcgen05)"}
+
+
+def psi0_states(wl):
+    return int(wl.occ.shape[1])
+
+
+def throughput_block(args, ctx, _lib, aggregate, name, steps, warm=2):
+    """FP32-mixed throughput of another configuration (not the headline)."""
+    wl, psi0 = make_workload(name, warm + steps + 8)
+    h = _lib.TDDFT.from_workload(wl, precision=_lib.FP32_MIXED, proj_mode=args.proj, stream=ctx.stream)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi0, 0.0)
+    info = h.info()
+    h.step(warm)
+    ms, prof, launches = timed_steps(ctx, h, steps)
+    units, sec = aggregate(wl.updates_per_step * steps, ms / 1e3)
+    rec = {"workload": WORKLOADS[name], "value": units / sec, "unit": UNIT, "ms_per_step": sec * 1e3 / steps,
+           "steps": steps, "K_full": info["K_full"], "K_half": info["K_half"], "gpu_launches": launches,
+           "roofline": roofline_of(prof, wl.nk * psi0.shape[1] * wl.ng, name), "kernels": kernel_table(prof)}
+    h.close()
+    return rec, wl, psi0
+
+
+def cluster_block(args, ctx, _lib, aggregate):
+    torch = ctx.torch
+    rec, wl, psi0 = throughput_block(args, ctx, _lib, aggregate, "cluster", steps=10, warm=3)
+    ups = wl.updates_per_step
+    nst = 3 + 10
+    # mixed-vs-FP64 on the same start (the mixed run again from t = 0 for nst steps)
+    g = _lib.TDDFT.from_workload(wl, precision=_lib.FP32_MIXED, proj_mode=args.proj, stream=ctx.stream)
+    g.set_fields(wl.times, wl.A, wl.B)
+    g.set_states(psi0, 0.0)
+    g.step(args.fp64_steps)
+    n32, m32, E32, _ = g.observables(fields=True, check=False)
+    g.close()
+    if not args.no_fp64:
+        g = _lib.TDDFT.from_workload(wl, precision=_lib.FP64, stream=ctx.stream)
+        g.set_fields(wl.times, wl.A, wl.B)
+        g.set_states(psi0.astype(np.complex128), 0.0)
+        _, _, E0, _ = g.observables(fields=False, check=False)
+        g.step(1)
+        ctx.barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        g.step(2)
+        f1.record()
+        ctx.barrier()
+        ms64 = f0.elapsed_time(f1) / 2
+        g.step(args.fp64_steps - 3)
+        n64, m64, E64, _ = g.observables(fields=True, check=False)
+        g.close()
+        rec["fp64"] = {"value": ups / (ms64 / 1e3), "ms_per_step": ms64,
+                       "speedup_mixed_vs_fp64": ms64 / rec["ms_per_step"],
+                       "steps_compared": args.fp64_steps,
+                       "dM_per_atom_muB": float(np.linalg.norm(E32["M"] - E64["M"]) / len(wl.pos)),
+                       "max_dn_rel": float(np.abs(n32 - n64).max() / np.abs(n64).max()),
+                       "max_dm_rel": float(np.abs(m32 - m64).max() / np.abs(m64).max()),
+                       "dE_Ha": float(abs(E32["total"] - E64["total"])),
+                       "E_drift_fp64_Ha": float(E64["total"] - E0["total"])}
+    if not args.no_propagators:
+        props = {"steps": nst, "reference": "Chebyshev ETRS, same start"}
+        for name, kind in (("taylor4", _lib.EXP_TAYLOR), ("crank_nicolson", _lib.EXP_CRANK_NICOLSON)):
+            g = _lib.TDDFT.from_workload(wl, precision=_lib.FP32_MIXED, exp_kind=kind, stream=ctx.stream)
+            g.set_fields(wl.times, wl.A, wl.B)
+            g.set_states(psi0, 0.0)
+            gi = g.info()
+            terms = (gi["K_full"] + 2 * gi["K_half"]) if kind == _lib.EXP_CRANK_NICOLSON else 12
+            p = {"K_full": gi["K_full"], "K_half": gi["K_half"], "h_applies_per_step": terms}
+            try:
+                g.step(1)
+                ctx.barrier()
+                p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                p0.record()
+                g.step(2)
+                p1.record()
+                ctx.barrier()
+                msp = p0.elapsed_time(p1) / 2
+                p.update(ms_per_step=msp, value=ups / (msp / 1e3))
+                g.step(args.fp64_steps - 3)
+                _, _, Ep, nrm = g.observables(fields=False, check=False)
+                p.update(dM_per_atom_muB_vs_chebyshev=float(np.linalg.norm(Ep["M"] - E32["M"]) / len(wl.pos)),
+                         max_norm_error=float(np.abs(nrm - 1.0).max()), status=int(Ep["status"]))
+            except _lib.TddftError as err:  # e.g. Taylor-4 leaving the spectral window (unstable)
+                ctx.barrier()
+                p.update(status=err.status, error=str(err)[:160])
+            g.close()
+            props[name] = p
+        rec["propagators"] = props
+    return rec
+
+
+def adjoint_block(args, ctx, _lib, max_over_ranks):
+    """The differentiation workload: 13-atom cluster at 48^3, 104 spinors, 64-sample laser
+    envelope, L = M_z(T) after `adj_steps` steps with checkpoints every `adj_ckpt`; one gradient =
+    the forward run and the discrete-adjoint backward run through the autograd wrapper."""
+    torch = ctx.torch
+    from paper_2506_21908_gb300 import synthetic as S
+    from paper_2506_21908_gb300.autograd import MagnetizationFromPulse, PulseBasis, mz_seed
+    nst = args.adj_steps
+    dwl = S.cluster(n=48, nsteps=nst, laser=False)
+    dpsi = S.cluster_states(dwl)
+    basis = PulseBasis(dwl.times, 64, mode="laser", omega=0.057)
+    a0 = np.random.default_rng(20250624).uniform(0.0, 0.01, 64)
+    res = {}
+    precs = [(_lib.FP32_MIXED, "fp32_mixed")] + ([(_lib.FP64, "fp64")] if args.adj_fp64 else [])
+    for prec, name in precs:
+        hd = _lib.TDDFT.from_workload(dwl, precision=prec, stream=ctx.stream)
+        a = torch.tensor(a0, requires_grad=True)
+        ctx.barrier()
+        t0 = time.perf_counter()
+        L = MagnetizationFromPulse.apply(a, hd, dpsi, basis, nst, mz_seed(48, dwl.L), args.adj_ckpt)
+        L.backward()
+        ctx.barrier()
+        dt_g = max_over_ranks(time.perf_counter() - t0)
+        res[name] = {"seconds": dt_g, "grad_per_s": 1.0 / dt_g, "loss": float(L.detach()),
+                     "grad_norm": float(a.grad.norm())}
+        hd.close()
+    return {"workload": "13-atom cluster, 48^3, 104 spinors, 64-sample laser envelope, L = M_z(T)",
+            "steps": nst, "ckpt_every": args.adj_ckpt, "per_precision": res,
+            "what": "forward + discrete-adjoint backward of the whole horizon, one 64-parameter gradient (measured)"}
+
+
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The FP64 CPU oracle on the host cores (one single-threaded process per core, one spinor
+    each), each step the bounded sample of time_oracle, on the headline workload."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    d = time_oracle(nbands=1, steps=args.steps, warm=args.warmup)
-    ts = d["times"]
-    t = statistics.mean(ts)
-    value = d["nbands"] * d["ng"] / t
+    ncores = os.cpu_count() or 1
+    res = time_oracle(args.workload, ncores, nrep=args.warmup + args.steps)
+    per_step = [max(r["step_s"][i] for r in res) for i in range(args.warmup, args.warmup + args.steps)]
+    t = statistics.mean(per_step)
+    value = ncores * res[0]["ng"] / t
+    sample = ("each step: %d single-threaded FP64 numpy oracle processes at once, one spinor of the %s "
+              "workload each; timed: a Chebyshev series of order 2 and one density + potential evaluation, "
+              "scaled to a full ETRS step (K = %s)" % (ncores, args.workload, res[0]["K"]))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "precision": "FP64 CPU oracle",
-                                "sample": "%d of 104 spinors per step" % d["nbands"]},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "each step: one ETRS step of the cluster workload on %d of 104 spinors "
-                                      "(numpy FP64, single thread)" % d["nbands"]},
+           "config": {"workload": WORKLOADS[args.workload], "precision": "FP64 CPU oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -424,19 +567,22 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--oracle-bands", type=int, default=2)
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=25, help="steps of the cluster's mixed-vs-FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--proj", type=int, default=1,
-                    help="projector contraction: 1 FP32 CUDA cores, 2 TF32 tensor cores, 3 TF32x3 tensor cores")
+    ap.add_argument("--no-cluster", action="store_true")
+    ap.add_argument("--no-bcc", action="store_true")
+    ap.add_argument("--proj", type=int, default=1, help="projector contraction: " + str(PROJ_NAMES))
     ap.add_argument("--no-propagators", action="store_true", help="skip the Taylor-4 / Crank-Nicolson comparison")
-    ap.add_argument("--adj-steps", type=int, default=20)
-    ap.add_argument("--adj-ckpt", type=int, default=10)
+    ap.add_argument("--adj-steps", type=int, default=500)
+    ap.add_argument("--adj-ckpt", type=int, default=50)
+    ap.add_argument("--adj-fp64", action="store_true", help="also time the FP64 adjoint (slow)")
     ap.add_argument("--states", type=int, default=0,
                     help="propagate only the first N spinors (small profiling case; not the headline)")
     args = ap.parse_args()

@@ -180,8 +180,6 @@ struct tddft_ctx {
   double t = 0, emin = 0, emax = 0, nl_bound = 0, kin_max = 0;
   int K_full = 0, K_half = 0;
   std::vector<cd> cf_full, cf_half;
-  bool use_fused = false;  // fused term kernel (where two planes fit in shared memory)
-  bool use_cluster = false;  // one-kernel kinetic term on 16-CTA clusters (FP32, n = 32, 48, 64)
   bool use_tma = false;      // FP32 xy passes fed by bulk asynchronous copies
   bool epi_pairs = false;    // epilogue threads take one point of two spinors
   // device memory
@@ -590,10 +588,6 @@ template <typename R> tddft_status kinetic(tddft_ctx* c, const void* in, void* o
   const int nbatch = 2 * c->nkb;
   const double by = 2.0 * nbatch * (double)c->N3 * 2 * sizeof(R);
   tddft_status s;
-  if (c->use_cluster && c->prec != TDDFT_FP64 && kinetic_cluster_supported(c->N))
-    return c->launch(KC_FFT_Z, "kinetic cluster", [&] {
-      return launch_kinetic_cluster(c->st, c->N, in, out, nbatch, c->tw, zp);
-    }, by);
   if ((s = c->launch(KC_FFT_XY, "fft xy", [&] { return xy_pass<R>(c, in, out, nbatch, false); }, by))) return s;
   if ((s = c->launch(KC_FFT_Z, "fft z", [&] { return launch_fft_z<R>(c->st, c->N, out, nbatch, c->tw, Z_KIN, zp); }, by))) return s;
   return c->launch(KC_FFT_XY, "ifft xy", [&] { return xy_pass<R>(c, out, out, nbatch, true); }, by);
@@ -637,64 +631,6 @@ template <typename R> tddft_status kinetic_and_gather(tddft_ctx* c, const void* 
   return c->cuda(cudaStreamWaitEvent(c->st, c->ev_join, 0), "join wait");
 }
 
-// Fused form of one Chebyshev series: per term a projector gather of T_k, the z pass with the
-// kinetic multiply (tmp holds the xy transform of T_k), and one fused kernel that finishes the
-// inverse transform, applies the potential and projectors, updates T_{k+1} and the
-// accumulators and leaves the xy transform of T_{k+1} in tmp.
-template <typename R>
-tddft_status cheb_series_fused(tddft_ctx* c, const void* in, const R* Vr, const double A[3], void* acc1,
-                               const std::vector<cd>& cf1, int K1, void* acc2, const std::vector<cd>& cf2, int K2,
-                               EpiParams ep, void* const* slots) {
-  const int K = std::max(K1, acc2 ? K2 : 0);
-  ZParams zp{};
-  const double pi = 3.14159265358979323846;
-  for (int a = 0; a < 3; ++a) zp.gs[a] = 2.0 * pi / c->L[a];
-  zp.scale = 1.0 / (double)c->N3;
-  zp.comps_per_k = 2 * c->nb;
-  fill_shifts(c, A, zp.shift);
-  const int nbatch = 2 * c->nkb;
-  const double pass = (double)c->psi_elems() * 2 * sizeof(R);  // one read or write of a spinor array
-  ProjTables<R> pt = c->tables<R>();
-  tddft_status s;
-  if ((s = c->launch(KC_FFT_XY, "fft xy", [&] { return launch_fft_xy<R>(c->st, c->N, in, c->tmp, nbatch, c->tw, false); }, 2 * pass)))
-    return s;
-  const void* prev = in;
-  const void* cur = in;
-  for (int k = 0; k < K; ++k) {
-    if ((s = gather<R>(c, cur, A))) return s;
-    if ((s = c->launch(KC_FFT_Z, "fft z", [&] { return launch_fft_z<R>(c->st, c->N, c->tmp, nbatch, c->tw, Z_KIN, zp); }, 2 * pass)))
-      return s;
-    void* out;
-    if (slots) out = slots[k + 1];
-    else if (k == 0) out = c->Ta;
-    else if (prev == in) out = (cur == c->Ta) ? c->Tb : c->Ta;
-    else out = const_cast<void*>(prev);
-    ep.mode = (k == 0) ? EPI_FIRST : EPI_RECUR;
-    ep.use_acc1 = (k + 1 <= K1);
-    ep.use_acc2 = (acc2 != nullptr && k + 1 <= K2);
-    if (ep.use_acc1) {
-      ep.a0[0] = cf1[0].real(); ep.a0[1] = cf1[0].imag();
-      ep.a1[0] = cf1[k + 1].real(); ep.a1[1] = cf1[k + 1].imag();
-    }
-    if (ep.use_acc2) {
-      ep.b0[0] = cf2[0].real(); ep.b0[1] = cf2[0].imag();
-      ep.b1[0] = cf2[k + 1].real(); ep.b1[1] = cf2[k + 1].imag();
-    }
-    const int do_fwd = (k + 1 < K) ? 1 : 0;
-    const int nacc = ep.use_acc1 + ep.use_acc2;
-    const double streams = 3.0 + (k == 0 ? 0.0 : 1.0) + do_fwd + nacc * (k == 0 ? 1.0 : 2.0);
-    const void* tkm1 = (k == 0) ? nullptr : prev;
-    if ((s = c->launch(KC_EPI, "fused chebyshev term", [&] {
-           return launch_fused_term<R>(c->st, c->N, c->tmp, cur, tkm1, out, acc1, acc2, Vr, pt, c->dcbuf, c->nkb,
-                                       c->tw, ep, do_fwd);
-         }, streams * pass + 4.0 * c->N3 * sizeof(R))))
-      return s;
-    prev = cur;
-    cur = out;
-  }
-  return TDDFT_OK;
-}
-
 // Accumulation schedule of one series acc = sum_{i <= Ka} cf[i] T_i in the unfused recurrence:
 // epilogue k has T_{k-1}, T_k and T_{k+1} in registers, so the accumulator is touched only
 // when three terms are pending or T_{k+1} is its last term (one read-modify-write per three
@@ -735,8 +671,6 @@ tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double
   const void* prev = in;
   const void* cur = in;
   tddft_status s;
-  if (c->use_fused && fused_supported<R>(c->N))
-    return cheb_series_fused<R>(c, in, Vr, A, acc1, cf1, K1, acc2, cf2, K2, ep, slots);
   int done1 = 0, done2 = 0;
   for (int k = 0; k < K; ++k) {
     if ((s = kinetic_and_gather<R>(c, cur, A))) return s;
@@ -1592,14 +1526,6 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
       if (pj->lambda_so[i] != 0.0)
         return c->fail(TDDFT_ERR_ARG, "spin-orbit coupling couples the spin channels: it needs the non-collinear mode");
   {
-    // Default: five launches per Chebyshev term (FFT passes, gather, pointwise epilogue), the
-    // faster form on this part.  TDDFT_FUSED=1 selects the fused term kernel (same results).
-    const char* e = std::getenv("TDDFT_FUSED");
-    c->use_fused = (e && e[0] == '1');
-    // TDDFT_CLUSTER=1 selects the one-kernel cluster kinetic term (same results; slower on
-    // this part than the three passes, which overlap HBM traffic and shared-memory FFTs better).
-    const char* f = std::getenv("TDDFT_CLUSTER");
-    c->use_cluster = f && f[0] == '1';
     // FP32 xy passes take their planes through bulk asynchronous copies; TDDFT_NO_TMA=1 keeps
     // the register-fed passes (same results).
     const char* g = std::getenv("TDDFT_NO_TMA");

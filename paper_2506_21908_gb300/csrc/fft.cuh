@@ -282,12 +282,45 @@ template <typename C, bool INV> struct SmallDFT<C, 6, INV> {
   }
 };
 
+template <typename C, bool INV> struct SmallDFT<C, 12, INV> {
+  // 12 = 3 x 4 (n = 4 n1 + n2, k = k1 + 3 k2): three-point DFTs over n1 for each n2, twiddle
+  // w12^{n2 k1}, four-point DFTs over n2 for each k1.
+  __device__ __forceinline__ static void run(C* v) {
+    using R = decltype(C::x);
+    const R h = (R)0.8660254037844386467637;  // sin(pi/3) = cos(pi/6)
+    const R sg = INV ? (R)1 : (R)-1;          // w12^m = exp(sg i pi m / 6)
+    C y[4][3];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      y[n2][0] = v[n2];
+      y[n2][1] = v[n2 + 4];
+      y[n2][2] = v[n2 + 8];
+      SmallDFT<C, 3, INV>::run(y[n2]);
+    }
+    // twiddles w12^{n2 k1}: m = 1 (h, sg/2), 2 (1/2, sg h), 3 (0, sg), 4 (-1/2, sg h), 6 (-1, 0)
+    y[1][1] = cmul(y[1][1], cmake<C>(h, sg * (R)0.5));
+    y[1][2] = cmul(y[1][2], cmake<C>((R)0.5, sg * h));
+    y[2][1] = cmul(y[2][1], cmake<C>((R)0.5, sg * h));
+    y[2][2] = cmul(y[2][2], cmake<C>((R)-0.5, sg * h));
+    y[3][1] = cmake<C>(-sg * y[3][1].y, sg * y[3][1].x);  // times sg i
+    y[3][2] = cmake<C>(-y[3][2].x, -y[3][2].y);           // times -1
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+      C u[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      SmallDFT<C, 4, INV>::run(u);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 3 * k2] = u[k2];
+    }
+  }
+};
+
 template <int N> struct TwoFactor { static constexpr bool ok = false; };
 template <> struct TwoFactor<16> { static constexpr bool ok = true; static constexpr int R1 = 4, R2 = 4; };
 template <> struct TwoFactor<24> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 3; };
 template <> struct TwoFactor<32> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 4; };
 template <> struct TwoFactor<48> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 6; };
 template <> struct TwoFactor<64> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 8; };
+template <> struct TwoFactor<96> { static constexpr bool ok = true; static constexpr int R1 = 8, R2 = 12; };
 
 // Row pitch of a two-factor xy plane in shared memory: congruent to 8 modulo 16 elements, so that
 // the in-row exchange (8 lanes per row, columns rotated by K0) and the column accesses are both

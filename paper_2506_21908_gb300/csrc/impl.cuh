@@ -79,18 +79,6 @@ template <typename R>
 cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* Tk, const void* Tkm1,
                             void* Tout, void* acc1, void* acc2, const R* V, const ProjTables<R>& pt,
                             const void* dc, int nkb, const EpiParams& ep);
-// Whole kinetic term of each spinor component in one kernel (16-CTA clusters, FP32, n in
-// {32, 48, 64}): out = IFFT(1/2 |G + k + A|^2 FFT(in)).
-bool kinetic_cluster_supported(int N);
-cudaError_t launch_kinetic_cluster(cudaStream_t st, int N, const void* in, void* out, int nbatch, const void* tw,
-                                   const ZParams& zp);
-
-// Fused inverse-xy FFT + Chebyshev epilogue + forward-xy FFT of T_{k+1} (FIRST/RECUR modes).
-template <typename R> bool fused_supported(int N);
-template <typename R>
-cudaError_t launch_fused_term(cudaStream_t st, int N, void* tmp, const void* Tk, const void* Tkm1, void* Tout,
-                              void* acc1, void* acc2, const R* V, const ProjTables<R>& pt, const void* dc, int nkb,
-                              const void* tw, const EpiParams& ep, int do_fwd);
 // rho_v of all spinors; part (density_groups(N3, nkb) x 4 x N3 doubles, may be null) lets the
 // band sum run as several groups reduced in a fixed order.
 int density_groups(size_t N3, int nkb);

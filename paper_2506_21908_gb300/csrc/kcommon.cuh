@@ -4,14 +4,15 @@
 
 namespace tddft {
 
-template <int N> struct FFTThreads { static constexpr int value = (N >= 96) ? 512 : 256; };
+// 96 = 8 x 12: 384 threads give every two-factor item loop (768 and 1152 items) and every
+// radix-stage butterfly loop (1152, 2304, 3072 butterflies) whole iterations.
+template <int N> struct FFTThreads { static constexpr int value = (N >= 96) ? 384 : 256; };
 
 // Minimum resident CTAs per SM requested from the register allocator: several CTAs of the
-// FP32 passes up to 64^3 fit without spills; FP64 and 96^3 variants keep their registers.
+// FP32 passes up to 64^3 fit without spills, two of the FP32 96^3 passes (80 KB of shared
+// memory each); FP64 variants keep their registers.
 template <typename R, int N> struct FFTMinBlocks { static constexpr int value = 1; };
-template <int N> struct FFTMinBlocks<float, N> { static constexpr int value = (N <= 64) ? 1024 / FFTThreads<N>::value : 1; };
-template <typename R, int N> struct FusedMinBlocks { static constexpr int value = 1; };
-template <int N> struct FusedMinBlocks<float, N> { static constexpr int value = (N <= 64) ? 2 : 1; };
+template <int N> struct FFTMinBlocks<float, N> { static constexpr int value = (N <= 64) ? 1024 / FFTThreads<N>::value : 2; };
 
 template <int N> __device__ __forceinline__ int freq(int i) { return i < N / 2 ? i : i - N; }
 

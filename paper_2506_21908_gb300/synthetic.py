@@ -222,38 +222,106 @@ def lowdin(psi_k, dV):
     return Sm.T @ psi_k
 
 
-def atomic_orbital_states(L, n, pos, kpts, axes, per_atom=8, n_par=5, sigma=1.0, seed=0):
+# The 9 atomic basis functions as sums of separable terms c * d_x^px d_y^py d_z^pz * Gaussian:
+# s; p_x, p_y, p_z; d_xy, d_yz, d_zx, d_(x^2-y^2), d_(3z^2-r^2) = 2 z^2 - x^2 - y^2.
+_BASIS_TERMS = [[(1.0, 0, 0, 0)], [(1.0, 1, 0, 0)], [(1.0, 0, 1, 0)], [(1.0, 0, 0, 1)], [(1.0, 1, 1, 0)],
+                [(1.0, 0, 1, 1)], [(1.0, 1, 0, 1)], [(1.0, 2, 0, 0), (-1.0, 0, 2, 0)],
+                [(2.0, 0, 0, 2), (-1.0, 2, 0, 0), (-1.0, 0, 2, 0)]]
+# distinct power triples (px, py, pz) of those terms
+_TRIPLES = sorted({(t[1], t[2], t[3]) for m in _BASIS_TERMS for t in m})
+
+
+def _axis_factors(n, h, Lax, R, kax, sigma):
+    """Per-axis factors d^p exp(-d^2 / (2 sigma^2)) exp(-i k (R + d)), p = 0, 1, 2, on the n grid
+    coordinates of one axis (d the minimum-image displacement from R): (3, n)."""
+    d = min_image(np.arange(n) * h - R, Lax)
+    g = np.exp(-d * d / (2.0 * sigma * sigma))
+    if kax != 0.0:
+        g = g * np.exp(-1j * kax * (R + d))
+    return np.stack([g, d * g, d * d * g])
+
+
+def atomic_orbital_states(L, n, pos, kpts, axes, per_atom=8, n_par=5, sigma=1.0, seed=0, select=None,
+                          dtype=np.complex128):
     """8 orbitals per atom: seeded random complex combinations of the s, p and d
     Gaussians (width sigma) on that atom; n_par parallel and the rest
     antiparallel to the atom's spin axis; Bloch phase folded into u_k;
-    Loewdin-orthonormalised per k-point."""
+    Loewdin-orthonormalised per k-point.
+
+    The basis functions (and the Bloch phase) are products of one-dimensional factors on the
+    orthorhombic grid, so the Gram matrix of the basis on the grid is a sum of products of
+    one-dimensional sums; the spinor overlap S follows from it and the spinor products, and the
+    orthonormalised states psi_i = sum_j (S^-1/2)_{ji} chi_j phi_j are formed as one coefficient
+    matrix times the separable basis, one z-plane at a time (in the precision of `dtype`:
+    complex128, or complex64 with single-precision products).  `select` picks the state indices
+    to return (all by default)."""
     rng = np.random.default_rng(seed)
     L = np.asarray(L, np.float64)
-    r = grid_coords(L, n).reshape(-1, 3)
+    pos = np.asarray(pos, np.float64)
+    h = L / n
     dV = float(np.prod(L)) / n ** 3
-    nk = len(kpts)
     natoms = len(pos)
     ns = natoms * per_atom
     coef = rng.normal(size=(natoms, per_atom, 9)) + 1j * rng.normal(size=(natoms, per_atom, 9))
-    out = np.empty((nk, ns, 2, n ** 3), np.complex128)
-    for a in range(natoms):
-        d = min_image(r - pos[a], L)
-        g = np.exp(-(d * d).sum(-1) / (2.0 * sigma * sigma))
-        x, y, z = d[:, 0], d[:, 1], d[:, 2]
-        basis = np.stack([g, x * g, y * g, z * g, x * y * g, y * z * g, z * x * g,
-                          (x * x - y * y) * g, (3 * z * z - (d * d).sum(-1)) * g])
-        orbs = coef[a] @ basis  # (per_atom, npts)
-        th, ph = axes[a]
-        for j in range(per_atom):
-            chi = spinor_along(th, ph, parallel=(j < n_par))
-            for ik, kv in enumerate(kpts):
-                phase = np.exp(-1j * ((pos[a][None, :] + d) @ kv))
-                out[ik, a * per_atom + j, 0] = chi[0] * orbs[j] * phase
-                out[ik, a * per_atom + j, 1] = chi[1] * orbs[j] * phase
-    for ik in range(nk):
-        flat = out[ik].reshape(ns, -1)
-        out[ik] = lowdin(flat, dV).reshape(ns, 2, -1)
-    return out.reshape(nk, ns, 2, n, n, n)
+    sel = np.arange(ns) if select is None else np.asarray(select)
+    chi = np.array([spinor_along(axes[a][0], axes[a][1], parallel=(j < n_par))
+                    for a in range(natoms) for j in range(per_atom)])  # (ns, 2)
+    nt = len(_TRIPLES)
+    tindex = {t: i for i, t in enumerate(_TRIPLES)}
+    # T[m, tau]: weight of triple tau in basis function m
+    T = np.zeros((9, nt))
+    for m, terms in enumerate(_BASIS_TERMS):
+        for c, px, py, pz in terms:
+            T[m, tindex[(px, py, pz)]] += c
+    real = np.dtype(dtype) == np.complex64
+    out = np.empty((len(kpts), len(sel), 2, n, n, n), dtype)
+    for ik, kv in enumerate(np.asarray(kpts, np.float64)):
+        F = [np.stack([_axis_factors(n, h[ax], L[ax], pos[a, ax], kv[ax], sigma) for a in range(natoms)])
+             for ax in range(3)]  # F[ax]: (natoms, 3, n)
+        # one-dimensional overlaps O[ax][a, p, b, q] = sum_j conj(F_ap(j)) F_bq(j)
+        O = [np.einsum("apj,bqj->apbq", f.conj(), f) for f in F]
+        # Gram of the triples: Gt[a tau, b tau'] = prod_ax O[ax][a, p_ax, b, q_ax] dV
+        Gt = np.empty((natoms, nt, natoms, nt), np.complex128)
+        for i, (px, py, pz) in enumerate(_TRIPLES):
+            for j, (qx, qy, qz) in enumerate(_TRIPLES):
+                Gt[:, i, :, j] = O[0][:, px, :, qx] * O[1][:, py, :, qy] * O[2][:, pz, :, qz] * dV
+        # orbital coefficients on the triples: Ct[a, tau, s] for the states s on atom a
+        Ct = np.zeros((natoms, nt, ns), np.complex128)
+        for a in range(natoms):
+            Ct[a, :, a * per_atom:(a + 1) * per_atom] = (coef[a] @ T).T
+        Ct = Ct.reshape(natoms * nt, ns)
+        S = (chi.conj() @ chi.T) * (Ct.conj().T @ Gt.reshape(natoms * nt, natoms * nt) @ Ct)
+        w, U = np.linalg.eigh(S)
+        Sm = (U * (1.0 / np.sqrt(w))) @ U.conj().T
+        # W[a tau, i, sigma] = sum_s Sm[s, i] Ct[a tau, s] chi[s, sigma]
+        W = np.stack([(Ct * chi[None, :, x]) @ Sm[:, sel] for x in range(2)], axis=-1)
+        W = W.reshape(natoms * nt, 2 * len(sel)).T
+        # plane factors P[a tau](y, x) = F_y(a, py) F_x(a, px)
+        P = np.stack([np.einsum("ay,ax->ayx", F[1][:, py], F[0][:, px]) for (px, py, pz) in _TRIPLES], axis=1)
+        P = P.reshape(natoms * nt, n * n)
+        Fz = np.stack([F[2][:, pz] for (px, py, pz) in _TRIPLES], axis=1).reshape(natoms * nt, n)
+        if np.isrealobj(P) and np.isrealobj(Fz):
+            # real basis (k = 0): real and imaginary parts as two real products
+            ft = np.float32 if real else np.float64
+            if real:
+                # single-precision products: factors below 1e-12 (their contributions lie far below
+                # complex64 resolution) are set to zero, so that no product underflows into the
+                # slow subnormal range
+                P = np.where(np.abs(P) < 1e-12, 0.0, P)
+                Fz = np.where(np.abs(Fz) < 1e-12, 0.0, Fz)
+            Wr, Wi = np.ascontiguousarray(W.real, dtype=ft), np.ascontiguousarray(W.imag, dtype=ft)
+            P = np.ascontiguousarray(P, dtype=ft)
+            for z in range(n):
+                fz = Fz[:, z].astype(ft)[None, :]
+                blk = out[ik, :, :, z].reshape(2 * len(sel), n * n)
+                blk.real = (Wr * fz) @ P
+                blk.imag = (Wi * fz) @ P
+        else:
+            if real:
+                W, P = W.astype(np.complex64), P.astype(np.complex64)
+            for z in range(n):
+                out[ik, :, :, z] = ((W * Fz[:, z][None, :].astype(W.dtype)) @ P).reshape(len(sel), 2, n, n)
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -342,6 +410,18 @@ def large(nsteps=200, seed=20250625, nstates=1024):
     times, A, B = laser_table(nsteps, dt)
     return Workload("large96", L, 96, pos, np.zeros(len(pos), np.int32), Z, rc, w, 2, D, lam, 5.0,
                     np.zeros((1, 3)), np.ones(1), np.ones((1, nstates)), dt, nsteps, seed, times, A, B)
+
+
+def large_axes(natoms, tilted=1, tilt_deg=20.0):
+    """Spin axes of the large supercell's atoms: along z, one atom tilted as in the cluster."""
+    return cluster_axes(natoms, tilted, tilt_deg)
+
+
+def large_states(wl, select=None, dtype=np.complex64):
+    """The large supercell's atomic-orbital spinors (8 per atom), complex64 by default (the
+    FP32-mixed storage; the complex128 array of all 1024 is 29 GB)."""
+    return atomic_orbital_states(wl.L, wl.n, wl.pos, wl.kpts, large_axes(len(wl.pos)), seed=wl.seed,
+                                 select=select, dtype=dtype)
 
 
 def small_parity(n=16, nstates=5, nk=2, seed=7, lam=0.02, lmax=2, field=True, natoms=3):

@@ -194,19 +194,9 @@ def test_error_paths_on_device(lib):
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-5)])
-def test_fused_term_path_matches_oracle(lib, precision, tol, monkeypatch):
-    """The fused Chebyshev term kernel (inverse xy FFT + epilogue + forward xy FFT in one launch)
-    gives the same results as the default five-launch term."""
-    monkeypatch.setenv("TDDFT_FUSED", "1")
-    wl = S.small_parity(n=16, nstates=3, nk=2, natoms=3)
-    psi0 = S.small_parity_states(wl)
-    rows, psi_g, o = run_pair(lib, wl, psi0, 2, (-20.0, 100.0), precision=precision)
-    for r in rows:
-        assert r["n"] <= tol and r["m"] <= tol
-
-
-def test_largest_grid_fp64_96(lib):
-    """Maximum grid (96^3) in FP64, one atom with SOC."""
+def test_largest_grid_96(lib, precision, tol):
+    """Maximum grid (96^3, the two-factor 8 x 12 FFT passes) in FP64 and FP32-mixed, one atom with
+    SOC and one spinor with both components occupied, one step against the oracle."""
     wl = S.small_parity(n=96, nstates=1, nk=1, natoms=1, field=False)
     Lc = 24.0
     wl.L = np.array([Lc, Lc, Lc])
@@ -224,10 +214,10 @@ def test_largest_grid_fp64_96(lib):
     psi0[0, 0, 1] = base * (0.3 - 0.5j) * np.exp(1j * r[..., 1] * g[2])
     psi0 /= math.sqrt((np.abs(psi0) ** 2).sum() * Lc ** 3 / 96 ** 3)
     # kinetic maximum 1/2 * 3 (pi / h)^2 = 237 Ha at h = 0.25 bohr
-    rows, psi_g, o = run_pair(lib, wl, psi0, 1, (-30.0, 270.0))
+    rows, psi_g, o = run_pair(lib, wl, psi0, 1, (-30.0, 270.0), precision=precision)
     for r_ in rows:
-        assert r_["n"] <= 1e-10 and r_["m"] <= 1e-10
-    assert rel(psi_g, o.psi) <= 1e-10
+        assert r_["n"] <= tol and r_["m"] <= tol
+    assert rel(psi_g, o.psi) <= tol
 
 
 @pytest.mark.parametrize("proj_mode,tol", [(3, 2e-5), (2, 3e-3)])
@@ -276,30 +266,6 @@ def test_atom_moments_match_oracle_on_symmetric_cluster(lib):
     assert np.abs(M - Mo).max() <= 1e-10 * np.abs(Mo).max()
     assert np.abs(N - No).max() <= 1e-10 * np.abs(No).max()
     assert np.allclose(M.sum(axis=0), E["M"], atol=1e-10)
-
-
-@pytest.mark.parametrize("n", [32, 48, 64])
-def test_cluster_kinetic_fp32_apply_h(lib, n, monkeypatch):
-    """FP32-mixed Hamiltonian with the one-kernel kinetic term (16-CTA clusters holding a whole
-    component in distributed shared memory) against the oracle, and against the three-pass
-    kinetic term of the same library."""
-    from paper_2506_21908_gb300 import _lib
-    wl = S.small_parity(n=n, nstates=2, nk=2, natoms=2)
-    psi0 = S.small_parity_states(wl)
-    outs = []
-    for cluster in ("1", "0"):
-        monkeypatch.setenv("TDDFT_CLUSTER", cluster)
-        h = _lib.TDDFT.from_workload(wl, precision=1, e_min=-20, e_max=400)
-        h.set_fields(wl.times, wl.A, wl.B)
-        h.set_states(psi0, 0.1)
-        outs.append(h.apply_hamiltonian(psi0))
-        h.close()
-    s = System.from_workload(wl)
-    o = Oracle(s, FieldTable(wl.times, wl.A, wl.B), wl.dt, psi0, t0=0.1, bounds=(-20, 400))
-    A, _ = o.f.at(0.1)
-    ref = s.apply_h(psi0, o.V, A)
-    assert rel(outs[0], ref) <= 2e-5
-    assert rel(outs[0], outs[1]) <= 2e-6
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-5)])
