@@ -209,7 +209,8 @@ KERNEL_SOURCES = {
     "epilogue": ("epilogue.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
     "fft_xy": ("kernels.cu", "fft_tma.cu", "bulk.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
     "fft_z_kinetic": ("kernels.cu", "fft.cuh", "impl.cuh", "kcommon.cuh"),
-    "proj_gather": ("kernels.cu", "proj_tc.cu", "proj_tile.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+    "proj_gather": ("kernels.cu", "proj_tile.cu", "bulk.cuh", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+    "proj_scatter": ("proj_tile.cu", "bulk.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
 }
 
 
@@ -417,7 +418,10 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-PROJ_NAMES = {1: "FP32 CUDA cores", 2: "TF32 tensor cores (tcgen05)", 3: "3xTF32 tensor cores (tcgen05)"}
+PROJ_NAMES = {1: "FP32 CUDA cores", 2: "TF32 tensor cores (tcgen05, brick by brick)",
+              3: "split TF32 x3 tensor cores (tcgen05, brick by brick)",
+              4: "split BF16 x3 tensor cores (tcgen05, brick by brick)",
+              5: "split FP16 x3 tensor cores (tcgen05, brick by brick)"}
 
 
 def psi0_states(wl):
@@ -578,7 +582,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
     ap.add_argument("--no-bcc", action="store_true")
-    ap.add_argument("--proj", type=int, default=1, help="projector contraction: " + str(PROJ_NAMES))
+    ap.add_argument("--proj", type=int, default=5, help="projector contraction: " + str(PROJ_NAMES))
     ap.add_argument("--no-propagators", action="store_true", help="skip the Taylor-4 / Crank-Nicolson comparison")
     ap.add_argument("--adj-steps", type=int, default=500)
     ap.add_argument("--adj-ckpt", type=int, default=50)

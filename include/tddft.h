@@ -58,10 +58,14 @@ typedef enum {
 enum { TDDFT_FP64 = 0, TDDFT_FP32_MIXED = 1 };
 enum { TDDFT_EXP_CHEBYSHEV = 0, TDDFT_EXP_TAYLOR = 1, TDDFT_EXP_CRANK_NICOLSON = 2 };
 enum { TDDFT_SPIN_NONCOLLINEAR = 0, TDDFT_SPIN_COLLINEAR = 1, TDDFT_SPIN_UNPOLARISED = 2 };
-/* Projector contraction: FP64 / FP32 on the CUDA cores, or on the tensor cores (tcgen05,
- * FP32-mixed precision with lmax = 2) as one TF32 product or as the split 3 x TF32 product
- * (hi*hi + hi*lo + lo*hi, close to FP32 accuracy); FP32 accumulation in every case. */
-enum { TDDFT_PROJ_FP64 = 0, TDDFT_PROJ_FP32 = 1, TDDFT_PROJ_TF32 = 2, TDDFT_PROJ_TF32X3 = 3 };
+/* Projector contraction (Eq. Vps with the L.S blocks): FP64 / FP32 on the CUDA cores, or on the
+ * tensor cores (tcgen05, FP32-mixed precision, grid size divisible by 16) as one TF32 product or as
+ * a split product hi*hi + hi*lo + lo*hi of TF32, BF16 or FP16 parts (each value = hi + lo; TF32 x3
+ * and FP16 x3 close to FP32 accuracy, BF16 x3 about 16 bits); FP32 accumulation in every case.  The
+ * tensor-core forms contract brick by brick (bricks of 32 or 16 x 8 x 8 grid points against every
+ * projector sphere reaching into them) for both the projection <beta~|psi> and V_NL psi. */
+enum { TDDFT_PROJ_FP64 = 0, TDDFT_PROJ_FP32 = 1, TDDFT_PROJ_TF32 = 2, TDDFT_PROJ_TF32X3 = 3,
+       TDDFT_PROJ_BF16X3 = 4, TDDFT_PROJ_F16X3 = 5 };
 
 /* Energies returned by tddft_observables, indices into E[TDDFT_NE]. */
 enum {
@@ -112,9 +116,10 @@ typedef struct {
 /* Run parameters.
  *   precision : TDDFT_FP64, or TDDFT_FP32_MIXED (spinors, FFTs, potential apply and projectors
  *               in FP32; density, XC, Hartree, energies and norms in FP64)
- *   proj_mode : TDDFT_PROJ_FP64 / TDDFT_PROJ_FP32 / TDDFT_PROJ_TF32 / TDDFT_PROJ_TF32X3 (the CUDA-core
- *               modes follow the precision; the tensor-core modes need FP32-mixed and lmax = 2,
- *               else TDDFT_ERR_UNSUPPORTED)
+ *   proj_mode : TDDFT_PROJ_FP64 / TDDFT_PROJ_FP32 (CUDA cores; they follow the precision) or one of
+ *               the tensor-core modes TDDFT_PROJ_TF32 / _TF32X3 / _BF16X3 / _F16X3 (FP32-mixed
+ *               precision and a grid size divisible by 16, else TDDFT_ERR_UNSUPPORTED; the discrete
+ *               adjoint uses the CUDA-core contraction in every mode)
  *   nk, kpts[nk][3] (1/bohr, cartesian), kw[nk] (weights)
  *   nstates   : propagated spinors per k-point; occ[nk][nstates] occupations f
  *   dt        : time step (may be negative to run backwards)
@@ -258,7 +263,8 @@ tddft_status tddft_info(tddft_handle h, int* K_full, int* K_half, double* e_min,
  * those launches (each spinor array a launch must read or write counted once; tables
  * shared by all spinors not counted).  Classes: 0 FFT xy-plane pass, 1 FFT z pass with
  * kinetic multiply, 2 Hamiltonian/Chebyshev epilogue, 3 projector gather, 4 density,
- * 5 potential (XC, Hartree, assembly), 6 other.  ncls <= 8; any output may be NULL. */
+ * 5 potential (XC, Hartree, assembly), 6 other, 7 projector scatter on the tensor cores.
+ * ncls <= 8; any output may be NULL. */
 tddft_status tddft_profile(tddft_handle h, int enable);
 tddft_status tddft_profile_read(tddft_handle h, int ncls, double* ms, long long* count, double* bytes);
 

@@ -15,10 +15,11 @@ LIB_PATH = os.path.join(HERE, "libtddft.so")
 
 FP64, FP32_MIXED = 0, 1
 SPIN_NONCOLLINEAR, SPIN_COLLINEAR, SPIN_UNPOLARISED = 0, 1, 2
-PROJ_FP64, PROJ_FP32, PROJ_TF32, PROJ_TF32X3 = 0, 1, 2, 3
+PROJ_FP64, PROJ_FP32, PROJ_TF32, PROJ_TF32X3, PROJ_BF16X3, PROJ_F16X3 = 0, 1, 2, 3, 4, 5
 EXP_CHEBYSHEV, EXP_TAYLOR, EXP_CRANK_NICOLSON = 0, 1, 2
 E_NAMES = ["kin", "nl", "loc", "H", "xc", "Z", "total", "t", "xc_pot", "N"]
-KERNEL_CLASSES = ["fft_xy", "fft_z_kinetic", "epilogue", "proj_gather", "density", "potential", "other"]
+KERNEL_CLASSES = ["fft_xy", "fft_z_kinetic", "epilogue", "proj_gather", "density", "potential", "other",
+                  "proj_scatter"]
 
 # Every entry point declared in include/tddft.h (checked by the CPU tests).
 EXPORTS = ["tddft_create", "tddft_set_fields", "tddft_set_states", "tddft_get_states", "tddft_step",

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <cstdint>
 #include <complex>
 #include <map>
 #include <array>
@@ -207,7 +208,11 @@ struct tddft_ctx {
   double* red_part = nullptr;  // partials of the two-pass reductions (band dots, field sums)
   int* owner = nullptr;      // nearest atom of each grid point (per-atom moments)
   double* atom_sums = nullptr;
-  float* tc_part = nullptr;  // tensor-core gather partial products
+  // tile-centric tensor-core projectors (proj_mode TF32, TF32X3, BF16X3, F16X3)
+  bool tile = false;
+  TileDev td;
+  float* tile_part = nullptr;  // gather partial products, nk * groups * td.part_layer floats
+  void* vnl = nullptr;         // V_NL T_k from the tensor-core scatter (spinor layout)
   int* tc_err = nullptr;     // wait errors: bit 1 tensor-core projector, bit 2 bulk-copy FFT pass
   void *g_tab = nullptr, *s_tab = nullptr, *Dmat = nullptr;
   void *g_row = nullptr, *s_row = nullptr, *nrm = nullptr;
@@ -497,6 +502,214 @@ tddft_status build_tables(tddft_ctx* c, const tddft_projectors* pj, const int* s
   return TDDFT_OK;
 }
 
+// ------------------------------------------------------------------ brick tables of the tensor-core projectors
+// Rounding of the operand values to the tensor-core element kinds (round to nearest; TF32 ties
+// away from zero, as the hardware conversion does; BF16 and FP16 ties to even).
+uint32_t f32_bits(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  return u;
+}
+float bits_f32(uint32_t u) {
+  float x;
+  std::memcpy(&x, &u, 4);
+  return x;
+}
+uint32_t to_tf32(float x) { return (f32_bits(x) + 0x1000u) & 0xFFFFE000u; }
+uint32_t to_bf16(float x) {
+  const uint32_t u = f32_bits(x);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+uint32_t to_f16(float f) {
+  const uint32_t x = f32_bits(f);
+  const uint32_t sign = (x >> 16) & 0x8000u;
+  const int e = (int)((x >> 23) & 0xFFu) - 127 + 15;
+  uint32_t m = x & 0x7FFFFFu;
+  if (((x >> 23) & 0xFFu) == 0xFFu) return sign | 0x7C00u | (m ? 0x200u : 0u);
+  if (e >= 31) return sign | 0x7C00u;
+  if (e <= 0) {  // subnormal half: value = hm 2^-24
+    if (e < -10) return sign;
+    m |= 0x800000u;
+    const int shift = 14 - e;
+    uint32_t hm = m >> shift;
+    const uint32_t rem = m & ((1u << shift) - 1u), half = 1u << (shift - 1);
+    if (rem > half || (rem == half && (hm & 1u))) ++hm;
+    return sign | hm;
+  }
+  uint32_t r = sign | ((uint32_t)e << 10) | (m >> 13);
+  const uint32_t rem = m & 0x1FFFu;
+  if (rem > 0x1000u || (rem == 0x1000u && (r & 1u))) ++r;  // a carry rounds into the exponent
+  return r;
+}
+double from_kind(int ek, uint32_t v) {
+  if (ek == TILE_TF32) return bits_f32(v);
+  if (ek == TILE_BF16) return bits_f32(v << 16);
+  const uint32_t sign = (v & 0x8000u) << 16, e = (v >> 10) & 0x1Fu, m = v & 0x3FFu;
+  if (e == 0) return (sign ? -1.0 : 1.0) * std::ldexp((double)m, -24);
+  if (e == 31) return bits_f32(sign | 0x7F800000u | (m << 13));
+  return bits_f32(sign | ((e - 15 + 127) << 23) | (m << 13));
+}
+uint32_t to_kind(int ek, double x) {
+  if (ek == TILE_TF32) return to_tf32((float)x);
+  if (ek == TILE_BF16) return to_bf16((float)x);
+  return to_f16((float)x);
+}
+
+struct TileHost {
+  int BX = 32, nbx = 0, nby = 0, nbz = 0, smax = 0, kch_max = 0;
+  std::vector<int> it_brick, it_nslot, it_npad, it_kch, slot_atom, a_ptr, a_item, a_slot;
+  std::vector<long long> it_goff, it_soff, it_poff;
+  std::vector<float> slot_delta;          // [nitems][smax][4]
+  std::vector<unsigned char> g_tab, s_tab;
+  long long part_layer = 0;
+};
+
+// Bricks of BX x 8 x 8 points; per brick the atom images ("slots") whose spheres reach into it,
+// and the real projector values beta_{slot,p}(r) of every brick point (from the per-atom entries
+// of build_tables, FP64), rounded to the operand kind in the swizzled K-major layout:
+//   gather  (operand B): per chunk of 128-byte rows of points, npad rows (slot, p) x 128 bytes;
+//   scatter (operand A): per tile of 128 points and chunk of 128-byte rows of (slot, p), 128 rows.
+// With three products each chunk holds the hi part, then lo = value - hi.
+tddft_status build_tile_tables(tddft_ctx* c, const HostTables& ht, int ek, int terms, TileHost& th) {
+  const int N = c->N, nlm = c->nlm;
+  if (N % 16 != 0) return c->fail(TDDFT_ERR_UNSUPPORTED, "tensor-core projectors need a grid size divisible by 16");
+  th.BX = (N % 32 == 0) ? 32 : 16;
+  th.nbx = N / th.BX;
+  th.nby = th.nbz = N / 8;
+  th.smax = 256 / nlm;
+  const int esz = (ek == TILE_TF32) ? 4 : 2, epr = 128 / esz, npart = (terms == 3) ? 2 : 1;
+  const int pts = th.BX * 64, nch = pts / epr, ntile = pts / 128;
+  const int nbr = th.nbx * th.nby * th.nbz;
+  const int tab = 3 + nlm;
+  const double h[3] = {c->L[0] / N, c->L[1] / N, c->L[2] / N};
+  // slot of (atom, image) in each brick, in order of first appearance (atoms ascending)
+  std::vector<std::vector<long long>> keys(nbr);
+  struct Ent { int brick, slot, local; size_t e; };
+  std::vector<Ent> ents;
+  ents.reserve(ht.g_idx.size());
+  for (int a = 0; a < c->natoms; ++a) {
+    for (int e = ht.g_ptr[a]; e < ht.g_ptr[a + 1]; ++e) {
+      const int idx = ht.g_idx[e];
+      const int x = idx % N, y = (idx / N) % N, z = idx / (N * N);
+      const double* d = &ht.g_tab[(size_t)e * tab];
+      int img[3];
+      const int xyz[3] = {x, y, z};
+      for (int ax = 0; ax < 3; ++ax)
+        img[ax] = (int)std::lround((xyz[ax] * h[ax] - d[ax] - c->pos[3 * a + ax]) / c->L[ax]);
+      const long long key = (long long)a * 27 + (img[0] + 1) * 9 + (img[1] + 1) * 3 + (img[2] + 1);
+      const int b = (x / th.BX) + th.nbx * ((y / 8) + th.nby * (z / 8));
+      auto& kv = keys[b];
+      int sl = -1;
+      for (int i = 0; i < (int)kv.size(); ++i)
+        if (kv[i] == key) { sl = i; break; }
+      if (sl < 0) {
+        sl = (int)kv.size();
+        kv.push_back(key);
+      }
+      const int local = (x % th.BX) + th.BX * ((y % 8) + 8 * (z % 8));
+      ents.push_back({b, sl, local, (size_t)e});
+    }
+  }
+  std::vector<int> item_of(nbr, -1);
+  for (int b = 0; b < nbr; ++b) {
+    if (keys[b].empty()) continue;
+    if ((int)keys[b].size() > th.smax)
+      return c->fail(TDDFT_ERR_UNSUPPORTED, "too many projector spheres reach one brick for the tensor-core path");
+    item_of[b] = (int)th.it_brick.size();
+    th.it_brick.push_back(b);
+  }
+  const int nit = (int)th.it_brick.size();
+  th.it_nslot.resize(nit);
+  th.it_npad.resize(nit);
+  th.it_kch.resize(nit);
+  th.it_goff.resize(nit);
+  th.it_soff.resize(nit);
+  th.it_poff.resize(nit);
+  th.slot_atom.assign((size_t)nit * th.smax, 0);
+  th.slot_delta.assign((size_t)nit * th.smax * 4, 0.0f);
+  long long goff = 0, soff = 0, poff = 0;
+  for (int i = 0; i < nit; ++i) {
+    const int b = th.it_brick[i];
+    const int ns = (int)keys[b].size();
+    th.it_nslot[i] = ns;
+    th.it_npad[i] = std::max(16, (ns * nlm + 15) / 16 * 16);
+    th.it_kch[i] = (ns * nlm + epr - 1) / epr;
+    th.kch_max = std::max(th.kch_max, th.it_kch[i]);
+    th.it_goff[i] = goff;
+    th.it_soff[i] = soff;
+    th.it_poff[i] = poff;
+    goff += (long long)nch * npart * th.it_npad[i] * 128;
+    soff += (long long)ntile * th.it_kch[i] * npart * 128 * 128;
+    poff += (long long)ns * nlm * 128;
+    const int bx = b % th.nbx, by = (b / th.nbx) % th.nby, bz = b / (th.nbx * th.nby);
+    const double rb[3] = {bx * th.BX * h[0], by * 8 * h[1], bz * 8 * h[2]};
+    for (int sl = 0; sl < ns; ++sl) {
+      const long long key = keys[b][sl];
+      const int a = (int)(key / 27), r = (int)(key % 27);
+      const int img[3] = {r / 9 - 1, (r / 3) % 3 - 1, r % 3 - 1};
+      th.slot_atom[(size_t)i * th.smax + sl] = a;
+      for (int ax = 0; ax < 3; ++ax)
+        th.slot_delta[((size_t)i * th.smax + sl) * 4 + ax] =
+            (float)(rb[ax] - (c->pos[3 * a + ax] + img[ax] * c->L[ax]));
+    }
+  }
+  th.part_layer = poff;
+  // dense projector values per item: vals[item][slot * nlm + p][local point]
+  std::vector<long long> vbase(nit + 1, 0);
+  for (int i = 0; i < nit; ++i) vbase[i + 1] = vbase[i] + (long long)th.it_nslot[i] * nlm * pts;
+  std::vector<double> vals((size_t)vbase[nit], 0.0);
+  for (const Ent& en : ents) {
+    const int i = item_of[en.brick];
+    const double* t = &ht.g_tab[en.e * tab + 3];
+    for (int p = 0; p < nlm; ++p) vals[(size_t)vbase[i] + ((size_t)en.slot * nlm + p) * pts + en.local] = t[p];
+  }
+  auto sw = [](size_t off) { return off ^ (((off >> 7) & 7u) << 4); };
+  auto store = [&](std::vector<unsigned char>& dst, size_t base, size_t off, uint32_t v) {
+    unsigned char* q = dst.data() + base + sw(off);
+    if (esz == 4) std::memcpy(q, &v, 4);
+    else { const uint16_t w = (uint16_t)v; std::memcpy(q, &w, 2); }
+  };
+  th.g_tab.assign((size_t)goff, 0);
+  th.s_tab.assign((size_t)soff, 0);
+  for (int i = 0; i < nit; ++i) {
+    const int ns = th.it_nslot[i], npad = th.it_npad[i], kch = th.it_kch[i];
+    const double* v = &vals[(size_t)vbase[i]];
+    for (int n = 0; n < ns * nlm; ++n)
+      for (int lp = 0; lp < pts; ++lp) {
+        const double x = v[(size_t)n * pts + lp];
+        if (x == 0.0) continue;
+        const uint32_t hi = to_kind(ek, x);
+        const uint32_t lo = to_kind(ek, x - from_kind(ek, hi));
+        // gather: chunk lp / epr, row n, element lp % epr
+        const int ch = lp / epr, el = lp % epr;
+        const size_t gb = (size_t)th.it_goff[i] + (size_t)ch * npart * npad * 128;
+        store(th.g_tab, gb, (size_t)n * 128 + (size_t)el * esz, hi);
+        if (npart == 2) store(th.g_tab, gb + (size_t)npad * 128, (size_t)n * 128 + (size_t)el * esz, lo);
+        // scatter: tile lp / 128, K chunk n / epr, row lp % 128, element n % epr
+        const int tl = lp / 128, row = lp % 128, kc = n / epr, ke = n % epr;
+        const size_t sb = (size_t)th.it_soff[i] + ((size_t)tl * kch + kc) * npart * 128 * 128;
+        store(th.s_tab, sb, (size_t)row * 128 + (size_t)ke * esz, hi);
+        if (npart == 2) store(th.s_tab, sb + 128 * 128, (size_t)row * 128 + (size_t)ke * esz, lo);
+      }
+  }
+  // (item, slot) pairs of every atom, items ascending
+  th.a_ptr.assign(c->natoms + 1, 0);
+  for (int i = 0; i < nit; ++i)
+    for (int sl = 0; sl < th.it_nslot[i]; ++sl) th.a_ptr[th.slot_atom[(size_t)i * th.smax + sl] + 1]++;
+  for (int a = 0; a < c->natoms; ++a) th.a_ptr[a + 1] += th.a_ptr[a];
+  th.a_item.assign(th.a_ptr[c->natoms], 0);
+  th.a_slot.assign(th.a_ptr[c->natoms], 0);
+  std::vector<int> fill(th.a_ptr.begin(), th.a_ptr.end() - 1);
+  for (int i = 0; i < nit; ++i)
+    for (int sl = 0; sl < th.it_nslot[i]; ++sl) {
+      const int a = th.slot_atom[(size_t)i * th.smax + sl];
+      th.a_item[fill[a]] = i;
+      th.a_slot[fill[a]] = sl;
+      ++fill[a];
+    }
+  return TDDFT_OK;
+}
+
 template <typename R>
 tddft_status upload_typed(tddft_ctx* c, void** dst, const std::vector<double>& src, const char* what) {
   std::vector<R> tmp(src.begin(), src.end());
@@ -574,7 +787,9 @@ cudaError_t epilogue(tddft_ctx* c, const void* kin, const void* Tk, const void* 
                      void* acc2, const R* V, const ProjTables<R>& pt, const void* dc, int nkb, const EpiParams& ep) {
   EpiParams e = ep;
   e.spinor_pairs = c->epi_pairs ? 1 : 0;
-  return launch_epilogue<R>(c->st, c->N, kin, Tk, Tkm1, Tout, acc1, acc2, V, pt, dc, nkb, e);
+  // with the tensor-core projectors (tables without atoms) V_NL T_k waits in vnl
+  const void* kin2 = (c->tile && pt.natoms == 0) ? c->vnl : nullptr;
+  return launch_epilogue<R>(c->st, c->N, kin, kin2, Tk, Tkm1, Tout, acc1, acc2, V, pt, dc, nkb, e);
 }
 
 // Kinetic part of H on all spinors: out = T in (three FFT passes).
@@ -601,13 +816,12 @@ template <typename R> tddft_status gather(tddft_ctx* c, const void* in, const do
   fill_shifts(c, A, ep.shift);
   ProjTables<R> pt = c->tables<R>();
   const double by = (double)c->n_entries * c->nkb * 2 * 2 * sizeof(R);  // psi at the sphere points
-  if (c->prec != TDDFT_FP64 && c->proj_mode >= TDDFT_PROJ_TF32) {
-    ProjTables<float> pf = c->tables<float>();
+  if (c->tile) {
+    const double byt = (double)c->psi_elems() * 2 * sizeof(float);  // psi read once
     return c->launch_on(sg, KC_PROJ, "projector gather (tensor cores)", [&] {
-      return launch_proj_gather_tc(sg, c->N, in, c->nk, c->nb, pf, c->dV, ep,
-                                   c->proj_mode == TDDFT_PROJ_TF32X3 ? 1 : 0, c->tc_part, c->cbuf, c->dcbuf,
-                                   c->tc_err);
-    }, by);
+      return launch_tile_gather(sg, c->N, in, c->nk, c->nb, c->td, c->dV, ep, (const float*)c->Dmat, c->tile_part,
+                                c->cbuf, c->dcbuf, c->tc_err);
+    }, byt);
   }
   return c->launch_on(sg, KC_PROJ, "projector gather", [&] {
     return launch_proj_gather<R>(sg, c->N, in, c->nkb, pt, c->dV, ep, c->cbuf, c->dcbuf);
@@ -616,11 +830,14 @@ template <typename R> tddft_status gather(tddft_ctx* c, const void* in, const do
 
 // The kinetic passes and the projector gather of one term: with a second stream the gather runs
 // beside the FFT passes (fork after the previous epilogue, join before the next one).
+// With the tensor-core projectors the scatter then forms V_NL psi in vnl.
+template <typename R> tddft_status nl_scatter(tddft_ctx* c, const double A[3]);
 template <typename R> tddft_status kinetic_and_gather(tddft_ctx* c, const void* cur, const double A[3]) {
   tddft_status s;
   if (!c->side || c->natoms == 0) {
     if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
-    return gather<R>(c, cur, A);
+    if ((s = gather<R>(c, cur, A))) return s;
+    return nl_scatter<R>(c, A);
   }
   if ((s = c->cuda(cudaEventRecord(c->ev_fork, c->st), "fork")) ||
       (s = c->cuda(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork wait")))
@@ -628,7 +845,27 @@ template <typename R> tddft_status kinetic_and_gather(tddft_ctx* c, const void* 
   if ((s = gather<R>(c, cur, A, c->side))) return s;
   if ((s = c->cuda(cudaEventRecord(c->ev_join, c->side), "join"))) return s;
   if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
-  return c->cuda(cudaStreamWaitEvent(c->st, c->ev_join, 0), "join wait");
+  if ((s = c->cuda(cudaStreamWaitEvent(c->st, c->ev_join, 0), "join wait"))) return s;
+  return nl_scatter<R>(c, A);
+}
+
+// Tensor-core projectors: vnl = V_NL in, from the D c of the gather (main stream, after the
+// join); the epilogue then adds vnl instead of running its own projector scatter.
+template <typename R> tddft_status nl_scatter(tddft_ctx* c, const double A[3]) {
+  if (!c->tile) return TDDFT_OK;
+  EpiParams ep{};
+  ep.nstates = c->nb;
+  fill_shifts(c, A, ep.shift);
+  const double by = (double)c->psi_elems() * 2 * sizeof(float);  // vnl written once
+  return c->launch(KC_SCATTER, "projector scatter (tensor cores)", [&] {
+    return launch_tile_scatter(c->st, c->N, c->vnl, c->nk, c->nb, c->td, ep, c->dcbuf, c->tc_err);
+  }, by);
+}
+// Projector tables for the epilogue: none when the tensor cores already added V_NL psi.
+template <typename R> ProjTables<R> epi_tables(const tddft_ctx* c) {
+  ProjTables<R> pt = c->tables<R>();
+  if (c->tile) pt.natoms = 0;
+  return pt;
 }
 
 // Accumulation schedule of one series acc = sum_{i <= Ka} cf[i] T_i in the unfused recurrence:
@@ -667,7 +904,7 @@ tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double
   ep.inv_delta = 1.0 / (0.5 * (c->emax - c->emin));
   ep.nstates = c->nb;
   fill_shifts(c, A, ep.shift);
-  ProjTables<R> pt = c->tables<R>();
+  ProjTables<R> pt = epi_tables<R>(c);
   const void* prev = in;
   const void* cur = in;
   tddft_status s;
@@ -708,7 +945,7 @@ tddft_status taylor_series(tddft_ctx* c, const void* in, bool vcur, const double
   fill_shifts(c, A, ep.shift);
   ep.mode = EPI_TAYLOR;
   ep.use_acc1 = 1;
-  ProjTables<R> pt = c->tables<R>();
+  ProjTables<R> pt = epi_tables<R>(c);
   const R* Vr = vsel<R>(c, vcur);
   const void* cur = in;
   for (int k = 1; k <= K; ++k) {
@@ -1436,11 +1673,12 @@ template <typename R> tddft_status do_apply_h(tddft_ctx* c, const void* in, void
   }
   if ((s = kinetic<R>(c, c->Ta, c->tmp, A))) return s;
   if ((s = gather<R>(c, c->Ta, A))) return s;
+  if ((s = nl_scatter<R>(c, A))) return s;
   EpiParams ep{};
   ep.mode = EPI_APPLY;
   ep.nstates = c->nb;
   fill_shifts(c, A, ep.shift);
-  ProjTables<R> pt = c->tables<R>();
+  ProjTables<R> pt = epi_tables<R>(c);
   const R* Vr = vsel<R>(c, true);
   if ((s = c->launch(KC_EPI, "apply H", [&] {
          return epilogue<R>(c, c->tmp, c->Ta, nullptr, c->Tb, nullptr, nullptr, Vr, pt, c->dcbuf, c->nkb, ep);
@@ -1480,7 +1718,7 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   if (pr->precision != TDDFT_FP64 && pr->precision != TDDFT_FP32_MIXED) return c->fail(TDDFT_ERR_ARG, "bad precision");
   c->prec = pr->precision;
   c->proj_mode = pr->proj_mode;
-  if (c->proj_mode < TDDFT_PROJ_FP64 || c->proj_mode > TDDFT_PROJ_TF32X3) return c->fail(TDDFT_ERR_ARG, "bad proj_mode");
+  if (c->proj_mode < TDDFT_PROJ_FP64 || c->proj_mode > TDDFT_PROJ_F16X3) return c->fail(TDDFT_ERR_ARG, "bad proj_mode");
   if (pr->nk < 1 || pr->nk > kMaxK || !pr->kpts || !pr->kw) return c->fail(TDDFT_ERR_ARG, "nk must be 1..16 with kpts and kw");
   if (pr->nstates < 1 || !pr->occ) return c->fail(TDDFT_ERR_ARG, "nstates must be >= 1 with occ");
   c->nk = pr->nk;
@@ -1548,8 +1786,11 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
   }
   c->lmax = c->natoms > 0 ? pj->lmax : 0;
   c->nlm = (c->lmax + 1) * (c->lmax + 1);
-  if (c->proj_mode >= TDDFT_PROJ_TF32 && c->natoms > 0 && (c->prec == TDDFT_FP64 || c->nlm != 9))
-    return c->fail(TDDFT_ERR_UNSUPPORTED, "tensor-core projectors need FP32-mixed precision and lmax = 2");
+  if (c->proj_mode >= TDDFT_PROJ_TF32 && c->prec == TDDFT_FP64)
+    return c->fail(TDDFT_ERR_UNSUPPORTED, "tensor-core projectors need FP32-mixed precision");
+  c->tile = c->proj_mode >= TDDFT_PROJ_TF32 && c->natoms > 0;
+  if (c->tile && c->N % 16 != 0)
+    return c->fail(TDDFT_ERR_UNSUPPORTED, "tensor-core projectors need a grid size divisible by 16");
   c->r_cut = pj->r_cut;
   c->pos.assign(atoms->pos, atoms->pos + 3 * c->natoms);
   std::vector<double> Zr(2 * std::max(1, c->natoms), 0.0);
@@ -1586,9 +1827,6 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
       (s = c->alloc(&c->rho_part, (size_t)density_groups(N3, c->nkb) * 4 * N3 * 8, "density partials")))
     return s;
   if ((s = c->alloc(&c->tc_err, 16, "tc flag")) || (s = c->cuda(cudaMemset(c->tc_err, 0, 16), "tc flag init"))) return s;
-  if (c->prec != TDDFT_FP64 && c->proj_mode >= TDDFT_PROJ_TF32 && c->natoms > 0 &&
-      (s = c->alloc(&c->tc_part, proj_tc_part_floats(c->natoms, c->nk, c->nb) * sizeof(float), "tc partials")))
-    return s;
   if ((s = c->cuda(cudaMemset(c->flag, 0, 16), "flag init"))) return s;
 
   // ---- twiddles exp(-2 pi i t / N)
@@ -1680,7 +1918,52 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
       if ((s = upload_typed<float>(c, &c->g_row, ht.g_row, "g_row")) || (s = upload_typed<float>(c, &c->s_row, ht.s_row, "s_row")) ||
           (s = upload_typed<float>(c, &c->nrm, ht.nrm, "nrm")) || (s = upload_typed<float>(c, &c->Dmat, ht.Dmat, "D")))
         return s;
-      if (c->proj_mode >= TDDFT_PROJ_TF32 && (s = upload_typed<float>(c, &c->g_tab, ht.g_tab, "g_tab"))) return s;
+    }
+    if (c->tile) {
+      const int ek = (c->proj_mode == TDDFT_PROJ_BF16X3) ? TILE_BF16 : (c->proj_mode == TDDFT_PROJ_F16X3) ? TILE_F16 : TILE_TF32;
+      const int terms = (c->proj_mode == TDDFT_PROJ_TF32) ? 1 : 3;
+      TileHost th;
+      if ((s = build_tile_tables(c, ht, ek, terms, th))) return s;
+      if (tile_scatter_smem(ek, terms, th.kch_max) > 227 * 1024)
+        return c->fail(TDDFT_ERR_UNSUPPORTED, "too many projector spheres reach one brick for the tensor-core scatter");
+      TileDev& td = c->td;
+      td.ek = ek;
+      td.terms = terms;
+      td.BX = th.BX;
+      td.nbx = th.nbx;
+      td.nby = th.nby;
+      td.nbz = th.nbz;
+      td.nitems = (int)th.it_brick.size();
+      td.natoms = c->natoms;
+      td.nlm = c->nlm;
+      td.smax = th.smax;
+      td.kch_max = th.kch_max;
+      for (int a = 0; a < 3; ++a) td.h[a] = c->L[a] / c->N;
+      td.part_layer = (size_t)th.part_layer;
+      int *ib, *ins, *inp, *ikc, *sa, *ap, *ai, *as;
+      long long *igo, *iso, *ipo;
+      float* sd;
+      unsigned char *gt, *st2;
+      if ((s = upload(c, &ib, th.it_brick, "tile bricks")) || (s = upload(c, &ins, th.it_nslot, "tile slots")) ||
+          (s = upload(c, &inp, th.it_npad, "tile npad")) || (s = upload(c, &ikc, th.it_kch, "tile kch")) ||
+          (s = upload(c, &igo, th.it_goff, "tile goff")) || (s = upload(c, &iso, th.it_soff, "tile soff")) ||
+          (s = upload(c, &ipo, th.it_poff, "tile poff")) || (s = upload(c, &sa, th.slot_atom, "tile slot atoms")) ||
+          (s = upload(c, &sd, th.slot_delta, "tile slot deltas")) || (s = upload(c, &gt, th.g_tab, "tile gather table")) ||
+          (s = upload(c, &st2, th.s_tab, "tile scatter table")) || (s = upload(c, &ap, th.a_ptr, "tile atom ptr")) ||
+          (s = upload(c, &ai, th.a_item, "tile atom items")) || (s = upload(c, &as, th.a_slot, "tile atom slots")))
+        return s;
+      td.it_brick = ib; td.it_nslot = ins; td.it_npad = inp; td.it_kch = ikc;
+      td.it_goff = igo; td.it_soff = iso; td.it_poff = ipo;
+      td.slot_atom = sa; td.slot_delta = reinterpret_cast<const float4*>(sd);
+      td.g_tab = gt; td.s_tab = st2;
+      td.a_ptr = ap; td.a_item = ai; td.a_slot = as;
+      const size_t groups = (size_t)(2 * c->nb + 63) / 64;
+      if ((s = c->alloc(&c->tile_part, (size_t)c->nk * groups * td.part_layer * sizeof(float) + 16, "tile partials")))
+        return s;
+      // points of bricks without projectors are never written by the scatter: zero once
+      if ((s = c->alloc(&c->vnl, c->psi_elems() * 2 * sizeof(float), "vnl")) ||
+          (s = c->cuda(cudaMemset(c->vnl, 0, c->psi_elems() * 2 * sizeof(float)), "vnl init")))
+        return s;
     }
   }
   return c->cuda(cudaDeviceSynchronize(), "create sync");

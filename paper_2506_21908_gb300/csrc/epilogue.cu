@@ -30,7 +30,8 @@ template <int AK> struct EpiMinBlocks<float, AK> { static constexpr int value = 
 
 template <typename R, int NLM, int AK, int SP>
 __global__ void __launch_bounds__(256, EpiMinBlocks<R, AK>::value)
-k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::type* Tk,
+k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::type* __restrict__ kin2,
+           const typename CT<R>::type* Tk,
            const typename CT<R>::type* Tkm1, typename CT<R>::type* Tout, typename CT<R>::type* acc1,
            typename CT<R>::type* acc2, const R* __restrict__ V, size_t N3, ProjTables<R> pt,
            const typename CT<R>::type* __restrict__ dc, EpiParams ep) {
@@ -64,7 +65,12 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
     if constexpr (SP) prefetch_l2(b + o + step);
   };
   const Pair<C> pu2 = ld(Tk, ou), pd2 = ld(Tk, od);
-  const Pair<C> ku2 = ld(kin, ou), kd2 = ld(kin, od);
+  Pair<C> ku2 = ld(kin, ou), kd2 = ld(kin, od);
+  if (kin2) {  // V_NL psi from the tensor-core scatter, added to the kinetic part
+    const Pair<C> vu = ld(kin2, ou), vd = ld(kin2, od);
+    ku2 = {cadd(ku2.a, vu.a), cadd(ku2.b, vu.b)};
+    kd2 = {cadd(kd2.a, vd.a), cadd(kd2.b, vd.b)};
+  }
   // Chebyshev terms: every input is requested before any arithmetic (more loads in flight)
   const bool cheb = AK < 2 || ep.mode == EPI_RECUR || ep.mode == EPI_FIRST;
   const bool rec = ep.mode == EPI_RECUR;
@@ -199,9 +205,9 @@ static void epi_sp(bool sp, int ak, dim3 grid, size_t smem, cudaStream_t st, A..
 }
 
 template <typename R>
-cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* Tk, const void* Tkm1, void* Tout,
-                            void* acc1, void* acc2, const R* V, const ProjTables<R>& pt, const void* dc, int nkb,
-                            const EpiParams& ep) {
+cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* kin2, const void* Tk, const void* Tkm1,
+                            void* Tout, void* acc1, void* acc2, const R* V, const ProjTables<R>& pt, const void* dc,
+                            int nkb, const EpiParams& ep) {
   using C = typename CT<R>::type;
   const size_t N3 = (size_t)N * N * N;
   // spinor pairs need an even number of states, so that a pair shares its k-point
@@ -214,7 +220,7 @@ cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void*
   const size_t smem = epx.dc_staged ? dcb : 0;
   const bool cheb = ep.mode == EPI_FIRST || ep.mode == EPI_RECUR;
   const int ak = !cheb ? 2 : (ep.use_acc2 ? 2 : (ep.use_acc1 ? 1 : 0));
-#define EPI_ARGS (const C*)kin, (const C*)Tk, (const C*)Tkm1, (C*)Tout, (C*)acc1, (C*)acc2, V, N3, pt, (const C*)dc, epx
+#define EPI_ARGS (const C*)kin, (const C*)kin2, (const C*)Tk, (const C*)Tkm1, (C*)Tout, (C*)acc1, (C*)acc2, V, N3, pt, (const C*)dc, epx
   switch (nlm) {
     case 0: epi_sp<R, 0>(sp, ak, grid, smem, st, EPI_ARGS); break;
     case 1: epi_sp<R, 1>(sp, ak, grid, smem, st, EPI_ARGS); break;
@@ -228,8 +234,8 @@ cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void*
 
 
 #define TDDFT_EPI_INST(R)                                                                                       \
-  template cudaError_t launch_epilogue<R>(cudaStream_t, int, const void*, const void*, const void*, void*, void*, \
-                                          void*, const R*, const ProjTables<R>&, const void*, int,              \
+  template cudaError_t launch_epilogue<R>(cudaStream_t, int, const void*, const void*, const void*, const void*,  \
+                                          void*, void*, void*, const R*, const ProjTables<R>&, const void*, int, \
                                           const EpiParams&);
 
 TDDFT_EPI_INST(float)

@@ -13,7 +13,8 @@ constexpr int kMaxK = 16;      // k-points per handle
 constexpr int kMaxNLM = 9;     // (lmax + 1)^2 with lmax <= 2
 constexpr int kNumCls = 8;     // profiling classes
 
-enum KernelClass { KC_FFT_XY = 0, KC_FFT_Z = 1, KC_EPI = 2, KC_PROJ = 3, KC_DENS = 4, KC_POT = 5, KC_OTHER = 6 };
+enum KernelClass { KC_FFT_XY = 0, KC_FFT_Z = 1, KC_EPI = 2, KC_PROJ = 3, KC_DENS = 4, KC_POT = 5, KC_OTHER = 6,
+                   KC_SCATTER = 7 };
 
 // Multiplier of the z pass: kinetic 1/2|G + s_k|^2 * scale, Poisson 4 pi / G^2 * scale.
 struct ZParams {
@@ -76,8 +77,9 @@ template <typename R>
 cudaError_t launch_proj_gather(cudaStream_t st, int N, const void* psi, int nkb, const ProjTables<R>& pt,
                                double dV, const EpiParams& ep, void* c_out, void* dc_out);
 template <typename R>
-cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* Tk, const void* Tkm1,
-                            void* Tout, void* acc1, void* acc2, const R* V, const ProjTables<R>& pt,
+// kin: the kinetic part of H T_k; kin2 (may be null): V_NL T_k from the tensor-core scatter.
+cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void* kin2, const void* Tk,
+                            const void* Tkm1, void* Tout, void* acc1, void* acc2, const R* V, const ProjTables<R>& pt,
                             const void* dc, int nkb, const EpiParams& ep);
 // rho_v of all spinors; part (density_groups(N3, nkb) x 4 x N3 doubles, may be null) lets the
 // band sum run as several groups reduced in a fixed order.
@@ -114,11 +116,45 @@ cudaError_t launch_nm_from_rho(cudaStream_t st, size_t N3, const double* rho, do
 // min v, max v, max |b| of the potential (out3); part: field_sums_part_doubles() scratch.
 cudaError_t launch_window_extrema(cudaStream_t st, size_t N3, const double* V, double* part, double* out3);
 
-// Tensor-core projector contraction (tcgen05 kind::tf32), FP32-mixed path, l <= 2.
-cudaError_t launch_proj_gather_tc(cudaStream_t st, int N, const void* psi, int nk, int nstates,
-                                  const ProjTables<float>& pt, double dV, const EpiParams& ep, int split3,
-                                  float* part, void* c_out, void* dc_out, int* err);
-size_t proj_tc_part_floats(int natoms, int nk, int nstates);
+// ---------------------------------------------------------------- tile-centric tensor-core projectors
+// Element kinds of the tensor-core operands.
+enum { TILE_TF32 = 0, TILE_BF16 = 1, TILE_F16 = 2 };
+
+// Device view of the brick tables (built at creation, see build_tile_tables in api.cu).  An
+// "item" is a brick of BX x 8 x 8 points with at least one projector slot (atom image whose
+// sphere reaches into the brick); items are in brick order.
+struct TileDev {
+  int ek = 0, terms = 1;                    // element kind, 1 or 3 (hi*hi + hi*lo + lo*hi) products
+  int BX = 32, nbx = 0, nby = 0, nbz = 0;   // brick extent in x and bricks per axis
+  int nitems = 0, natoms = 0, nlm = 0, smax = 0, kch_max = 0;
+  double h[3] = {0, 0, 0};                  // grid spacing
+  size_t part_layer = 0;                    // floats of partial products per (k-point, component group)
+  const int* it_brick = nullptr;            // [nitems] linear brick index bx + nbx (by + nby bz)
+  const int* it_nslot = nullptr;            // [nitems] slots
+  const int* it_npad = nullptr;             // [nitems] gather N: nlm * nslot rounded up to 16
+  const int* it_kch = nullptr;              // [nitems] scatter K chunks of 128 bytes
+  const long long* it_goff = nullptr;       // [nitems] byte offset of the item's gather table
+  const long long* it_soff = nullptr;       // [nitems] byte offset of the item's scatter table
+  const long long* it_poff = nullptr;       // [nitems] float offset of the item's partial products
+  const int* slot_atom = nullptr;           // [nitems][smax] atom of each slot
+  const float4* slot_delta = nullptr;       // [nitems][smax] brick origin minus the atom image (bohr)
+  const unsigned char* g_tab = nullptr;     // gather operand B: per item, chunk, part: npad rows x 128 B
+  const unsigned char* s_tab = nullptr;     // scatter operand A: per item, tile, K chunk, part: 128 x 128 B
+  const int* a_ptr = nullptr;               // [natoms + 1] (item, slot) pairs of each atom, in item order
+  const int* a_item = nullptr;
+  const int* a_slot = nullptr;
+};
+size_t tile_gather_smem(int terms);
+size_t tile_scatter_smem(int ek, int terms, int kch_max);
+// c[kb][a][2p + sigma] and dc = D c of every spinor (gather on the tensor cores, fixed-order
+// reduction over the bricks); part: nk * groups * part_layer floats, groups = ceil(2 nstates / 64).
+cudaError_t launch_tile_gather(cudaStream_t st, int N, const void* psi, int nk, int nstates, const TileDev& td,
+                               double dV, const EpiParams& ep, const float* Dmat, float* part, void* c_out,
+                               void* dc_out, int* err);
+// out = V_NL psi from dc at the points of every brick with projectors (scatter on the tensor
+// cores); out has the spinor layout and is left untouched elsewhere.
+cudaError_t launch_tile_scatter(cudaStream_t st, int N, void* out, int nk, int nstates, const TileDev& td,
+                                const EpiParams& ep, const void* dc, int* err);
 
 // Voronoi (nearest-atom) cells and per-atom sums of m and n.
 cudaError_t launch_voronoi_owner(cudaStream_t st, int N, const double* L, int natoms, const double* pos, int* owner);

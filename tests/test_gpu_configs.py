@@ -109,10 +109,11 @@ def large_case():
     return wl, psi, sample, ref, vnl
 
 
-@pytest.mark.parametrize("proj_mode,tol", [(1, 2e-5), (3, 2e-5), (2, 3e-3)])
+@pytest.mark.parametrize("proj_mode,tol", [(1, 2e-5), (3, 2e-5), (5, 2e-5), (4, 1e-4), (2, 3e-3)])
 def test_large_grid_and_atoms_sampled_h(lib, large_case, proj_mode, tol):
-    """96^3 with all 128 atoms of the large supercell: CUDA-core FP32, TF32x3 and TF32 projector
-    contractions; the tensor-core error budget is relative to the non-local part."""
+    """96^3 with all 128 atoms of the large supercell: CUDA-core FP32 and the tensor-core TF32x3,
+    FP16x3, BF16x3 and TF32 projector contractions (bricks of 32 x 8 x 8 points with up to 24
+    projector spheres each); the tensor-core error budget is relative to the non-local part."""
     wl, psi, sample, ref, vnl = large_case
     hpsi, _ = gpu_apply(wl, psi, 1, (-50.0, 450.0), proj_mode=proj_mode)
     err = np.abs(hpsi[:, sample] - ref).max()

@@ -220,13 +220,19 @@ def test_largest_grid_96(lib, precision, tol):
     assert rel(psi_g, o.psi) <= tol
 
 
-@pytest.mark.parametrize("proj_mode,tol", [(3, 2e-5), (2, 3e-3)])
+TC_MODES = [(3, 2e-5), (5, 2e-5), (4, 1e-4), (2, 3e-3)]  # TF32x3, FP16x3, BF16x3, TF32
+
+
+@pytest.mark.parametrize("proj_mode,tol", TC_MODES)
 @pytest.mark.parametrize("nstates", [5, 40])
-def test_tensor_core_projectors_apply_h(lib, proj_mode, tol, nstates):
-    """tcgen05 projector contraction (TF32 x3 and TF32) in the FP32-mixed Hamiltonian against the
-    oracle; 5 states give one ragged 64-component tile, 40 states two tiles per k-point."""
+@pytest.mark.parametrize("n", [16, 32])
+def test_tensor_core_projectors_apply_h(lib, proj_mode, tol, nstates, n):
+    """Brick-by-brick tcgen05 projector contraction (gather and scatter) in the FP32-mixed
+    Hamiltonian against the oracle: bricks of 16 (n = 16) and 32 (n = 32) x 8 x 8 points; 5 states
+    give one ragged group of components, 40 states two groups per k-point; two k-points, laser and
+    static B; the error budget of the split products is relative to the non-local part."""
     from paper_2506_21908_gb300 import _lib
-    wl = S.small_parity(n=16, nstates=nstates, nk=2, natoms=3)
+    wl = S.small_parity(n=n, nstates=nstates, nk=2, natoms=3)
     psi0 = S.small_parity_states(wl)
     h = _lib.TDDFT.from_workload(wl, precision=1, proj_mode=proj_mode, e_min=-20, e_max=100)
     h.set_fields(wl.times, wl.A, wl.B)
@@ -509,3 +515,15 @@ def test_lower_angular_momentum_projectors(lib, lmax, nstates, precision):
     tol = 1e-10 if precision == 0 else 2e-5
     for r in rows:
         assert r["n"] <= tol and r["m"] <= tol, r
+
+
+@pytest.mark.parametrize("proj_mode,tol", [(5, 2e-5), (3, 2e-5), (4, 1e-4)])
+def test_tensor_core_projectors_step_matches_oracle(lib, proj_mode, tol):
+    """Two ETRS steps with the tensor-core projector contraction (32^3, four SOC atoms, two
+    k-points, laser and static B) against the FP64 oracle: n, m and psi."""
+    wl = S.small_parity(n=32, nstates=6, nk=2, natoms=4)
+    psi0 = S.small_parity_states(wl)
+    rows, psi_g, o = run_pair(lib, wl, psi0, 2, (-20.0, 400.0), precision=1, proj_mode=proj_mode)
+    for r in rows:
+        assert r["n"] <= tol and r["m"] <= tol, (r["n"], r["m"])
+    assert rel(psi_g, o.psi) <= tol
