@@ -322,6 +322,7 @@ def run_ours(args):
 
     stream = torch.cuda.current_stream().cuda_stream
     ctx = Ctx(torch, dist, stream)
+    peaks = _lib.measure_peaks() if not args.no_peaks else None
 
     def max_over_ranks(x):
         return aggregate(0.0, x)[1]
@@ -410,7 +411,7 @@ def run_ours(args):
                    "projector_contraction": PROJ_NAMES[args.proj],
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "M_final": E_mixed["M"].tolist(), "max_norm_error": float(np.abs(norms - 1.0).max()),
+        "clocks": clocks, "measured_peaks_tflops": peaks, "M_final": E_mixed["M"].tolist(), "max_norm_error": float(np.abs(norms - 1.0).max()),
         "cluster": cluster, "bcc": bcc, "adjoint": adjoint,
     }
     print(json.dumps(out))
@@ -582,6 +583,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
     ap.add_argument("--no-bcc", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FMA / tensor-core peak microbenchmarks")
     ap.add_argument("--proj", type=int, default=5, help="projector contraction: " + str(PROJ_NAMES))
     ap.add_argument("--no-propagators", action="store_true", help="skip the Taylor-4 / Crank-Nicolson comparison")
     ap.add_argument("--adj-steps", type=int, default=500)

@@ -249,6 +249,25 @@ tddft_status tddft_atom_moments(tddft_handle h, double* M, double* N);
  * (FP32 in FP32-mixed mode) and the FP64 density and XC field; synchronises the stream. */
 tddft_status tddft_torques(tddft_handle h, double* soc, double* xc, double* zeeman);
 
+/* Testing hook of the failure-detection path (the paper has no counterpart).  Every bounded wait
+ * of the bulk-copy FFT pass and the first wait of the tensor-core projector gather try first with
+ * `first_polls` polls of their mbarrier (0 restores the default, 2^26); when that first try gives
+ * up, the kernel sets its error bit and waits again with the default limit, so the copies and
+ * matrix products in flight still complete and no index leaves its buffer.  The next
+ * tddft_observables of a handle whose kernels set the bit returns TDDFT_ERR_CUDA (the results of
+ * that handle are then invalid: the tensor-core kernels launched after the bit was set skip their
+ * work).  Applies to every handle on the current device until called again. */
+tddft_status tddft_set_wait_test_limit(unsigned first_polls);
+
+/* Measured peak rates of the current GPU, the denominators of the roofline fractions that the
+ * copy bandwidth and the library GEMM do not give (the paper has no counterpart): out[0] FP64 and
+ * out[1] FP32 fused multiply-adds on the CUDA cores, out[2] TF32, out[3] FP16 and out[4] BF16 dense
+ * tcgen05 products with FP32 accumulation, in TFLOP/s (2 FLOPs per multiply-add), from kernels that
+ * touch no global memory, timed with CUDA events (about 0.3 s in all).  Writes min(nout, 5)
+ * values; synchronises the device; allocates and frees a few bytes of device memory.  Errors:
+ * TDDFT_ERR_ARG (null out or nout < 1), TDDFT_ERR_CUDA. */
+tddft_status tddft_measure_peaks(double* out, int nout);
+
 /* Use this CUDA stream (a cudaStream_t; NULL = legacy default stream) for all work. */
 tddft_status tddft_set_stream(tddft_handle h, void* stream);
 
@@ -284,8 +303,9 @@ tddft_status tddft_profile_read(tddft_handle h, int ncls, double* ms, long long*
  * is one file-scope static device array of 64^3 + 64 complex FP64 values (4 MiB + 1 KiB),
  * present on every GPU that loads the library until the process exits.  Hence n must be one
  * of 8, 12, 16, 24, 32, 48, 64; larger grids return TDDFT_ERR_ARG.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call on a device shares the array, so calls that overlap on the
+ * looks up that array's device address (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not call the entry point
+ * again in a process that has reset the device (cudaDeviceReset), whose cached address is gone.  Every call on a device shares the array, so calls that overlap on the
  * GPU (different streams, or host threads) race with each other; each call overwrites the
  * part it uses before reading it, so nothing carries over from earlier calls.
  * Errors: TDDFT_ERR_ARG (null pointer, unsupported n, non-positive L), TDDFT_ERR_CUDA;

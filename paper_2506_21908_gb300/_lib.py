@@ -26,7 +26,8 @@ EXPORTS = ["tddft_create", "tddft_set_fields", "tddft_set_states", "tddft_get_st
            "tddft_observables", "tddft_get_potential", "tddft_apply_hamiltonian", "tddft_set_stream",
            "tddft_info", "tddft_profile", "tddft_profile_read", "tddft_last_error", "tddft_destroy",
            "tddft_hartree_noalloc", "tddft_backward", "tddft_atom_moments", "tddft_torques",
-           "tddft_set_states_c64", "tddft_get_states_c64"]
+           "tddft_set_states_c64", "tddft_get_states_c64", "tddft_set_wait_test_limit",
+           "tddft_measure_peaks"]
 
 
 class TddftError(RuntimeError):
@@ -93,6 +94,8 @@ def load(path=LIB_PATH):
         "tddft_backward": [vp, i, i, vp, vp, vp, vp],
         "tddft_atom_moments": [vp, vp, vp],
         "tddft_torques": [vp, vp, vp, vp],
+        "tddft_set_wait_test_limit": [ctypes.c_uint],
+        "tddft_measure_peaks": [vp, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -318,12 +321,46 @@ class TDDFT:
             pass
 
 
+def measure_peaks():
+    """Measured peak rates of the current GPU in TFLOP/s: FP64 and FP32 FMA on the CUDA cores,
+    TF32, FP16 and BF16 tensor-core products (tddft_measure_peaks)."""
+    lib = load()
+    out = np.zeros(5)
+    st = lib.tddft_measure_peaks(_ptr(out), 5)
+    if st != 0:
+        raise TddftError(st, "tddft_measure_peaks failed")
+    return dict(zip(["fp64_fma", "fp32_fma", "tf32_mma", "fp16_mma", "bf16_mma"], out.tolist()))
+
+
 def hartree_noalloc(n_dev, vH_dev, L, stream=None):
-    """Allocation-free Hartree solve on device tensors (float64, shape (n, n, n)), queued on
-    ``stream`` (a raw cudaStream_t value; None = legacy default stream)."""
+    """Allocation-free Hartree solve on device tensors: n_dev and vH_dev are contiguous float64
+    CUDA tensors of one shape (n, n, n) on one device; the work is queued on ``stream`` (a raw
+    cudaStream_t value; None = torch's current stream of that device).  Every argument is checked
+    here, before the library is called, so a wrong tensor raises instead of reaching a kernel."""
+    import torch
+    for name, t in (("n_dev", n_dev), ("vH_dev", vH_dev)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("%s must be a torch tensor" % name)
+        if t.dtype != torch.float64:
+            raise TypeError("%s must be float64, not %s" % (name, t.dtype))
+        if t.dim() != 3 or not (t.shape[0] == t.shape[1] == t.shape[2]):
+            raise ValueError("%s must have shape (n, n, n), not %s" % (name, tuple(t.shape)))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if tuple(n_dev.shape) != tuple(vH_dev.shape):
+        raise ValueError("n_dev and vH_dev differ in shape: %s, %s" % (tuple(n_dev.shape), tuple(vH_dev.shape)))
+    if not (n_dev.is_cuda and vH_dev.is_cuda):
+        raise ValueError("n_dev and vH_dev must be CUDA tensors")
+    if n_dev.device != vH_dev.device:
+        raise ValueError("n_dev and vH_dev are on different devices: %s, %s" % (n_dev.device, vH_dev.device))
+    L = _f64(L)
+    if L.shape != (3,):
+        raise ValueError("L must hold the three cell lengths")
     lib = load()
     n = int(n_dev.shape[-1])
-    L = _f64(L)
-    st = lib.tddft_hartree_noalloc(_ptr(n_dev), _ptr(vH_dev), n, _ptr(L), ctypes.c_void_p(stream or 0))
+    with torch.cuda.device(n_dev.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(n_dev.device).cuda_stream
+        st = lib.tddft_hartree_noalloc(_ptr(n_dev), _ptr(vH_dev), n, _ptr(L), ctypes.c_void_p(stream or 0))
     if st != 0:
         raise TddftError(st, lib.tddft_last_error(None).decode())

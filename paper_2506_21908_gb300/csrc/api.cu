@@ -2144,6 +2144,18 @@ tddft_status tddft_torques(tddft_handle h, double* soc, double* xc, double* zeem
   return TDDFT_OK;
 }
 
+tddft_status tddft_set_wait_test_limit(unsigned first_polls) {
+  using namespace tddft;
+  const unsigned v = first_polls ? first_polls : (1u << 26);  // the kernels' default limit
+  cudaError_t e = set_first_wait_fft(v);
+  if (e == cudaSuccess) e = set_first_wait_tile(v);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("tddft_set_wait_test_limit: ") + cudaGetErrorString(e));
+    return TDDFT_ERR_CUDA;
+  }
+  return TDDFT_OK;
+}
+
 tddft_status tddft_set_stream(tddft_handle h, void* stream) {
   if (!h) return TDDFT_ERR_ARG;
   h->st = (cudaStream_t)stream;

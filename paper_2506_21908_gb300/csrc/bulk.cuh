@@ -11,10 +11,15 @@ namespace tddft {
 
 constexpr unsigned BULK_WAIT_LIMIT = 1u << 26;
 
+// Polls allowed for the first try of a bounded wait (BULK_WAIT_LIMIT unless the testing hook of
+// the failure-detection path, tddft_set_wait_test_limit, shortened it; the retry after an expired
+// first try always has the full limit).  One copy per translation unit.
+static __device__ unsigned g_first_wait = BULK_WAIT_LIMIT;
+
 __device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ bool bulk_try_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned it = 0; it < BULK_WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool bulk_try_wait(uint32_t bar, uint32_t parity, unsigned limit = BULK_WAIT_LIMIT) {
+  for (unsigned it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -27,9 +32,31 @@ __device__ __forceinline__ bool bulk_try_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
+// Non-blocking polls (mbarrier.test_wait): the first try shortened by the testing hook counts
+// polls that return at once, where one try_wait may itself suspend until the phase completes.
+__device__ __forceinline__ bool bulk_test_wait(uint32_t bar, uint32_t parity, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// First try of a bounded wait: the full try_wait limit, or the testing hook's short test_wait.
+__device__ __forceinline__ bool bulk_first_try(uint32_t bar, uint32_t parity) {
+  const unsigned lim = g_first_wait;
+  return lim >= BULK_WAIT_LIMIT ? bulk_try_wait(bar, parity) : bulk_test_wait(bar, parity, lim);
+}
+
 // Wait for phase `parity` of the barrier; on expiry set bit `flag` of *err.
 __device__ __forceinline__ void bulk_wait(uint32_t bar, uint32_t parity, int* err, int flag) {
-  if (!bulk_try_wait(bar, parity)) {
+  if (!bulk_first_try(bar, parity)) {
     atomicOr(err, flag);
     bulk_try_wait(bar, parity);
   }

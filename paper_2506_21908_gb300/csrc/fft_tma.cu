@@ -280,4 +280,6 @@ cudaError_t launch_fft_xy_tma(cudaStream_t st, int N, const void* src, void* dst
 }
 
 
+cudaError_t set_first_wait_fft(unsigned polls) { return cudaMemcpyToSymbol(g_first_wait, &polls, sizeof(polls)); }
+
 }  // namespace tddft

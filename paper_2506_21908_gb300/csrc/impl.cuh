@@ -144,6 +144,10 @@ struct TileDev {
   const int* a_item = nullptr;
   const int* a_slot = nullptr;
 };
+// Testing hook of the failure-detection path: polls of the first try of the bounded waits of the
+// bulk-copy FFT pass and of the tensor-core gather (this device).
+cudaError_t set_first_wait_fft(unsigned polls);
+cudaError_t set_first_wait_tile(unsigned polls);
 size_t tile_gather_smem(int terms);
 size_t tile_scatter_smem(int ek, int terms, int kch_max);
 // c[kb][a][2p + sigma] and dc = D c of every spinor (gather on the tensor cores, fixed-order

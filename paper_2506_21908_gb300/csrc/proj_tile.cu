@@ -361,6 +361,9 @@ k_tile_gather(const float2* __restrict__ psi, int N, int comps_per_k, int groups
       const uint32_t id = idesc<EK>(npad);
       for (int c = 0; c < nch; ++c) {
         const int s = c & 1;
+        // the first wait may be shortened by the testing hook: on expiry the error bit is set and
+        // the wait is retried with the full limit
+        if (c == 0 && !bulk_first_try(sm_addr(&bar_full[s]), 0)) atomicOr(err, 1);
         if (!pt_wait(sm_addr(&bar_full[s]), (c >> 1) & 1)) abort_flag = 1;
         if (abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -737,5 +740,7 @@ cudaError_t launch_tile_scatter(cudaStream_t st, int N, void* out, int nk, int n
     default: return cudaErrorInvalidValue;
   }
 }
+
+cudaError_t set_first_wait_tile(unsigned polls) { return cudaMemcpyToSymbol(g_first_wait, &polls, sizeof(polls)); }
 
 }  // namespace tddft

@@ -3,12 +3,14 @@
 (48^3, 8 k-points x 128 spinors, static B plus laser) and the large supercell's grid and atoms
 (96^3, 128 atoms with SOC; 16 of its 1024 spinors, so that the host-side inputs stay small).
 
-The oracle cannot propagate these systems in seconds, so the checks take outputs it computes
-one spinor at a time: the potential from the density of all spinors, and H psi on sampled
-spinors (Eq. HNC-SDFT with the 2x2 potential and the L.S projectors).  A full step is checked
-through properties that hold at any size: norm and charge conservation, and agreement of the
-FP32-mixed step with the FP64 step (itself pinned element-wise to the oracle at small sizes)
-within the metric's |dM| <= 1e-5 mu_B per atom."""
+The oracle cannot propagate these systems with all their spinors in seconds, so the checks take
+outputs it computes one spinor at a time: the potential from the density of all spinors, H psi on
+sampled spinors (Eq. HNC-SDFT with the 2x2 potential and the L.S projectors), and one full ETRS
+step of the large and bcc supercells at full grid and with all atoms (and all 8 k-points) on a few
+spinors, compared element by element.  A full step with all spinors is checked through properties
+that hold at any size: norm and charge conservation, and agreement of the FP32-mixed step with the
+FP64 step (itself pinned element-wise to the oracle) within the metric's |dM| <= 1e-5 mu_B per
+atom."""
 import numpy as np
 import pytest
 
@@ -118,3 +120,66 @@ def test_large_grid_and_atoms_sampled_h(lib, large_case, proj_mode, tol):
     hpsi, _ = gpu_apply(wl, psi, 1, (-50.0, 450.0), proj_mode=proj_mode)
     err = np.abs(hpsi[:, sample] - ref).max()
     assert err <= tol * np.abs(vnl).max() + 2e-5 * np.abs(ref).max()
+
+
+def _oracle_one_step(wl, psi, cheb_tol=1e-16):
+    from oracle import Oracle
+    o = Oracle(System.from_workload(wl), FieldTable(wl.times, wl.A, wl.B), wl.dt, psi, n_sc=wl.n_sc,
+               cheb_tol=cheb_tol)
+    o.step()
+    n, m, E, _ = o.observables()
+    return o, n, m, E
+
+
+@pytest.fixture(scope="module")
+def large_step_case():
+    """The large supercell at full grid and with all 128 atoms, one of its 1024 spinors (the
+    first Loewdin-orthonormalised atomic-orbital spinor), one ETRS step of dt = 0.04 with the laser
+    table, by the oracle (FP64, window of reading P2)."""
+    wl = S.large(nsteps=4, nstates=1)
+    psi = S.large_states(wl, select=[0], dtype=np.complex128)
+    o, n, m, E = _oracle_one_step(wl, psi)
+    return wl, psi, o, n, m, E
+
+
+@pytest.fixture(scope="module")
+def bcc_step_case():
+    """The bcc supercell at full grid and atoms with all 8 k-points (Bloch phases), one spinor per
+    k-point, static B_x plus laser, one ETRS step by the oracle."""
+    wl = S.bcc(nsteps=4)
+    psi = np.ascontiguousarray(S.bcc_states(wl)[:, :1])
+    wl.occ = wl.occ[:, :1]
+    o, n, m, E = _oracle_one_step(wl, psi)
+    return wl, psi, o, n, m, E
+
+
+def _gpu_one_step(wl, psi, o, precision, proj_mode=None):
+    from paper_2506_21908_gb300 import _lib
+    h = _lib.TDDFT.from_workload(wl, precision=precision, proj_mode=proj_mode, e_min=o.emin, e_max=o.emax)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi, 0.0)
+    h.step(1)
+    n, m, E, _ = h.observables()
+    out = h.get_states()
+    h.close()
+    return n, m, E, out
+
+
+@pytest.mark.parametrize("precision,proj_mode,tol", [(0, None, 1e-10), (1, 5, 2e-5), (1, 1, 2e-5)])
+def test_large_full_size_step_matches_oracle(lib, large_step_case, precision, proj_mode, tol):
+    wl, psi, o, n_o, m_o, E_o = large_step_case
+    n, m, E, out = _gpu_one_step(wl, psi, o, precision, proj_mode)
+    assert rel(n, n_o) <= tol and rel(m, m_o) <= tol
+    assert rel(out, o.psi) <= tol
+    if precision == 0:
+        assert abs(E["total"] - E_o["total"]) <= 1e-8
+
+
+@pytest.mark.parametrize("precision,proj_mode,tol", [(0, None, 1e-10), (1, 5, 2e-5)])
+def test_bcc_full_size_step_matches_oracle(lib, bcc_step_case, precision, proj_mode, tol):
+    wl, psi, o, n_o, m_o, E_o = bcc_step_case
+    n, m, E, out = _gpu_one_step(wl, psi, o, precision, proj_mode)
+    assert rel(n, n_o) <= tol and rel(m, m_o) <= tol
+    assert rel(out, o.psi) <= tol
+    if precision == 0:
+        assert abs(E["total"] - E_o["total"]) <= 1e-8

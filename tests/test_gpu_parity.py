@@ -527,3 +527,53 @@ def test_tensor_core_projectors_step_matches_oracle(lib, proj_mode, tol):
     for r in rows:
         assert r["n"] <= tol and r["m"] <= tol, (r["n"], r["m"])
     assert rel(psi_g, o.psi) <= tol
+
+
+def xc_threshold_case(n=24):
+    """States whose magnetisation vanishes identically over most of the cell: an orbital phi in
+    spin up and the same phi in spin down with equal occupation (m = 0 wherever the third state is
+    negligible), a third narrow orbital with a tilted spin and half occupation, and vacuum
+    (n < 1e-14) near the cell corners.  No SOC and no field, so the first two states stay exact
+    spin partners: the locally collinear XC takes its |m| <= 1e-14 branch (b_xc = 0) in most of the
+    cell and its n < 1e-14 branch (no XC) in the corners (reading P8)."""
+    wl = S.small_parity(n=n, nstates=3, nk=1, natoms=1, lam=0.0, field=False, seed=11)
+    Lc = 12.0
+    wl.L = np.array([Lc, Lc, Lc])
+    wl.pos = np.array([[6.1, 5.9, 6.0]])
+    wl.r_cut = 4.0
+    wl.occ = np.array([[1.0, 1.0, 0.5]])
+    g = np.arange(n) * Lc / n
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+
+    def gauss(c, s):
+        return np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) / (2 * s * s))
+
+    dV = Lc ** 3 / n ** 3
+    phi = gauss((6.0, 6.0, 6.0), 1.2) * (1.0 + 0.3j * np.cos(2 * np.pi * X / Lc))
+    phi /= np.sqrt((np.abs(phi) ** 2).sum() * dV)
+    chi = (np.cos(0.5), np.sin(0.5) * np.exp(0.4j))
+    phi3 = gauss((5.0, 6.5, 6.3), 0.7).astype(np.complex128)
+    phi3 -= (np.vdot(phi, phi3) * dV) * phi
+    phi3 /= np.sqrt((np.abs(phi3) ** 2).sum() * dV)
+    psi = np.zeros((1, 3, 2, n, n, n), np.complex128)
+    psi[0, 0, 0] = phi
+    psi[0, 1, 1] = phi
+    psi[0, 2, 0] = chi[0] * phi3
+    psi[0, 2, 1] = chi[1] * phi3
+    return wl, psi
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-5)])
+def test_xc_threshold_branches_match_oracle(lib, precision, tol):
+    from oracle import xc as oxc
+    wl, psi0 = xc_threshold_case()
+    s = System.from_workload(wl)
+    n0, m0 = s.n_m(s.rho_v(psi0))
+    mag = np.sqrt((m0 ** 2).sum(axis=0))
+    # both branches are taken at many points, and the ordinary path elsewhere
+    assert ((mag <= oxc.M_THR) & (n0 >= oxc.N_THR)).mean() > 0.02
+    assert (n0 < oxc.N_THR).mean() > 0.05 and (mag > oxc.M_THR).mean() > 0.3
+    rows, psi_g, o = run_pair(lib, wl, psi0, 2, (-25.0, 120.0), precision=precision)
+    for r in rows:
+        assert r["n"] <= tol and r["m"] <= tol, (r["n"], r["m"])
+    assert rel(psi_g, o.psi) <= tol

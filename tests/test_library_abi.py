@@ -123,3 +123,25 @@ def test_binding_routes_complex64_to_the_c64_calls():
     assert not c64 and arr.dtype == np.complex128
     with pytest.raises(AssertionError):
         h._spinor_arg(np.zeros(5, np.complex64))
+
+
+@pytest.mark.parametrize("case", ["float32", "shape", "noncubic", "noncontig", "mismatch", "cpu"])
+def test_hartree_noalloc_binding_rejects_bad_tensors_before_any_call(case):
+    """The allocation-free Hartree binding checks dtype, shape, contiguity, equal shapes and the
+    device of both tensors before it calls the library (no launch can see a wrong buffer)."""
+    import torch
+    from paper_2506_21908_gb300 import _lib
+    good = torch.zeros((8, 8, 8), dtype=torch.float64)
+    n, v = good, good.clone()
+    if case == "float32":
+        n = good.float()
+    elif case == "shape":
+        n = torch.zeros((8, 8), dtype=torch.float64)
+    elif case == "noncubic":
+        n, v = torch.zeros((8, 8, 16), dtype=torch.float64), torch.zeros((8, 8, 16), dtype=torch.float64)
+    elif case == "noncontig":
+        n = torch.zeros((8, 8, 16), dtype=torch.float64)[:, :, ::2]
+    elif case == "mismatch":
+        v = torch.zeros((16, 16, 16), dtype=torch.float64)
+    with pytest.raises((TypeError, ValueError)):
+        _lib.hartree_noalloc(n, v, [10.0, 10.0, 10.0])
