@@ -206,7 +206,7 @@ def cpu_baseline(name):
 # CUDA sources that define each kernel class (its kernels, the device helpers they inline and
 # the parameter structs they take).
 KERNEL_SOURCES = {
-    "epilogue": ("epilogue.cu", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
+    "epilogue": ("epilogue.cu", "proj_tile.cu", "bulk.cuh", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
     "fft_xy": ("kernels.cu", "fft_tma.cu", "bulk.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
     "fft_z_kinetic": ("kernels.cu", "fft.cuh", "impl.cuh", "kcommon.cuh"),
     "proj_gather": ("kernels.cu", "proj_tile.cu", "bulk.cuh", "kepi.cuh", "fft.cuh", "impl.cuh", "kcommon.cuh"),
@@ -545,6 +545,54 @@ def adjoint_block(args, ctx, _lib, max_over_ranks):
             "what": "forward + discrete-adjoint backward of the whole horizon, one 64-parameter gradient (measured)"}
 
 
+# --------------------------------------------------------------------------- accuracy over a horizon
+def run_horizon(args):
+    """Mixed (FP32, the bench's projector mode) against the FP64 path on the same start over a long
+    horizon: |dM| per atom (mu_B), max |dn| and |dm| relative to the FP64 fields, the total
+    energies and the FP64 path's own energy drift, every `--horizon-every` steps.  One JSON line
+    per configuration (not a throughput line)."""
+    import torch
+    from paper_2506_21908_gb300 import _lib
+    stream = torch.cuda.current_stream().cuda_stream
+    plan = [("cluster", args.horizon), ("bcc", args.horizon_bcc), ("large", args.horizon_large)]
+    for name, nst in plan:
+        if nst <= 0:
+            continue
+        wl, psi0 = make_workload(name, nst + 8)
+        every = max(1, min(args.horizon_every, nst))
+        hs = []
+        for prec, proj in ((_lib.FP32_MIXED, args.proj), (_lib.FP64, None)):
+            h = _lib.TDDFT.from_workload(wl, precision=prec, proj_mode=proj, stream=stream)
+            h.set_fields(wl.times, wl.A, wl.B)
+            h.set_states(psi0, 0.0)
+            hs.append(h)
+        info32, info64 = hs[0].info(), hs[1].info()
+        rows = []
+        t_wall = time.time()
+        E0 = None
+        for done in range(0, nst + 1, every):
+            if done:
+                for h in hs:
+                    h.step(every)
+            torch.cuda.synchronize()
+            obs = [h.observables(fields=True, check=False) for h in hs]
+            (n32, m32, E32, _), (n64, m64, E64, _) = obs
+            if E0 is None:
+                E0 = E64["total"]
+            rows.append({"step": done, "t": E64["t"],
+                         "dM_per_atom_muB": float(np.linalg.norm(E32["M"] - E64["M"]) / len(wl.pos)),
+                         "max_dn_rel": float(np.abs(n32 - n64).max() / np.abs(n64).max()),
+                         "max_dm_rel": float(np.abs(m32 - m64).max() / np.abs(m64).max()),
+                         "E_fp32": E32["total"], "E_fp64": E64["total"], "E_fp64_drift": E64["total"] - E0,
+                         "M_fp64": E64["M"].tolist()})
+        for h in hs:
+            h.close()
+        print(json.dumps({"horizon": name, "workload": WORKLOADS[name], "steps": nst, "every": every,
+                          "projector_contraction": PROJ_NAMES[args.proj], "K_fp32": [info32["K_full"], info32["K_half"]],
+                          "K_fp64": [info64["K_full"], info64["K_half"]], "wall_s": time.time() - t_wall,
+                          "max_dM_per_atom_muB": max(r["dM_per_atom_muB"] for r in rows), "rows": rows}), flush=True)
+
+
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args):
     """The FP64 CPU oracle on the host cores (one single-threaded process per core, one spinor
@@ -591,10 +639,17 @@ def main():
     ap.add_argument("--adj-fp64", action="store_true", help="also time the FP64 adjoint (slow)")
     ap.add_argument("--states", type=int, default=0,
                     help="propagate only the first N spinors (small profiling case; not the headline)")
+    ap.add_argument("--horizon", type=int, default=0,
+                    help="accuracy run instead of the benchmark: cluster steps of mixed against FP64")
+    ap.add_argument("--horizon-bcc", type=int, default=0)
+    ap.add_argument("--horizon-large", type=int, default=0)
+    ap.add_argument("--horizon-every", type=int, default=50)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.horizon or args.horizon_bcc or args.horizon_large:
+        run_horizon(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -288,9 +288,9 @@ tddft_status tddft_profile(tddft_handle h, int enable);
 tddft_status tddft_profile_read(tddft_handle h, int ncls, double* ms, long long* count, double* bytes);
 
 /* Allocation-free Hartree (Poisson) solve; the paper has no counterpart to this entry
- * point.  For callers that cannot allocate device memory -- code running during CUDA
- * stream capture, frameworks that reserve all device memory up front, or loops that
- * cannot afford an allocation's implicit synchronisation.
+ * point.  For callers that cannot allocate device memory -- frameworks that reserve all
+ * device memory up front and forbid further allocations, or loops that cannot afford an
+ * allocation's implicit synchronisation.
  *
  * Computes v_H(r) = sum_{G != 0} 4 pi n(G) / |G|^2 exp(i G.r) / N^3 (G = 0 term dropped), the
  * same Hartree potential the library adds to V_v, for a real density n[N^3] on an n x n x n

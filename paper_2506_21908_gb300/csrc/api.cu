@@ -183,6 +183,7 @@ struct tddft_ctx {
   std::vector<cd> cf_full, cf_half;
   bool use_tma = false;      // FP32 xy passes fed by bulk asynchronous copies
   bool epi_pairs = false;    // epilogue threads take one point of two spinors
+  bool epi_fuse = false;     // tensor-core projectors: scatter and Chebyshev epilogue in one kernel
   // device memory
   cudaStream_t st = nullptr;
   // second stream for the projector gather, which runs beside the FFT passes of the same term
@@ -610,9 +611,10 @@ tddft_status build_tile_tables(tddft_ctx* c, const HostTables& ht, int ek, int t
       ents.push_back({b, sl, local, (size_t)e});
     }
   }
+  // every brick is an item (the fused epilogue visits every point); bricks no sphere reaches have
+  // no slots, and the gather and the plain scatter skip them
   std::vector<int> item_of(nbr, -1);
   for (int b = 0; b < nbr; ++b) {
-    if (keys[b].empty()) continue;
     if ((int)keys[b].size() > th.smax)
       return c->fail(TDDFT_ERR_UNSUPPORTED, "too many projector spheres reach one brick for the tensor-core path");
     item_of[b] = (int)th.it_brick.size();
@@ -632,7 +634,7 @@ tddft_status build_tile_tables(tddft_ctx* c, const HostTables& ht, int ek, int t
     const int b = th.it_brick[i];
     const int ns = (int)keys[b].size();
     th.it_nslot[i] = ns;
-    th.it_npad[i] = std::max(16, (ns * nlm + 15) / 16 * 16);
+    th.it_npad[i] = ns ? std::max(16, (ns * nlm + 15) / 16 * 16) : 0;
     th.it_kch[i] = (ns * nlm + epr - 1) / epr;
     th.kch_max = std::max(th.kch_max, th.it_kch[i]);
     th.it_goff[i] = goff;
@@ -832,12 +834,13 @@ template <typename R> tddft_status gather(tddft_ctx* c, const void* in, const do
 // beside the FFT passes (fork after the previous epilogue, join before the next one).
 // With the tensor-core projectors the scatter then forms V_NL psi in vnl.
 template <typename R> tddft_status nl_scatter(tddft_ctx* c, const double A[3]);
-template <typename R> tddft_status kinetic_and_gather(tddft_ctx* c, const void* cur, const double A[3]) {
+template <typename R>
+tddft_status kinetic_and_gather(tddft_ctx* c, const void* cur, const double A[3], bool scatter = true) {
   tddft_status s;
   if (!c->side || c->natoms == 0) {
     if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
     if ((s = gather<R>(c, cur, A))) return s;
-    return nl_scatter<R>(c, A);
+    return scatter ? nl_scatter<R>(c, A) : TDDFT_OK;
   }
   if ((s = c->cuda(cudaEventRecord(c->ev_fork, c->st), "fork")) ||
       (s = c->cuda(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork wait")))
@@ -846,7 +849,7 @@ template <typename R> tddft_status kinetic_and_gather(tddft_ctx* c, const void* 
   if ((s = c->cuda(cudaEventRecord(c->ev_join, c->side), "join"))) return s;
   if ((s = kinetic<R>(c, cur, c->tmp, A))) return s;
   if ((s = c->cuda(cudaStreamWaitEvent(c->st, c->ev_join, 0), "join wait"))) return s;
-  return nl_scatter<R>(c, A);
+  return scatter ? nl_scatter<R>(c, A) : TDDFT_OK;
 }
 
 // Tensor-core projectors: vnl = V_NL in, from the D c of the gather (main stream, after the
@@ -909,8 +912,10 @@ tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double
   const void* cur = in;
   tddft_status s;
   int done1 = 0, done2 = 0;
+  // tensor-core projectors: the scatter and the epilogue run as one kernel
+  const bool fuse = c->tile && c->epi_fuse && std::is_same<R, float>::value;
   for (int k = 0; k < K; ++k) {
-    if ((s = kinetic_and_gather<R>(c, cur, A))) return s;
+    if ((s = kinetic_and_gather<R>(c, cur, A, !fuse))) return s;
     void* out;
     if (slots) out = slots[k + 1];
     else if (k == 0) out = c->Ta;
@@ -924,10 +929,24 @@ tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double
     const double streams = 3.0 + (k == 0 ? 0.0 : 1.0) + (ep.use_acc1 ? (ep.init1 ? 1.0 : 2.0) : 0.0) +
                            (ep.use_acc2 ? (ep.init2 ? 1.0 : 2.0) : 0.0);
     const double by = streams * c->psi_elems() * 2 * sizeof(R) + 4.0 * c->N3 * sizeof(R);
-    if ((s = c->launch(KC_EPI, "chebyshev epilogue", [&] {
-           return epilogue<R>(c, c->tmp, cur, tkm1, out, acc1, acc2, Vr, pt, c->dcbuf, c->nkb, ep);
-         }, by)))
+    if (fuse) {
+      EpiIO io;
+      io.kin = (const float2*)c->tmp;
+      io.Tk = (const float2*)cur;
+      io.Tkm1 = (const float2*)tkm1;
+      io.Tout = (float2*)out;
+      io.acc1 = (float2*)acc1;
+      io.acc2 = (float2*)acc2;
+      io.V = (const float*)Vr;
+      if ((s = c->launch(KC_EPI, "chebyshev epilogue with the tensor-core scatter", [&] {
+             return launch_tile_epilogue(c->st, c->N, c->nk, c->nb, c->td, ep, c->dcbuf, c->tc_err, io);
+           }, by)))
+        return s;
+    } else if ((s = c->launch(KC_EPI, "chebyshev epilogue", [&] {
+                  return epilogue<R>(c, c->tmp, cur, tkm1, out, acc1, acc2, Vr, pt, c->dcbuf, c->nkb, ep);
+                }, by))) {
       return s;
+    }
     prev = cur;
     cur = out;
   }
@@ -1773,6 +1792,11 @@ tddft_status create_impl(tddft_ctx* c, const tddft_cell* cell, const tddft_grid*
     // TDDFT_NO_EPI_PAIRS=1 keeps two points of one spinor per thread (same results).
     const char* h = std::getenv("TDDFT_NO_EPI_PAIRS");
     c->epi_pairs = !(h && h[0] == '1');
+    // With the tensor-core projectors the Chebyshev epilogue runs inside the scatter kernel, so
+    // V_NL psi never crosses HBM; TDDFT_NO_EPI_FUSE=1 keeps the scatter and the pointwise
+    // epilogue apart (same arithmetic).
+    const char* f = std::getenv("TDDFT_NO_EPI_FUSE");
+    c->epi_fuse = !(f && f[0] == '1');
   }
   if (atoms->natoms < 0 || (atoms->natoms > 0 && (!atoms->pos || !atoms->species))) return c->fail(TDDFT_ERR_ARG, "bad atoms");
   c->natoms = atoms->natoms;

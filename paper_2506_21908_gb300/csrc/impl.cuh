@@ -155,6 +155,21 @@ size_t tile_scatter_smem(int ek, int terms, int kch_max);
 cudaError_t launch_tile_gather(cudaStream_t st, int N, const void* psi, int nk, int nstates, const TileDev& td,
                                double dV, const EpiParams& ep, const float* Dmat, float* part, void* c_out,
                                void* dc_out, int* err);
+// Arrays of one Chebyshev term for the fused tensor-core epilogue (spinor layout; V the FP32
+// potential 4-vector).
+struct EpiIO {
+  const float2* kin = nullptr;
+  const float2* Tk = nullptr;
+  const float2* Tkm1 = nullptr;
+  float2* Tout = nullptr;
+  float2* acc1 = nullptr;
+  float2* acc2 = nullptr;
+  const float* V = nullptr;
+};
+// The whole Chebyshev epilogue (modes EPI_FIRST, EPI_RECUR) of every point with V_NL from the
+// tensor cores: one CTA per (component group, brick), every brick of the grid an item.
+cudaError_t launch_tile_epilogue(cudaStream_t st, int N, int nk, int nstates, const TileDev& td, const EpiParams& ep,
+                                 const void* dc, int* err, const EpiIO& io);
 // out = V_NL psi from dc at the points of every brick with projectors (scatter on the tensor
 // cores); out has the spinor layout and is left untouched elsewhere.
 cudaError_t launch_tile_scatter(cudaStream_t st, int N, void* out, int nk, int nstates, const TileDev& td,

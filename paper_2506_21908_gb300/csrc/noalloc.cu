@@ -1,9 +1,8 @@
 // Allocation-free Hartree (Poisson) solve: tddft_hartree_noalloc.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is being
-// captured, frameworks that reserve all device memory up front and forbid further
-// allocations, and latency-critical loops where an allocation's implicit device
-// synchronisation is not acceptable.  This entry point solves the same Poisson problem as
+// Some callers cannot call cudaMalloc: frameworks that reserve all device memory up front
+// and forbid further allocations, and latency-critical loops where an allocation's implicit
+// device synchronisation is not acceptable.  This entry point solves the same Poisson problem as
 // the library's own potential pipeline, but its scratch (one complex FP64 field and the
 // FFT twiddles) lives in a file-scope static device array instead of memory owned by a
 // handle.  The array exists on every GPU that loads the library, for the life of the

@@ -142,25 +142,32 @@ template <int EK> __device__ __forceinline__ void put(unsigned char* part, int r
   if constexpr (Elt<EK>::bytes == 4) *reinterpret_cast<uint32_t*>(part + off) = v;
   else *reinterpret_cast<uint16_t*>(part + off) = (uint16_t)v;
 }
-// Two neighbouring 16-bit elements k, k + 1 (k even) in one 4-byte store.
-__device__ __forceinline__ void put2(unsigned char* part, int row, int k, uint32_t v0, uint32_t v1) {
-  const uint32_t off = sw128((uint32_t)row * PT_ROWB + (uint32_t)(k * 2));
-  *reinterpret_cast<uint32_t*>(part + off) = (v0 & 0xFFFFu) | (v1 << 16);
-}
 
-template <int N>
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 16 consecutive columns of the thread's lane, without the wait for completion.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// After tmem_wait_ld: ties the loaded registers to a point after the wait, so that no use of them
+// is scheduled before it.
+__device__ __forceinline__ void tmem_regs_ready(uint32_t* r) {
+  asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+               "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Per-axis phase tables exp(+i q_a l h_a) of one brick (l = 0 .. extent-1).
 __device__ __forceinline__ void phase_tables(float2* px, float2* py, float2* pz, int BX, const TileDev& td,
@@ -211,6 +218,15 @@ constexpr int PT_MMA_WARP = PT_WARPS, PT_COPY_WARP = PT_WARPS + 1;
 
 // ============================================================================ gather
 
+// Chunks per accumulation group of the gather.  The tensor cores add each product into the FP32
+// accumulator with a rounding that is biased toward zero, so one accumulator that takes every
+// chunk of a brick (hundreds of MMAs) loses a relative 1e-5 of every partial sum, the same sign
+// everywhere.  The accumulation therefore restarts from zero every CPG chunks: group 0 accumulates
+// in the running sum R (tensor-memory columns 256..511), every later group in P (columns 0..255),
+// and the worker warps add P into R on the CUDA cores (round to nearest) between groups; the bias
+// falls with the length of a group.
+template <int TERMS> struct GatherGroups { static constexpr int CPG = (TERMS == 3) ? 4 : 8; };
+
 // CTA (kg, item): 64 components (group g of k-point k) against the slots of one brick.
 template <int EK, int TERMS>
 __global__ void __launch_bounds__(PT_NT, 1)
@@ -223,7 +239,8 @@ k_tile_gather(const float2* __restrict__ psi, int N, int comps_per_k, int groups
   constexpr int CPW = 64 / PT_WARPS;            // components per worker warp
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t bar_full[2], bar_empty[2], bar_acc;
+  constexpr int CPG = GatherGroups<TERMS>::CPG;
+  __shared__ uint64_t bar_full[2], bar_empty[2], bar_acc, bar_grp, bar_drain;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   __shared__ float2 px[32], py[8], pz[8];
@@ -233,11 +250,13 @@ k_tile_gather(const float2* __restrict__ psi, int N, int comps_per_k, int groups
   const int kg = blockIdx.x, it = blockIdx.y;
   const int k = kg / groups, comp0 = (kg % groups) * 64;
   const int nslot = td.it_nslot[it], npad = td.it_npad[it];
+  if (nslot == 0) return;  // a brick no projector sphere reaches
   const int BX = td.BX;
   const int brick = td.it_brick[it];
   const int bx = brick % td.nbx, by = (brick / td.nbx) % td.nby, bz = brick / (td.nbx * td.nby);
   const int x0 = bx * BX, y0 = by * 8, z0 = bz * 8;
   const int nch = BX * 64 / EPR;
+  const int ngrp = nch / CPG;  // nch is a multiple of 16 and of CPG, so ngrp >= 2
   const size_t N3 = (size_t)N * N * N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto stageA = [&](int s, int q) { return smem + (size_t)s * STAGE + (size_t)q * PT_PART; };
@@ -250,23 +269,27 @@ k_tile_gather(const float2* __restrict__ psi, int N, int comps_per_k, int groups
       bar_init(sm_addr(&bar_empty[s]), 1);
     }
     bar_init(sm_addr(&bar_acc), 1);
+    bar_init(sm_addr(&bar_grp), 1);
+    bar_init(sm_addr(&bar_drain), 32 * PT_WARPS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   phase_tables(px, py, pz, BX, td, ep.shift[k]);
   if (warp == PT_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(&tmem_base)),
-                 "r"(256));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
+  const uint32_t accP = tmem, accR = tmem + 256u;
+  // worker warp: lane quarter of the accumulator, and which alternate blocks of 16 columns it takes
+  const int quarter = warp & 3, half = (warp >> 2) & 1;
+  const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
 
   if (warp < PT_WARPS) {
     // ---- psi' = exp(i q.(r - r_b)) psi, split, into rows cl (re) and 64 + cl (im) of stage A.
-    // The CPW components of a warp are loaded for chunk c + 1 before chunk c is converted, so
-    // two chunks of loads are in flight per thread.
     constexpr int PPL = (EPR == 64) ? 2 : 1;  // points per lane
     using V = typename std::conditional<PPL == 2, float4, float2>::type;
     const int kk = lane * PPL;
@@ -291,13 +314,16 @@ k_tile_gather(const float2* __restrict__ psi, int N, int comps_per_k, int groups
         w[j] = v;
       }
     };
-    V wa[CPW], wb[CPW];
+    // loads run two chunks ahead of the conversion: chunk c + 2 is requested before chunk c is
+    // converted (wa: chunk c, wb: c + 1, wc: c + 2)
+    V wa[CPW], wb[CPW], wc[CPW];
     load(0, wa);
+    if (nch > 1) load(1, wb);
     for (int c = 0; c < nch; ++c) {
       const int s = c & 1;
-      if (c + 1 < nch) load(c + 1, wb);
+      if (c + 2 < nch) load(c + 2, wc);
       if (c >= 2 && !pt_wait(sm_addr(&bar_empty[s]), ((c >> 1) - 1) & 1)) abort_flag = 1;
-      if (abort_flag) break;
+      if (__any_sync(0xffffffffu, abort_flag != 0)) break;
       int lx, ly, lz;
       point(c, lx, ly, lz);
       const float2 ph0 = cm(cm(px[lx], py[ly]), pz[lz]);
@@ -335,7 +361,34 @@ k_tile_gather(const float2* __restrict__ psi, int N, int comps_per_k, int groups
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       pt_arrive(sm_addr(&bar_full[s]));
 #pragma unroll
-      for (int j = 0; j < CPW; ++j) wa[j] = wb[j];
+      for (int j = 0; j < CPW; ++j) {
+        wa[j] = wb[j];
+        wb[j] = wc[j];
+      }
+      // group g (1 <= g <= ngrp - 2) ended with chunk c - 2: add P into R before the next pass of
+      // this loop waits for the MMAs of the first chunk of group g + 1, which reuse P (the votes keep
+      // the warp together for the tensor-memory accesses)
+      const int gd = (c - 1) / CPG;
+      if ((c - 1) % CPG == 0 && gd >= 2 && gd <= ngrp - 1) {
+        if (!pt_wait(sm_addr(&bar_grp), (gd - 2) & 1)) abort_flag = 1;
+        if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int c0 = 16 * half; c0 < npad; c0 += 32) {
+          uint32_t pv[16], rv[16];
+          tmem_ld16_async(accP + lane_off + (uint32_t)c0, pv);
+          tmem_ld16_async(accR + lane_off + (uint32_t)c0, rv);
+          tmem_wait_ld();
+          tmem_regs_ready(pv);
+          tmem_regs_ready(rv);
+          float sum[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sum[j] = __uint_as_float(rv[j]) + __uint_as_float(pv[j]);
+          tmem_st16(accR + lane_off + (uint32_t)c0, sum);
+        }
+        tmem_wait_st();
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        pt_arrive(sm_addr(&bar_drain));
+      }
     }
   } else if (warp == PT_COPY_WARP) {
     if (lane == 0) {
@@ -360,55 +413,64 @@ k_tile_gather(const float2* __restrict__ psi, int N, int comps_per_k, int groups
     if (lane == 0) {
       const uint32_t id = idesc<EK>(npad);
       for (int c = 0; c < nch; ++c) {
-        const int s = c & 1;
+        const int s = c & 1, g = c / CPG, cg = c % CPG;
         // the first wait may be shortened by the testing hook: on expiry the error bit is set and
         // the wait is retried with the full limit
         if (c == 0 && !bulk_first_try(sm_addr(&bar_full[s]), 0)) atomicOr(err, 1);
-        if (!pt_wait(sm_addr(&bar_full[s]), (c >> 1) & 1)) abort_flag = 1;
+        // P holds group g - 1 until the worker warps have added it into R
+        if (cg == 0 && g >= 2 && !pt_wait(sm_addr(&bar_drain), (g - 2) & 1)) abort_flag = 1;
+        if (!abort_flag && !pt_wait(sm_addr(&bar_full[s]), (c >> 1) & 1)) abort_flag = 1;
         if (abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t dst = (g == 0) ? accR : accP;
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
           const uint32_t off = (uint32_t)ks * 32;
           const uint64_t ah = desc_sw128(sm_addr(stageA(s, 0)) + off), bh = desc_sw128(sm_addr(stageB(s, 0)) + off);
-          mma<EK>(tmem, ah, bh, id, (c | ks) ? 1u : 0u);
+          mma<EK>(dst, ah, bh, id, (cg | ks) ? 1u : 0u);
           if constexpr (TERMS == 3) {
             const uint64_t al = desc_sw128(sm_addr(stageA(s, 1)) + off), bl = desc_sw128(sm_addr(stageB(s, 1)) + off);
-            mma<EK>(tmem, ah, bl, id, 1u);
-            mma<EK>(tmem, al, bh, id, 1u);
+            mma<EK>(dst, ah, bl, id, 1u);
+            mma<EK>(dst, al, bh, id, 1u);
           }
         }
         mma_commit(sm_addr(&bar_empty[s]));
+        // groups 1 .. ngrp - 2 are added into R by the worker warps; the last one at the end
+        if (cg == CPG - 1 && g >= 1 && g <= ngrp - 2) mma_commit(sm_addr(&bar_grp));
       }
       // also after an abort: every MMA issued completes before the accumulator is read or freed
       mma_commit(sm_addr(&bar_acc));
+      if (!pt_wait(sm_addr(&bar_acc), 0)) atomicOr(err, 1);
     }
   }
-  // ---- accumulator (rows: component re / im; columns: slot x nlm) -> partial sums; the two
-  // warps of a lane quarter take alternate blocks of 16 columns
+  // ---- R + P (the last group) (rows: component re / im; columns: slot x nlm) -> partial sums;
+  // the two warps of a lane quarter take alternate blocks of 16 columns
   if (warp < PT_WARPS) {
-    const bool ok = pt_wait(sm_addr(&bar_acc), 0);
+    const bool ok = __all_sync(0xffffffffu, pt_wait(sm_addr(&bar_acc), 0));
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!ok || abort_flag) {
+    if (!ok || __any_sync(0xffffffffu, abort_flag != 0)) {
       if (lane == 0) atomicOr(err, 1);
     } else {
-      const int quarter = warp & 3, half = warp >> 2;
       const int row = quarter * 32 + lane;
       const int ncol = td.nlm * nslot;
       float* dst = part + (size_t)kg * td.part_layer + td.it_poff[it];
       for (int c0 = 16 * half; c0 < npad; c0 += 32) {
-        float v[16];
-        tmem_ld16<16>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+        uint32_t pv[16], rv[16];
+        tmem_ld16_async(accP + lane_off + (uint32_t)c0, pv);
+        tmem_ld16_async(accR + lane_off + (uint32_t)c0, rv);
+        tmem_wait_ld();
+        tmem_regs_ready(pv);
+        tmem_regs_ready(rv);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (c0 + j < ncol) dst[(size_t)(c0 + j) * 128 + row] = v[j];
+          if (c0 + j < ncol) dst[(size_t)(c0 + j) * 128 + row] = __uint_as_float(rv[j]) + __uint_as_float(pv[j]);
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == PT_MMA_WARP)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 // Sum the partial products of every (brick, slot) of atom a in a fixed order with the phase
@@ -469,12 +531,16 @@ k_tile_reduce(const float* __restrict__ part, TileDev td, int groups, int comps_
 // ============================================================================ scatter
 
 // CTA (kg, brick): SC components (X, the B operand, resident) against the brick's points in
-// tiles of 128 (the A operand, streamed); out = exp(-i q.(r - r_b)) (beta^T X) at every point of
-// the brick (points of bricks without projectors are never written and keep their zeros).
-template <int EK, int TERMS>
+// tiles of 128 (the A operand, streamed).  FUSED = 0: out = exp(-i q.(r - r_b)) (beta^T X) at every
+// point of a brick with projectors (the points of other bricks are never written and keep their
+// zeros).  FUSED = 1: the drain runs the Chebyshev epilogue of every point of the brick itself
+// (kinetic part from io.kin, V_NL from the tensor memory, the 2x2 local potential, T_{k+1} and the
+// accumulators) with the arithmetic of k_epilogue, so V_NL never crosses HBM; bricks without
+// projectors take the same path with V_NL = 0.
+template <int EK, int TERMS, int FUSED>
 __global__ void __launch_bounds__(PT_NT, 1)
 k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, int natoms, TileDev td, EpiParams ep,
-               const float2* __restrict__ dc, int* __restrict__ err) {
+               const float2* __restrict__ dc, int* __restrict__ err, EpiIO io) {
   constexpr int EPR = PT_ROWB / Elt<EK>::bytes;    // projector indices per K chunk
   constexpr int SC = (Elt<EK>::bytes == 4) ? 32 : 64;  // components per CTA
   constexpr int NPART = (TERMS == 3) ? 2 : 1;
@@ -492,6 +558,8 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
   const int kg = blockIdx.x, it = blockIdx.y;
   const int k = kg / sgroups, comp0 = (kg % sgroups) * SC;
   const int nslot = td.it_nslot[it], kch = td.it_kch[it];
+  if (!FUSED && nslot == 0) return;  // nothing to add at this brick
+  const bool has_nl = nslot > 0;
   const int BX = td.BX;
   const int brick = td.it_brick[it];
   const int bx = brick % td.nbx, by = (brick / td.nbx) % td.nby, bz = brick / (td.nbx * td.nby);
@@ -524,9 +592,13 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
     sincosf((float)(q[0] * dl.x + q[1] * dl.y + q[2] * dl.z), &sn, &c);
     sph[s] = make_float2(c, -sn);
   }
+  // tensor memory: two accumulators of 2 SC columns (tiles alternate); with three products the
+  // hi x lo and lo x hi products go to a second pair at column 256, so the rounding of the tensor
+  // cores' accumulation (biased toward zero) sees a third of the MMAs at full magnitude
+  constexpr uint32_t TMEM_COLS = (TERMS == 3) ? 512u : 256u;
   if (warp == PT_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(&tmem_base)),
-                 "r"(256));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -591,7 +663,7 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
 
   const int nchunk = ntile * kch;
   if (warp == PT_COPY_WARP) {
-    if (lane == 0) {
+    if (lane == 0 && has_nl) {
       const unsigned char* src = td.s_tab + td.it_soff[it];
       int issued = 0;
       for (int j = 0; j < nchunk; ++j) {
@@ -607,12 +679,12 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
         if (!pt_wait(sm_addr(&bar_full[j & 1]), (j >> 1) & 1)) atomicOr(err, 1);
     }
   } else if (warp == PT_MMA_WARP) {
-    if (lane == 0) {
+    if (lane == 0 && has_nl) {
       const uint32_t id = idesc<EK>(2 * SC);
       for (int t = 0; t < ntile && !abort_flag; ++t) {
         const int acc = t & 1;
         if (t >= 2 && !pt_wait(sm_addr(&bar_acce[acc]), ((t >> 1) - 1) & 1)) { abort_flag = 1; break; }
-        const uint32_t dtm = tmem + (uint32_t)(acc * 2 * SC);
+        const uint32_t dtm = tmem + (uint32_t)(acc * 2 * SC), dlo = dtm + 256u;
         for (int kc = 0; kc < kch; ++kc) {
           const int j = t * kch + kc, s = j & 1;
           if (!pt_wait(sm_addr(&bar_full[s]), (j >> 1) & 1)) { abort_flag = 1; break; }
@@ -624,8 +696,8 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
             mma<EK>(dtm, ah, bh, id, (kc | ks) ? 1u : 0u);
             if constexpr (TERMS == 3) {
               const uint64_t al = desc_sw128(sm_addr(apart(s, 1)) + off), bl = desc_sw128(sm_addr(xpart(kc, 1)) + off);
-              mma<EK>(dtm, ah, bl, id, 1u);
-              mma<EK>(dtm, al, bh, id, 1u);
+              mma<EK>(dlo, ah, bl, id, (kc | ks) ? 1u : 0u);
+              mma<EK>(dlo, al, bh, id, 1u);
             }
           }
           mma_commit(sm_addr(&bar_empty[s]));
@@ -639,32 +711,146 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
     }
   } else {
     // ---- drain: thread = point of the tile (lane quarter of the warp); the two warps of a
-    // quarter take one half of the components each; out = exp(-i q.(r - r_b)) (re + i im)
+    // quarter take one half of the components each; V_NL = exp(-i q.(r - r_b)) (re + i im)
     const int quarter = warp & 3, half = warp >> 2;
     const int row = quarter * 32 + lane;
+    const int cbeg = half * (SC / 2), cend = (half + 1) * (SC / 2);
+    // epilogue constants (Chebyshev term k: T_{k+1} = f (H - c) T_k / Delta - T_{k-1}, f = 1 or 2)
+    const float cc = (float)ep.c, idl = (float)ep.inv_delta;
+    const bool rec = ep.mode == EPI_RECUR;
+    const bool use1 = ep.use_acc1, use2 = ep.use_acc2;
+    const bool ld1 = use1 && !ep.init1, ld2 = use2 && !ep.init2;
     for (int t = 0; t < ntile; ++t) {
       const int acc = t & 1;
-      if (!pt_wait(sm_addr(&bar_accf[acc]), (t >> 1) & 1)) abort_flag = 1;
-      if (abort_flag) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (has_nl) {
+        if (!pt_wait(sm_addr(&bar_accf[acc]), (t >> 1) & 1)) abort_flag = 1;
+        if (abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+      }
       const int p = t * 128 + row;
       const int lx = p % BX, ly = (p / BX) & 7, lz = p / (BX * 8);
       const size_t idx = ((size_t)(z0 + lz) * N + (y0 + ly)) * N + (x0 + lx);
       const float2 ph = cm(cm(px[lx], py[ly]), pz[lz]);
       const float2 phc = make_float2(ph.x, -ph.y);
       const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * 2 * SC);
-      float2* o = out + ((size_t)k * comps_per_k + comp0) * N3 + idx;
-      for (int c0 = half * (SC / 2); c0 < (half + 1) * (SC / 2); c0 += 16) {
+      const size_t base = ((size_t)k * comps_per_k + comp0) * N3 + idx;  // component comp0 at this point
+      float V0 = 0.f, V1 = 0.f, hx = 0.f, hy = 0.f;
+      if constexpr (FUSED) {
+        V0 = io.V[idx];
+        V1 = io.V[N3 + idx];
+        hx = 0.5f * io.V[2 * N3 + idx];
+        hy = 0.5f * io.V[3 * N3 + idx];
+      }
+      for (int c0 = cbeg; c0 < cend; c0 += 16) {
         float re[16], im[16];
-        tmem_ld16<16>(tb + (uint32_t)c0, re);
-        tmem_ld16<16>(tb + (uint32_t)(SC + c0), im);
-        if (c0 + 16 >= (half + 1) * (SC / 2)) {
-          asm volatile("tcgen05.fence::before_thread_sync;");
-          pt_arrive(sm_addr(&bar_acce[acc]));
-        }
+        if (has_nl) {
+          uint32_t hr[16], hi_[16];
+          tmem_ld16_async(tb + (uint32_t)c0, hr);
+          tmem_ld16_async(tb + (uint32_t)(SC + c0), hi_);
+          if constexpr (TERMS == 3) {
+            uint32_t lr[16], li[16];
+            tmem_ld16_async(tb + 256u + (uint32_t)c0, lr);
+            tmem_ld16_async(tb + 256u + (uint32_t)(SC + c0), li);
+            tmem_wait_ld();
+            tmem_regs_ready(hr);
+            tmem_regs_ready(hi_);
+            tmem_regs_ready(lr);
+            tmem_regs_ready(li);
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (comp0 + c0 + j < comps_per_k) o[(size_t)(c0 + j) * N3] = cm(make_float2(re[j], im[j]), phc);
+            for (int j = 0; j < 16; ++j) {
+              re[j] = __uint_as_float(hr[j]) + __uint_as_float(lr[j]);
+              im[j] = __uint_as_float(hi_[j]) + __uint_as_float(li[j]);
+            }
+          } else {
+            tmem_wait_ld();
+            tmem_regs_ready(hr);
+            tmem_regs_ready(hi_);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              re[j] = __uint_as_float(hr[j]);
+              im[j] = __uint_as_float(hi_[j]);
+            }
+          }
+          if (c0 + 16 >= cend) {
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            pt_arrive(sm_addr(&bar_acce[acc]));
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) re[j] = im[j] = 0.f;
+        }
+        if constexpr (!FUSED) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (comp0 + c0 + j < comps_per_k) out[base + (size_t)(c0 + j) * N3] = cm(make_float2(re[j], im[j]), phc);
+        } else {
+          // four spinors at a time: every input is requested before any arithmetic
+#pragma unroll
+          for (int b = 0; b < 16; b += 8) {
+            float2 pu[4], pd[4], ku[4], kd[4], qu[4], qd[4], au[4], ad[4], bu[4], bd[4];
+            const float2 z2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int cu = c0 + b + 2 * j;
+              pu[j] = pd[j] = ku[j] = kd[j] = qu[j] = qd[j] = au[j] = ad[j] = bu[j] = bd[j] = z2;
+              if (comp0 + cu < comps_per_k) {
+                const size_t ou = base + (size_t)cu * N3, od = ou + N3;
+                pu[j] = io.Tk[ou]; pd[j] = io.Tk[od];
+                ku[j] = io.kin[ou]; kd[j] = io.kin[od];
+                if (rec) { qu[j] = io.Tkm1[ou]; qd[j] = io.Tkm1[od]; }
+                if (ld1) { au[j] = io.acc1[ou]; ad[j] = io.acc1[od]; }
+                if (ld2) { bu[j] = io.acc2[ou]; bd[j] = io.acc2[od]; }
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int cu = c0 + b + 2 * j;
+              if (comp0 + cu >= comps_per_k) continue;
+              const size_t ou = base + (size_t)cu * N3, od = ou + N3;
+              const float2 vu = cm(make_float2(re[b + 2 * j], im[b + 2 * j]), phc);
+              const float2 vd = cm(make_float2(re[b + 2 * j + 1], im[b + 2 * j + 1]), phc);
+              float2 hu = make_float2(ku[j].x + vu.x, ku[j].y + vu.y);
+              float2 hd = make_float2(kd[j].x + vd.x, kd[j].y + vd.y);
+              const float2 u = pu[j], d = pd[j];
+              hu = make_float2(hu.x + V0 * u.x + hx * d.x - hy * d.y, hu.y + V0 * u.y + hx * d.y + hy * d.x);
+              hd = make_float2(hd.x + V1 * d.x + hx * u.x + hy * u.y, hd.y + V1 * d.y + hx * u.y - hy * u.x);
+              float2 tu, td;
+              if (!rec) {
+                tu = make_float2((hu.x - cc * u.x) * idl, (hu.y - cc * u.y) * idl);
+                td = make_float2((hd.x - cc * d.x) * idl, (hd.y - cc * d.y) * idl);
+              } else {
+                tu = make_float2(2.f * (hu.x - cc * u.x) * idl - qu[j].x, 2.f * (hu.y - cc * u.y) * idl - qu[j].y);
+                td = make_float2(2.f * (hd.x - cc * d.x) * idl - qd[j].x, 2.f * (hd.y - cc * d.y) * idl - qd[j].y);
+              }
+              io.Tout[ou] = tu;
+              io.Tout[od] = td;
+              // accumulators: up to three terms (T_{k-1}, T_k, T_{k+1}) at once
+              auto upd = [&](float2* accp, int init, float2 ou_old, float2 od_old, const double* cmv, const double* c0v,
+                             const double* c1v) {
+                const float cmr = (float)cmv[0], cmi = (float)cmv[1], c0r = (float)c0v[0], c0i = (float)c0v[1];
+                const float c1r = (float)c1v[0], c1i = (float)c1v[1];
+                auto mulr = [](float2 a, float r_, float i_) { return make_float2(r_ * a.x - i_ * a.y, r_ * a.y + i_ * a.x); };
+                float2 nu = mulr(tu, c1r, c1i), nd = mulr(td, c1r, c1i);
+                const float2 pu0 = mulr(u, c0r, c0i), pd0 = mulr(d, c0r, c0i);
+                nu = make_float2(nu.x + pu0.x, nu.y + pu0.y);
+                nd = make_float2(nd.x + pd0.x, nd.y + pd0.y);
+                if (rec) {
+                  const float2 qu0 = mulr(qu[j], cmr, cmi), qd0 = mulr(qd[j], cmr, cmi);
+                  nu = make_float2(nu.x + qu0.x, nu.y + qu0.y);
+                  nd = make_float2(nd.x + qd0.x, nd.y + qd0.y);
+                }
+                if (!init) {
+                  nu = make_float2(nu.x + ou_old.x, nu.y + ou_old.y);
+                  nd = make_float2(nd.x + od_old.x, nd.y + od_old.y);
+                }
+                accp[ou] = nu;
+                accp[od] = nd;
+              };
+              if (use1) upd(io.acc1, ep.init1, au[j], ad[j], ep.am, ep.a0, ep.a1);
+              if (use2) upd(io.acc2, ep.init2, bu[j], bd[j], ep.bm, ep.b0, ep.b1);
+            }
+          }
+        }
       }
     }
     if (abort_flag && lane == 0) atomicOr(err, 1);
@@ -672,16 +858,23 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == PT_MMA_WARP)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 // ============================================================================ launchers
 
-size_t tile_gather_smem(int terms) { return (size_t)((terms == 3) ? 2 : 1) * (PT_PART + 256 * PT_ROWB) * 2 + 1024; }
+// At least 120 KB, so that one CTA (holding all 512 tensor-memory columns) runs per SM.
+size_t tile_gather_smem(int terms) {
+  const size_t need = (size_t)((terms == 3) ? 2 : 1) * (PT_PART + 256 * PT_ROWB) * 2 + 1024;
+  return need > 120 * 1024 ? need : 120 * 1024;
+}
+// With three products, at least 120 KB, so that one CTA (holding all 512 tensor-memory columns)
+// runs per SM.
 size_t tile_scatter_smem(int ek, int terms, int kch_max) {
   const int sc = (ek == TILE_TF32) ? 32 : 64;
   const size_t np = (terms == 3) ? 2 : 1;
-  return (size_t)kch_max * np * 2 * sc * PT_ROWB + 2 * np * PT_PART + 1024;
+  const size_t need = (size_t)kch_max * np * 2 * sc * PT_ROWB + 2 * np * PT_PART + 1024;
+  return (terms == 3 && need < 120 * 1024) ? 120 * 1024 : need;
 }
 
 template <int EK, int TERMS>
@@ -701,19 +894,31 @@ static cudaError_t gather_et(cudaStream_t st, int N, const void* psi, int nk, in
   return cudaGetLastError();
 }
 
-template <int EK, int TERMS>
+template <int EK, int TERMS, int FUSED>
 static cudaError_t scatter_et(cudaStream_t st, int N, void* out, int nk, int nstates, const TileDev& td,
-                              const EpiParams& ep, const void* dc, int* err) {
+                              const EpiParams& ep, const void* dc, int* err, const EpiIO& io) {
   constexpr int SC = (Elt<EK>::bytes == 4) ? 32 : 64;
   const int comps_per_k = 2 * nstates;
   const int sgroups = (comps_per_k + SC - 1) / SC;
   const size_t smem = tile_scatter_smem(EK, TERMS, td.kch_max);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  auto kf = k_tile_scatter<EK, TERMS>;
+  auto kf = k_tile_scatter<EK, TERMS, FUSED>;
   cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kf<<<dim3(nk * sgroups, td.nitems), PT_NT, smem, st>>>((float2*)out, N, comps_per_k, sgroups, nstates, td.natoms,
-                                                         td, ep, (const float2*)dc, err);
+                                                         td, ep, (const float2*)dc, err, io);
   return cudaGetLastError();
+}
+
+template <int FUSED>
+static cudaError_t scatter_dispatch(cudaStream_t st, int N, void* out, int nk, int nstates, const TileDev& td,
+                                    const EpiParams& ep, const void* dc, int* err, const EpiIO& io) {
+  switch (td.ek * 4 + td.terms) {
+    case TILE_TF32 * 4 + 1: return scatter_et<TILE_TF32, 1, FUSED>(st, N, out, nk, nstates, td, ep, dc, err, io);
+    case TILE_TF32 * 4 + 3: return scatter_et<TILE_TF32, 3, FUSED>(st, N, out, nk, nstates, td, ep, dc, err, io);
+    case TILE_BF16 * 4 + 3: return scatter_et<TILE_BF16, 3, FUSED>(st, N, out, nk, nstates, td, ep, dc, err, io);
+    case TILE_F16 * 4 + 3: return scatter_et<TILE_F16, 3, FUSED>(st, N, out, nk, nstates, td, ep, dc, err, io);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_tile_gather(cudaStream_t st, int N, const void* psi, int nk, int nstates, const TileDev& td,
@@ -732,13 +937,14 @@ cudaError_t launch_tile_gather(cudaStream_t st, int N, const void* psi, int nk, 
 cudaError_t launch_tile_scatter(cudaStream_t st, int N, void* out, int nk, int nstates, const TileDev& td,
                                 const EpiParams& ep, const void* dc, int* err) {
   if (td.nitems == 0) return cudaSuccess;
-  switch (td.ek * 4 + td.terms) {
-    case TILE_TF32 * 4 + 1: return scatter_et<TILE_TF32, 1>(st, N, out, nk, nstates, td, ep, dc, err);
-    case TILE_TF32 * 4 + 3: return scatter_et<TILE_TF32, 3>(st, N, out, nk, nstates, td, ep, dc, err);
-    case TILE_BF16 * 4 + 3: return scatter_et<TILE_BF16, 3>(st, N, out, nk, nstates, td, ep, dc, err);
-    case TILE_F16 * 4 + 3: return scatter_et<TILE_F16, 3>(st, N, out, nk, nstates, td, ep, dc, err);
-    default: return cudaErrorInvalidValue;
-  }
+  return scatter_dispatch<0>(st, N, out, nk, nstates, td, ep, dc, err, EpiIO{});
+}
+
+cudaError_t launch_tile_epilogue(cudaStream_t st, int N, int nk, int nstates, const TileDev& td, const EpiParams& ep,
+                                 const void* dc, int* err, const EpiIO& io) {
+  if (ep.mode != EPI_FIRST && ep.mode != EPI_RECUR) return cudaErrorInvalidValue;
+  if (td.nitems == 0) return cudaSuccess;
+  return scatter_dispatch<1>(st, N, nullptr, nk, nstates, td, ep, dc, err, io);
 }
 
 cudaError_t set_first_wait_tile(unsigned polls) { return cudaMemcpyToSymbol(g_first_wait, &polls, sizeof(polls)); }

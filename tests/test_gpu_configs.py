@@ -183,3 +183,24 @@ def test_bcc_full_size_step_matches_oracle(lib, bcc_step_case, precision, proj_m
     assert rel(out, o.psi) <= tol
     if precision == 0:
         assert abs(E["total"] - E_o["total"]) <= 1e-8
+
+
+@pytest.fixture(scope="module")
+def cluster_step_case():
+    """The magnetic cluster at full grid and with all 13 atoms, 4 of its 104 spinors (two spin
+    parallel and two antiparallel to their atom's axis), one ETRS step with the laser, by the oracle."""
+    wl = S.cluster(64, nsteps=4)
+    psi = np.ascontiguousarray(S.cluster_states(wl)[:, [0, 4, 51, 103]])
+    wl.occ = wl.occ[:, :4]
+    o, n, m, E = _oracle_one_step(wl, psi)
+    return wl, psi, o, n, m, E
+
+
+@pytest.mark.parametrize("precision,proj_mode,tol", [(0, None, 1e-10), (1, 5, 2e-5), (1, 1, 2e-5)])
+def test_cluster_full_size_step_matches_oracle(lib, cluster_step_case, precision, proj_mode, tol):
+    wl, psi, o, n_o, m_o, E_o = cluster_step_case
+    n, m, E, out = _gpu_one_step(wl, psi, o, precision, proj_mode)
+    assert rel(n, n_o) <= tol and rel(m, m_o) <= tol
+    assert rel(out, o.psi) <= tol
+    if precision == 0:
+        assert abs(E["total"] - E_o["total"]) <= 1e-8

@@ -1,6 +1,6 @@
 """GPU test of the allocation-free entry point tddft_hartree_noalloc.
 
-Callers that cannot allocate device memory (stream capture, pre-reserved memory pools,
+Callers that cannot allocate device memory (pre-reserved memory pools,
 allocation-free loops) use this entry point; it must give the same Hartree potential as
 the library's normal path.  On a handle with no atoms, no XC and no fields the potential
 4-vector returned by tddft_get_potential is V_v = [v_H, v_H, 0, 0], so its first component
