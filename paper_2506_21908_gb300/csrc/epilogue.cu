@@ -102,15 +102,24 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
   if (ld_acc1) { au1 = ld(acc1, ou); ad1 = ld(acc1, od); }
   if (ld_acc2) { au2 = ld(acc2, ou); ad2 = ld(acc2, od); }
   auto cmulr = [](C a, R cr, R ci) { return cmake<C>(cr * a.x - ci * a.y, cr * a.y + ci * a.x); };
+  // (x - c p) / Delta, and a times a complex series coefficient z; FP32 applies every constant as
+  // a float pair hi + lo (split_constants), FP64 as it is
+  auto shf = [&](R x, R p) -> R {
+    if constexpr (sizeof(R) == 4) return shifted_f(x, p, ep.f_c, ep.f_id);
+    else return (x - (R)ep.c * p) * (R)ep.inv_delta;
+  };
+  auto ccoef = [&](C a, const double* z, const float* zf) -> C {
+    if constexpr (sizeof(R) == 4) return cmul_split(a, zf);
+    else return cmulr(a, (R)z[0], (R)z[1]);
+  };
   if (AK == 2 && ep.mode == EPI_APPLY) {
     st(Tout, ou, hu[0], hu[1]);
     st(Tout, od, hd[0], hd[1]);
     return;
   }
   if (AK == 2 && ep.mode == EPI_TAYLOR) {
-    const R cr = (R)ep.a1[0], ci = (R)ep.a1[1];
     C tu[2], td[2];
-    for (int j = 0; j < 2; ++j) { tu[j] = cmulr(hu[j], cr, ci); td[j] = cmulr(hd[j], cr, ci); }
+    for (int j = 0; j < 2; ++j) { tu[j] = ccoef(hu[j], ep.a1, ep.f_a1); td[j] = ccoef(hd[j], ep.a1, ep.f_a1); }
     st(Tout, ou, tu[0], tu[1]);
     st(Tout, od, td[0], td[1]);
     const Pair<C> au = ld(acc1, ou), ad = ld(acc1, od);
@@ -118,7 +127,6 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
     st(acc1, od, cadd(ad.a, td[0]), cadd(ad.b, td[1]));
     return;
   }
-  const R cc = (R)ep.c, id = (R)ep.inv_delta;
   if (AK == 2 && (ep.mode == EPI_ADJ || ep.mode == EPI_ADJ0)) {
     // Clenshaw-type adjoint recurrence: S_k = f (H - c)/Delta S_{k+1} - S_{k+2} + seeds,
     // f = 2 (k >= 1) or 1 (k = 0); Tk holds S_{k+1}, Tkm1 holds S_{k+2} (may be null),
@@ -126,8 +134,8 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
     const R fct = (ep.mode == EPI_ADJ) ? (R)2 : (R)1;
     C su[2], sd[2];
     for (int j = 0; j < 2; ++j) {
-      su[j] = cmake<C>(fct * (hu[j].x - cc * pu[j].x) * id, fct * (hu[j].y - cc * pu[j].y) * id);
-      sd[j] = cmake<C>(fct * (hd[j].x - cc * pd[j].x) * id, fct * (hd[j].y - cc * pd[j].y) * id);
+      su[j] = cmake<C>(fct * shf(hu[j].x, pu[j].x), fct * shf(hu[j].y, pu[j].y));
+      sd[j] = cmake<C>(fct * shf(hd[j].x, pd[j].x), fct * shf(hd[j].y, pd[j].y));
     }
     if (Tkm1) {
       const Pair<C> qu = ld(Tkm1, ou), qd = ld(Tkm1, od);
@@ -136,15 +144,13 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
     }
     if (ep.use_acc1) {
       const Pair<C> yu = ld(acc1, ou), yd = ld(acc1, od);
-      const R ar = (R)ep.a1[0], ai = (R)ep.a1[1];
-      su[0] = cadd(su[0], cmulr(yu.a, ar, ai)); su[1] = cadd(su[1], cmulr(yu.b, ar, ai));
-      sd[0] = cadd(sd[0], cmulr(yd.a, ar, ai)); sd[1] = cadd(sd[1], cmulr(yd.b, ar, ai));
+      su[0] = cadd(su[0], ccoef(yu.a, ep.a1, ep.f_a1)); su[1] = cadd(su[1], ccoef(yu.b, ep.a1, ep.f_a1));
+      sd[0] = cadd(sd[0], ccoef(yd.a, ep.a1, ep.f_a1)); sd[1] = cadd(sd[1], ccoef(yd.b, ep.a1, ep.f_a1));
     }
     if (ep.use_acc2) {
       const Pair<C> yu = ld(acc2, ou), yd = ld(acc2, od);
-      const R br = (R)ep.b1[0], bi = (R)ep.b1[1];
-      su[0] = cadd(su[0], cmulr(yu.a, br, bi)); su[1] = cadd(su[1], cmulr(yu.b, br, bi));
-      sd[0] = cadd(sd[0], cmulr(yd.a, br, bi)); sd[1] = cadd(sd[1], cmulr(yd.b, br, bi));
+      su[0] = cadd(su[0], ccoef(yu.a, ep.b1, ep.f_b1)); su[1] = cadd(su[1], ccoef(yu.b, ep.b1, ep.f_b1));
+      sd[0] = cadd(sd[0], ccoef(yd.a, ep.b1, ep.f_b1)); sd[1] = cadd(sd[1], ccoef(yd.b, ep.b1, ep.f_b1));
     }
     st(Tout, ou, su[0], su[1]);
     st(Tout, od, sd[0], sd[1]);
@@ -154,31 +160,30 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
   C tu[2], td[2];
   if (first) {
     for (int j = 0; j < 2; ++j) {
-      tu[j] = cmake<C>((hu[j].x - cc * pu[j].x) * id, (hu[j].y - cc * pu[j].y) * id);
-      td[j] = cmake<C>((hd[j].x - cc * pd[j].x) * id, (hd[j].y - cc * pd[j].y) * id);
+      tu[j] = cmake<C>(shf(hu[j].x, pu[j].x), shf(hu[j].y, pu[j].y));
+      td[j] = cmake<C>(shf(hd[j].x, pd[j].x), shf(hd[j].y, pd[j].y));
     }
   } else {
     const C qus[2] = {qu0.a, qu0.b}, qds[2] = {qd0.a, qd0.b};
     for (int j = 0; j < 2; ++j) {
-      tu[j] = cmake<C>((R)2 * (hu[j].x - cc * pu[j].x) * id - qus[j].x, (R)2 * (hu[j].y - cc * pu[j].y) * id - qus[j].y);
-      td[j] = cmake<C>((R)2 * (hd[j].x - cc * pd[j].x) * id - qds[j].x, (R)2 * (hd[j].y - cc * pd[j].y) * id - qds[j].y);
+      tu[j] = cmake<C>((R)2 * shf(hu[j].x, pu[j].x) - qus[j].x, (R)2 * shf(hu[j].y, pu[j].y) - qus[j].y);
+      td[j] = cmake<C>((R)2 * shf(hd[j].x, pd[j].x) - qds[j].x, (R)2 * shf(hd[j].y, pd[j].y) - qds[j].y);
     }
   }
   st(Tout, ou, tu[0], tu[1]);
   st(Tout, od, td[0], td[1]);
   // Accumulators take up to three terms at once (T_{k-1}, T_k, T_{k+1}, all in registers here),
   // so the host updates each of them on every third term only.
-  auto upd = [&](C* acc, int init, const Pair<C>& au, const Pair<C>& ad, const double* cm, const double* c0,
-                 const double* c1) {
-    const R cmr = (R)cm[0], cmi = (R)cm[1], c0r = (R)c0[0], c0i = (R)c0[1], c1r = (R)c1[0], c1i = (R)c1[1];
+  auto upd = [&](C* acc, int init, const Pair<C>& au, const Pair<C>& ad, const double* cm, const float* cmf,
+                 const double* c0, const float* c0f, const double* c1, const float* c1f) {
     const C qus[2] = {qu0.a, qu0.b}, qds[2] = {qd0.a, qd0.b};
     C nu[2], nd[2];
     for (int j = 0; j < 2; ++j) {
-      nu[j] = cadd(cmulr(tu[j], c1r, c1i), cmulr(pu[j], c0r, c0i));
-      nd[j] = cadd(cmulr(td[j], c1r, c1i), cmulr(pd[j], c0r, c0i));
+      nu[j] = cadd(ccoef(tu[j], c1, c1f), ccoef(pu[j], c0, c0f));
+      nd[j] = cadd(ccoef(td[j], c1, c1f), ccoef(pd[j], c0, c0f));
       if (rec) {
-        nu[j] = cadd(nu[j], cmulr(qus[j], cmr, cmi));
-        nd[j] = cadd(nd[j], cmulr(qds[j], cmr, cmi));
+        nu[j] = cadd(nu[j], ccoef(qus[j], cm, cmf));
+        nd[j] = cadd(nd[j], ccoef(qds[j], cm, cmf));
       }
     }
     if (!init) {
@@ -188,8 +193,8 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
     st(acc, ou, nu[0], nu[1]);
     st(acc, od, nd[0], nd[1]);
   };
-  if (use1) upd(acc1, ep.init1, au1, ad1, ep.am, ep.a0, ep.a1);
-  if (use2) upd(acc2, ep.init2, au2, ad2, ep.bm, ep.b0, ep.b1);
+  if (use1) upd(acc1, ep.init1, au1, ad1, ep.am, ep.f_am, ep.a0, ep.f_a0, ep.a1, ep.f_a1);
+  if (use2) upd(acc2, ep.init2, au2, ad2, ep.bm, ep.f_bm, ep.b0, ep.f_b0, ep.b1, ep.f_b1);
 }
 
 template <typename R, int NLM, int SP, typename... A>
@@ -215,6 +220,7 @@ cudaError_t launch_epilogue(cudaStream_t st, int N, const void* kin, const void*
   dim3 grid((unsigned)(sp ? (N3 + 255) / 256 : (N3 / 2 + 255) / 256), sp ? nkb / 2 : nkb);
   const int nlm = pt.natoms > 0 ? pt.nlm : 0;
   EpiParams epx = ep;
+  split_constants(epx);
   const size_t dcb = (size_t)pt.natoms * 2 * nlm * sizeof(C) * (sp ? 2 : 1);
   epx.dc_staged = (nlm > 0 && dcb <= 32 * 1024) ? 1 : 0;
   const size_t smem = epx.dc_staged ? dcb : 0;

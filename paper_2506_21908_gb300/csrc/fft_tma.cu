@@ -40,15 +40,13 @@ __device__ __forceinline__ void issue_rows(const float2* g, size_t stride, float
 
 // Threads and resident CTAs: 256 threads; the two 36 KB buffers of a 64^2 plane allow three
 // CTAs per SM.  (512 threads at two CTAs per SM, one item per thread and side, were slower:
-// 0.190 against 0.161 ms per pass at 64^3 x 208 components.)
-// At 96^2 (8 x 12) 384 threads give both item loops whole iterations; the two 78 KB buffers
-// leave room for one CTA per SM.
+// 0.190 against 0.161 ms per pass at 64^3 x 208 components.)  At 96^2 the two 78 KB buffers leave
+// one CTA per SM, and the register-fed pass is faster (7.2 against 9.0 ms per pass at 96^3 x 2048
+// components), so 96 takes that pass.
 template <int N> struct XyTmaThreads { static constexpr int value = 256; };
-template <> struct XyTmaThreads<96> { static constexpr int value = 384; };
 template <int N> struct XyTmaBlocks { static constexpr int value = 4; };
 template <> struct XyTmaBlocks<64> { static constexpr int value = 3; };
 template <> struct XyTmaBlocks<48> { static constexpr int value = 3; };
-template <> struct XyTmaBlocks<96> { static constexpr int value = 1; };
 
 }  // namespace
 
@@ -243,7 +241,7 @@ k_fft_xy2_tma(const float2* src, float2* dst, const float2* __restrict__ twg, in
   }
 }
 
-bool fft_xy_tma_supported(int N) { return N == 16 || N == 24 || N == 32 || N == 48 || N == 64 || N == 96; }
+bool fft_xy_tma_supported(int N) { return N == 16 || N == 24 || N == 32 || N == 48 || N == 64; }
 
 template <int N>
 static cudaError_t xy_tma_n(cudaStream_t st, const void* src, void* dst, int nbatch, const void* tw, bool inv,
@@ -279,7 +277,6 @@ cudaError_t launch_fft_xy_tma(cudaStream_t st, int N, const void* src, void* dst
     case 32: return xy_tma_n<32>(st, src, dst, nbatch, tw, inv, err);
     case 48: return xy_tma_n<48>(st, src, dst, nbatch, tw, inv, err);
     case 64: return xy_tma_n<64>(st, src, dst, nbatch, tw, inv, err);
-    case 96: return xy_tma_n<96>(st, src, dst, nbatch, tw, inv, err);
     default: return cudaErrorNotSupported;
   }
 }

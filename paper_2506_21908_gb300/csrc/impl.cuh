@@ -41,7 +41,37 @@ struct EpiParams {
   int nstates;
   int dc_staged;                // fused kernel: D c copied to shared memory (set by its launcher)
   int spinor_pairs;             // epilogue: one point of two spinors per thread (even nstates)
+  // FP32 kernels: c and 1 / Delta as {hi, lo}, the coefficients as {re hi, im hi, re lo, im lo}
+  // (hi = the value rounded to float, lo = the rounded remainder; set by split_constants)
+  float f_c[2], f_id[2];
+  float f_a0[4], f_a1[4], f_b0[4], f_b1[4], f_am[4], f_bm[4];
 };
+
+// The series constants are applied identically at every term, every step and every grid point, so
+// the rounding of one of them to FP32 is an error of the same sign everywhere: a coefficient off
+// by a relative 6e-8 makes the propagator non-unitary by about that much per step, which adds up
+// linearly over a run (and a rounded 1 / Delta rescales H).  FP32 kernels therefore apply each
+// constant as the float pair hi + lo, exact to ~1e-14.
+inline void split_constants(EpiParams& e) {
+  auto s2 = [](double x, float* o) {
+    o[0] = (float)x;
+    o[1] = (float)(x - (double)o[0]);
+  };
+  auto s4 = [](const double* z, float* o) {
+    o[0] = (float)z[0];
+    o[1] = (float)z[1];
+    o[2] = (float)(z[0] - (double)o[0]);
+    o[3] = (float)(z[1] - (double)o[1]);
+  };
+  s2(e.c, e.f_c);
+  s2(e.inv_delta, e.f_id);
+  s4(e.a0, e.f_a0);
+  s4(e.a1, e.f_a1);
+  s4(e.b0, e.f_b0);
+  s4(e.b1, e.f_b1);
+  s4(e.am, e.f_am);
+  s4(e.bm, e.f_bm);
+}
 
 // Device-side projector tables.
 template <typename R> struct ProjTables {

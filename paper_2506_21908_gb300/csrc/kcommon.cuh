@@ -16,6 +16,18 @@ template <int N> struct FFTMinBlocks<float, N> { static constexpr int value = (N
 
 template <int N> __device__ __forceinline__ int freq(int i) { return i < N / 2 ? i : i - N; }
 
+// FP32 Chebyshev arithmetic with the series constants as float pairs hi + lo (see
+// split_constants): (x - c p) / Delta with c = {hi, lo} and 1 / Delta = {hi, lo} ...
+__device__ __forceinline__ float shifted_f(float x, float p, const float* c, const float* id) {
+  const float d = (x - c[0] * p) - c[1] * p;
+  return d * id[0] + d * id[1];
+}
+// ... and a z for the complex constant z = {re hi, im hi, re lo, im lo}.
+__device__ __forceinline__ float2 cmul_split(float2 a, const float* z) {
+  return make_float2((z[0] * a.x - z[1] * a.y) + (z[2] * a.x - z[3] * a.y),
+                     (z[0] * a.y + z[1] * a.x) + (z[2] * a.y + z[3] * a.x));
+}
+
 #define TDDFT_DISPATCH_N(N, CALL)          \
   switch (N) {                             \
     case 8: { constexpr int NN = 8; return CALL; }   \

@@ -716,7 +716,6 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
     const int row = quarter * 32 + lane;
     const int cbeg = half * (SC / 2), cend = (half + 1) * (SC / 2);
     // epilogue constants (Chebyshev term k: T_{k+1} = f (H - c) T_k / Delta - T_{k-1}, f = 1 or 2)
-    const float cc = (float)ep.c, idl = (float)ep.inv_delta;
     const bool rec = ep.mode == EPI_RECUR;
     const bool use1 = ep.use_acc1, use2 = ep.use_acc2;
     const bool ld1 = use1 && !ep.init1, ld2 = use2 && !ep.init2;
@@ -815,27 +814,27 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
               hu = make_float2(hu.x + V0 * u.x + hx * d.x - hy * d.y, hu.y + V0 * u.y + hx * d.y + hy * d.x);
               hd = make_float2(hd.x + V1 * d.x + hx * u.x + hy * u.y, hd.y + V1 * d.y + hx * u.y - hy * u.x);
               float2 tu, td;
+              // the series constants as float pairs (split_constants)
               if (!rec) {
-                tu = make_float2((hu.x - cc * u.x) * idl, (hu.y - cc * u.y) * idl);
-                td = make_float2((hd.x - cc * d.x) * idl, (hd.y - cc * d.y) * idl);
+                tu = make_float2(shifted_f(hu.x, u.x, ep.f_c, ep.f_id), shifted_f(hu.y, u.y, ep.f_c, ep.f_id));
+                td = make_float2(shifted_f(hd.x, d.x, ep.f_c, ep.f_id), shifted_f(hd.y, d.y, ep.f_c, ep.f_id));
               } else {
-                tu = make_float2(2.f * (hu.x - cc * u.x) * idl - qu[j].x, 2.f * (hu.y - cc * u.y) * idl - qu[j].y);
-                td = make_float2(2.f * (hd.x - cc * d.x) * idl - qd[j].x, 2.f * (hd.y - cc * d.y) * idl - qd[j].y);
+                tu = make_float2(2.f * shifted_f(hu.x, u.x, ep.f_c, ep.f_id) - qu[j].x,
+                                 2.f * shifted_f(hu.y, u.y, ep.f_c, ep.f_id) - qu[j].y);
+                td = make_float2(2.f * shifted_f(hd.x, d.x, ep.f_c, ep.f_id) - qd[j].x,
+                                 2.f * shifted_f(hd.y, d.y, ep.f_c, ep.f_id) - qd[j].y);
               }
               io.Tout[ou] = tu;
               io.Tout[od] = td;
               // accumulators: up to three terms (T_{k-1}, T_k, T_{k+1}) at once
-              auto upd = [&](float2* accp, int init, float2 ou_old, float2 od_old, const double* cmv, const double* c0v,
-                             const double* c1v) {
-                const float cmr = (float)cmv[0], cmi = (float)cmv[1], c0r = (float)c0v[0], c0i = (float)c0v[1];
-                const float c1r = (float)c1v[0], c1i = (float)c1v[1];
-                auto mulr = [](float2 a, float r_, float i_) { return make_float2(r_ * a.x - i_ * a.y, r_ * a.y + i_ * a.x); };
-                float2 nu = mulr(tu, c1r, c1i), nd = mulr(td, c1r, c1i);
-                const float2 pu0 = mulr(u, c0r, c0i), pd0 = mulr(d, c0r, c0i);
+              auto upd = [&](float2* accp, int init, float2 ou_old, float2 od_old, const float* cmf, const float* c0f,
+                             const float* c1f) {
+                float2 nu = cmul_split(tu, c1f), nd = cmul_split(td, c1f);
+                const float2 pu0 = cmul_split(u, c0f), pd0 = cmul_split(d, c0f);
                 nu = make_float2(nu.x + pu0.x, nu.y + pu0.y);
                 nd = make_float2(nd.x + pd0.x, nd.y + pd0.y);
                 if (rec) {
-                  const float2 qu0 = mulr(qu[j], cmr, cmi), qd0 = mulr(qd[j], cmr, cmi);
+                  const float2 qu0 = cmul_split(qu[j], cmf), qd0 = cmul_split(qd[j], cmf);
                   nu = make_float2(nu.x + qu0.x, nu.y + qu0.y);
                   nd = make_float2(nd.x + qd0.x, nd.y + qd0.y);
                 }
@@ -846,8 +845,8 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
                 accp[ou] = nu;
                 accp[od] = nd;
               };
-              if (use1) upd(io.acc1, ep.init1, au[j], ad[j], ep.am, ep.a0, ep.a1);
-              if (use2) upd(io.acc2, ep.init2, bu[j], bd[j], ep.bm, ep.b0, ep.b1);
+              if (use1) upd(io.acc1, ep.init1, au[j], ad[j], ep.f_am, ep.f_a0, ep.f_a1);
+              if (use2) upd(io.acc2, ep.init2, bu[j], bd[j], ep.f_bm, ep.f_b0, ep.f_b1);
             }
           }
         }
@@ -944,7 +943,9 @@ cudaError_t launch_tile_epilogue(cudaStream_t st, int N, int nk, int nstates, co
                                  const void* dc, int* err, const EpiIO& io) {
   if (ep.mode != EPI_FIRST && ep.mode != EPI_RECUR) return cudaErrorInvalidValue;
   if (td.nitems == 0) return cudaSuccess;
-  return scatter_dispatch<1>(st, N, nullptr, nk, nstates, td, ep, dc, err, io);
+  EpiParams epx = ep;
+  split_constants(epx);
+  return scatter_dispatch<1>(st, N, nullptr, nk, nstates, td, epx, dc, err, io);
 }
 
 cudaError_t set_first_wait_tile(unsigned polls) { return cudaMemcpyToSymbol(g_first_wait, &polls, sizeof(polls)); }

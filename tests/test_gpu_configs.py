@@ -89,6 +89,34 @@ def test_cluster_full_size_step_mixed_vs_fp64(lib, cluster_case):
     assert abs(E32["total"] - E64["total"]) <= 1e-4
 
 
+@pytest.fixture(scope="module")
+def cluster_enl(cluster_case):
+    """The oracle's nonlocal energy sum_i f_i <psi_i|V_NL|psi_i> of the cluster at t = 0."""
+    wl, psi, _, _, _ = cluster_case
+    s = System.from_workload(wl)
+    A, _ = FieldTable(wl.times, wl.A, wl.B).at(0.0)
+    wf = s.kw[0] * s.occ[0]
+    nk = s.apply_nonlocal(psi[0], s.kpts[0] + A)
+    return float(sum(wf[i] * np.vdot(psi[0, i], nk[i]).real for i in range(psi.shape[1])) * s.grid.dV)
+
+
+# The tensor cores round each accumulation of a product into the FP32 accumulator with a bias
+# toward zero; over the hundreds of MMAs of one brick sum this took a relative 1e-5 off every
+# projection (E_nl low by 1e-5 relative with FP16 x3, 1.4e-5 with TF32 x3), which the grouped
+# accumulation removes down to ~1.5e-6.  The tolerances are the bound for each contraction.
+@pytest.mark.parametrize("precision,proj_mode,tol", [(0, None, 1e-10), (1, 1, 1e-6), (1, 3, 4e-6), (1, 4, 1e-5),
+                                                     (1, 5, 4e-6)])
+def test_cluster_nonlocal_energy_matches_oracle(lib, cluster_case, cluster_enl, precision, proj_mode, tol):
+    from paper_2506_21908_gb300 import _lib
+    wl, psi, _, _, _ = cluster_case
+    h = _lib.TDDFT.from_workload(wl, precision=precision, proj_mode=proj_mode)
+    h.set_fields(wl.times, wl.A, wl.B)
+    h.set_states(psi, 0.0)
+    _, _, E, _ = h.observables(fields=False)
+    h.close()
+    assert abs(E["nl"] - cluster_enl) <= tol * abs(cluster_enl), (E["nl"], cluster_enl)
+
+
 def test_bcc_full_size_sampled_h_fp32_mixed(lib):
     wl = S.bcc(nsteps=8)
     psi = S.bcc_states(wl)

@@ -406,7 +406,7 @@ def test_gather_overlap_gives_identical_bits(lib, precision, monkeypatch):
     assert np.array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("n", [16, 24, 32, 48, 64, 96])
+@pytest.mark.parametrize("n", [16, 24, 32, 48, 64])
 def test_bulk_copy_xy_pass_gives_identical_bits(lib, n, monkeypatch):
     """FP32 xy passes fed by bulk asynchronous copies (double-buffered planes in shared memory)
     against the register-fed passes (TDDFT_NO_TMA=1): the same DFT arithmetic in the same order,
