@@ -28,6 +28,33 @@ __device__ __forceinline__ float2 cmul_split(float2 a, const float* z) {
                      (z[0] * a.y + z[1] * a.x) + (z[2] * a.y + z[3] * a.x));
 }
 
+// Accumulator updates acc += sum_j z_j t_j in float-float arithmetic, rounded to FP32 once.
+// Rounding each product of FP32 data with a fixed FP32 constant (and each partial sum) is biased
+// for a given constant: summed over a state the errors do not cancel, and the series output gains
+// or loses ~1e-8 of its norm per series, every step in the same direction (an FP32 path drifted
+// by ~6e-8 in norm per step).  Here every product is split exactly (p + pe = a b, by a fused
+// multiply-add) and every sum is exact (hi + lo, Knuth's two-sum), so the update is the exact
+// value rounded once.  __fmul_rn / __fadd_rn are never contracted into multiply-adds, which would
+// break the splits.
+__device__ __forceinline__ void ff_madd(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = fmaf(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo += e + pe;
+}
+// (hi, lo) += t z for the complex constant z = {re hi, im hi, re lo, im lo}.
+__device__ __forceinline__ void ff_cmadd(float2& hi, float2& lo, float2 t, const float* z) {
+  ff_madd(hi.x, lo.x, z[0], t.x);
+  ff_madd(hi.x, lo.x, -z[1], t.y);
+  ff_madd(hi.y, lo.y, z[0], t.y);
+  ff_madd(hi.y, lo.y, z[1], t.x);
+  lo.x += z[2] * t.x - z[3] * t.y;
+  lo.y += z[2] * t.y + z[3] * t.x;
+}
+
 #define TDDFT_DISPATCH_N(N, CALL)          \
   switch (N) {                             \
     case 8: { constexpr int NN = 8; return CALL; }   \
