@@ -232,8 +232,9 @@ def kernel_source_hash(kernel_class):
 def measured_traffic(kernel_class, workload, units_per_launch):
     """DRAM bytes (read + write) per launch of `kernel_class` from the committed ncu summary
     profiles/traffic_<class>_<workload>.txt (bytes per spinor-gridpoint unit, averaged over the
-    captured launches), scaled to this launch size; None when there is no summary or the kernels
-    changed since it was taken."""
+    captured launches, plus an optional per-launch constant such as a table read once per launch),
+    scaled to this launch size; None when there is no summary or the kernels changed since it was
+    taken."""
     path = os.path.join(ROOT, "profiles", "traffic_%s_%s.txt" % (kernel_class, workload))
     if not os.path.exists(path):
         return None, "no ncu summary for this kernel and workload"
@@ -244,7 +245,8 @@ def measured_traffic(kernel_class, workload, units_per_launch):
             kv[k.strip()] = v.strip()
     if kv.get("source_sha256") != kernel_source_hash(kernel_class):
         return None, "kernels changed since the ncu capture (%s)" % os.path.basename(path)
-    return float(kv["dram_bytes_per_unit"]) * units_per_launch, os.path.basename(path)
+    const = float(kv.get("dram_bytes_per_launch_const", "0"))
+    return float(kv["dram_bytes_per_unit"]) * units_per_launch + const, os.path.basename(path)
 
 
 def hbm_peak():
