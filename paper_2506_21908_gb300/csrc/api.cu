@@ -897,16 +897,12 @@ static void acc_schedule(int k, int Ka, const std::vector<cd>& cf, int& done, in
 
 // One Chebyshev series: T_k of H~ = (H - c)/Delta applied to `in`, accumulated with
 // coefficients cf1 (orders 0..K1) into acc1 and, when acc2 is set, cf2 (0..K2) into acc2.
-// acc1_pred: acc1 is the predictor (it only feeds the density at t + dt), whose FP32 updates
-// skip the float-float form that the state-carrying accumulators take.
 template <typename R>
 tddft_status cheb_series(tddft_ctx* c, const void* in, const R* Vr, const double A[3], void* acc1,
                          const std::vector<cd>& cf1, int K1, void* acc2, const std::vector<cd>& cf2, int K2,
-                         void* const* slots = nullptr, bool acc1_pred = false) {
+                         void* const* slots = nullptr) {
   const int K = std::max(K1, acc2 ? K2 : 0);
   EpiParams ep{};
-  ep.exact1 = acc1_pred ? 0 : 1;
-  ep.exact2 = 1;
   ep.c = 0.5 * (c->emax + c->emin);
   ep.inv_delta = 1.0 / (0.5 * (c->emax - c->emin));
   ep.nstates = c->nb;
@@ -995,7 +991,7 @@ template <typename R> tddft_status one_step(tddft_ctx* c) {
   tddft_status s;
   if (c->exp_kind != TDDFT_EXP_TAYLOR) {
     if ((s = cheb_series<R>(c, c->psi, vsel<R>(c, true), A0, c->pred, c->cf_full, c->K_full, c->phi, c->cf_half,
-                            c->K_half, nullptr, true)))
+                            c->K_half)))
       return s;
   } else {
     if ((s = taylor_series<R>(c, c->psi, true, A0, c->dt, c->K_full, c->pred))) return s;
@@ -1232,7 +1228,7 @@ tddft_status adjoint_step(tddft_ctx* c, AdjWork& w, const void* psi_n, double t0
   // ---- recompute the step, keeping every term
   if ((s = density<R>(c, psi_n, w.rho_n)) || (s = potential(c, w.rho_n, t0, w.V_n, f64 ? nullptr : w.Vf_n))) return s;
   if ((s = cheb_series<R>(c, psi_n, vptr<R>(c, w.V_n, w.Vf_n), A0, w.pred, c->cf_full, c->K_full, w.phi, c->cf_half,
-                          c->K_half, w.slots1.data(), true)))
+                          c->K_half, w.slots1.data())))
     return s;
   const void* src = w.pred;
   for (int j = 0; j <= c->n_sc; ++j) {

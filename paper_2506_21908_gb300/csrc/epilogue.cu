@@ -174,33 +174,28 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
   st(Tout, od, td[0], td[1]);
   // Accumulators take up to three terms at once (T_{k-1}, T_k, T_{k+1}, all in registers here),
   // so the host updates each of them on every third term only.
-  auto upd = [&](C* acc, int init, int exact, const Pair<C>& au, const Pair<C>& ad, const double* cm,
-                 const float* cmf, const double* c0, const float* c0f, const double* c1, const float* c1f) {
+  auto upd = [&](C* acc, int init, const Pair<C>& au, const Pair<C>& ad, const double* cm, const float* cmf,
+                 const double* c0, const float* c0f, const double* c1, const float* c1f) {
     const C qus[2] = {qu0.a, qu0.b}, qds[2] = {qd0.a, qd0.b};
     C nu[2], nd[2];
-    bool done = false;
     if constexpr (sizeof(R) == 4) {
-      if (exact) {
-        // float-float update, rounded once (ff_cmadd)
-        const C aus[2] = {au.a, au.b}, ads[2] = {ad.a, ad.b};
-        const C z2 = cmake<C>(0.f, 0.f);
-        for (int j = 0; j < 2; ++j) {
-          C hu2 = init ? z2 : aus[j], hd2 = init ? z2 : ads[j], lu = z2, ld = z2;
-          ff_cmadd(hu2, lu, tu[j], c1f);
-          ff_cmadd(hd2, ld, td[j], c1f);
-          ff_cmadd(hu2, lu, pu[j], c0f);
-          ff_cmadd(hd2, ld, pd[j], c0f);
-          if (rec) {
-            ff_cmadd(hu2, lu, qus[j], cmf);
-            ff_cmadd(hd2, ld, qds[j], cmf);
-          }
-          nu[j] = cadd(hu2, lu);
-          nd[j] = cadd(hd2, ld);
+      // float-float update, rounded once (ff_cmadd)
+      const C aus[2] = {au.a, au.b}, ads[2] = {ad.a, ad.b};
+      const C z2 = cmake<C>(0.f, 0.f);
+      for (int j = 0; j < 2; ++j) {
+        C hu2 = init ? z2 : aus[j], hd2 = init ? z2 : ads[j], lu = z2, ld = z2;
+        ff_cmadd(hu2, lu, tu[j], c1f);
+        ff_cmadd(hd2, ld, td[j], c1f);
+        ff_cmadd(hu2, lu, pu[j], c0f);
+        ff_cmadd(hd2, ld, pd[j], c0f);
+        if (rec) {
+          ff_cmadd(hu2, lu, qus[j], cmf);
+          ff_cmadd(hd2, ld, qds[j], cmf);
         }
-        done = true;
+        nu[j] = cadd(hu2, lu);
+        nd[j] = cadd(hd2, ld);
       }
-    }
-    if (!done) {
+    } else {
       for (int j = 0; j < 2; ++j) {
         nu[j] = cadd(ccoef(tu[j], c1, c1f), ccoef(pu[j], c0, c0f));
         nd[j] = cadd(ccoef(td[j], c1, c1f), ccoef(pd[j], c0, c0f));
@@ -217,8 +212,8 @@ k_epilogue(const typename CT<R>::type* __restrict__ kin, const typename CT<R>::t
     st(acc, ou, nu[0], nu[1]);
     st(acc, od, nd[0], nd[1]);
   };
-  if (use1) upd(acc1, ep.init1, ep.exact1, au1, ad1, ep.am, ep.f_am, ep.a0, ep.f_a0, ep.a1, ep.f_a1);
-  if (use2) upd(acc2, ep.init2, ep.exact2, au2, ad2, ep.bm, ep.f_bm, ep.b0, ep.f_b0, ep.b1, ep.f_b1);
+  if (use1) upd(acc1, ep.init1, au1, ad1, ep.am, ep.f_am, ep.a0, ep.f_a0, ep.a1, ep.f_a1);
+  if (use2) upd(acc2, ep.init2, au2, ad2, ep.bm, ep.f_bm, ep.b0, ep.f_b0, ep.b1, ep.f_b1);
 }
 
 template <typename R, int NLM, int SP, typename... A>

@@ -45,9 +45,6 @@ struct EpiParams {
   // (hi = the value rounded to float, lo = the rounded remainder; set by split_constants)
   float f_c[2], f_id[2];
   float f_a0[4], f_a1[4], f_b0[4], f_b1[4], f_am[4], f_bm[4];
-  // FP32 kernels: accumulator 1 / 2 carries the state (float-float updates, ff_cmadd); the
-  // predictor, which only feeds the density at t + dt, takes the plain FP32 update
-  int exact1, exact2;
 };
 
 // The series constants are applied identically at every term, every step and every grid point, so

@@ -827,28 +827,9 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
               io.Tout[ou] = tu;
               io.Tout[od] = td;
               // accumulators: up to three terms (T_{k-1}, T_k, T_{k+1}) at once
-              // accumulators that carry the state: float-float update, rounded once (ff_cmadd);
-              // the predictor: plain FP32 (both as in k_epilogue)
-              auto upd = [&](float2* accp, int init, int exact, float2 ou_old, float2 od_old, const float* cmf,
-                             const float* c0f, const float* c1f) {
-                if (!exact) {
-                  float2 nu = cmul_split(tu, c1f), nd = cmul_split(td, c1f);
-                  const float2 pu0 = cmul_split(u, c0f), pd0 = cmul_split(d, c0f);
-                  nu = make_float2(nu.x + pu0.x, nu.y + pu0.y);
-                  nd = make_float2(nd.x + pd0.x, nd.y + pd0.y);
-                  if (rec) {
-                    const float2 qu0 = cmul_split(qu[j], cmf), qd0 = cmul_split(qd[j], cmf);
-                    nu = make_float2(nu.x + qu0.x, nu.y + qu0.y);
-                    nd = make_float2(nd.x + qd0.x, nd.y + qd0.y);
-                  }
-                  if (!init) {
-                    nu = make_float2(nu.x + ou_old.x, nu.y + ou_old.y);
-                    nd = make_float2(nd.x + od_old.x, nd.y + od_old.y);
-                  }
-                  accp[ou] = nu;
-                  accp[od] = nd;
-                  return;
-                }
+              // float-float update, rounded once (ff_cmadd), as in k_epilogue
+              auto upd = [&](float2* accp, int init, float2 ou_old, float2 od_old, const float* cmf, const float* c0f,
+                             const float* c1f) {
                 const float2 z2 = make_float2(0.f, 0.f);
                 float2 hu2 = init ? z2 : ou_old, hd2 = init ? z2 : od_old, lu = z2, ld = z2;
                 ff_cmadd(hu2, lu, tu, c1f);
@@ -862,8 +843,8 @@ k_tile_scatter(float2* out, int N, int comps_per_k, int sgroups, int nstates, in
                 accp[ou] = make_float2(hu2.x + lu.x, hu2.y + lu.y);
                 accp[od] = make_float2(hd2.x + ld.x, hd2.y + ld.y);
               };
-              if (use1) upd(io.acc1, ep.init1, ep.exact1, au[j], ad[j], ep.f_am, ep.f_a0, ep.f_a1);
-              if (use2) upd(io.acc2, ep.init2, ep.exact2, bu[j], bd[j], ep.f_bm, ep.f_b0, ep.f_b1);
+              if (use1) upd(io.acc1, ep.init1, au[j], ad[j], ep.f_am, ep.f_a0, ep.f_a1);
+              if (use2) upd(io.acc2, ep.init2, bu[j], bd[j], ep.f_bm, ep.f_b0, ep.f_b1);
             }
           }
         }
