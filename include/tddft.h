@@ -63,7 +63,9 @@ enum { TDDFT_SPIN_NONCOLLINEAR = 0, TDDFT_SPIN_COLLINEAR = 1, TDDFT_SPIN_UNPOLAR
  * a split product hi*hi + hi*lo + lo*hi of TF32, BF16 or FP16 parts (each value = hi + lo; TF32 x3
  * and FP16 x3 close to FP32 accuracy, BF16 x3 about 16 bits); FP32 accumulation in every case.  The
  * tensor-core forms contract brick by brick (bricks of 32 or 16 x 8 x 8 grid points against every
- * projector sphere reaching into them) for both the projection <beta~|psi> and V_NL psi. */
+ * projector sphere reaching into them) for both the projection <beta~|psi> and V_NL psi; the
+ * projection restarts its tensor-core accumulation every few chunks of a brick and adds the groups
+ * on the CUDA cores, so that the accumulation's rounding does not bias it. */
 enum { TDDFT_PROJ_FP64 = 0, TDDFT_PROJ_FP32 = 1, TDDFT_PROJ_TF32 = 2, TDDFT_PROJ_TF32X3 = 3,
        TDDFT_PROJ_BF16X3 = 4, TDDFT_PROJ_F16X3 = 5 };
 
@@ -115,7 +117,8 @@ typedef struct {
 
 /* Run parameters.
  *   precision : TDDFT_FP64, or TDDFT_FP32_MIXED (spinors, FFTs, potential apply and projectors
- *               in FP32; density, XC, Hartree, energies and norms in FP64)
+ *               in FP32, the series constants as float pairs and the series accumulators updated
+ *               in float-float arithmetic; density, XC, Hartree, energies and norms in FP64)
  *   proj_mode : TDDFT_PROJ_FP64 / TDDFT_PROJ_FP32 (CUDA cores; they follow the precision) or one of
  *               the tensor-core modes TDDFT_PROJ_TF32 / _TF32X3 / _BF16X3 / _F16X3 (FP32-mixed
  *               precision and a grid size divisible by 16, else TDDFT_ERR_UNSUPPORTED; the discrete
